@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: Jamiolkowski-fidelity evaluations per second on one GB300 (or N, one process each).
+
+Workload (one step): F_J of the 10 mid-size instances -- n = 16 qubits on a line, 200 gates
+(U3 layers + nearest-neighbour CX bricks), 10 noises (depolarising or amplitude damping,
+p, gamma ~ U[1e-4, 1e-2]) after random gates -- each through Alg. II's doubled network
+(Sec. IV-B), seeds 0-9 (rank r uses seeds 10r..10r+9; weak scaling).
+
+value   : evaluations/s with inputs resident on the device (CUDA events on the launch stream,
+          L2 flushed with a 256 MiB write before every step, max over ranks).
+e2e     : evaluations/s through the public C-ABI calls from host arrays (load, plan -- reused
+          from the structural plan cache --, upload, run, read back F), host wall clock.
+roofline: the dominant kernel class, its algorithmic flops / bytes over its CUDA-event time.
+plain   : the same workload in FP64 (AJF_PREC_F64) for the fast-vs-plain comparison.
+cpu_baseline / --impl reference: the CPU oracle (oracle/network.py, Alg. II, min-fill order)
+          on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_INSTANCES = 10
+WORKLOAD = ("mid: n=16 line, 200 gates (U3 + NN-CX bricks), 10 noises (dep/AD, U[1e-4,1e-2]), "
+            "Alg. II doubled network, 10 seeds per step")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "bf16_tflops": p.get("bf16_tflops", 1900.0),
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", 1700.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.file:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [r.strip().split(",") for r in f if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(budget_s: float = 30.0):
+    """Oracle O2 (Alg. II network, min-fill order, numpy tensordot, complex128) on mid seed 0."""
+    import numpy as np  # noqa: F401
+    from oracle import network
+    from paper_2103_11595_gb300 import workloads as W
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        network.alg2_fidelity(W.mid(done % N_INSTANCES if done else 0), order="minfill")
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 1:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} evaluation(s) of mid seed 0 (Alg. II, oracle/network.py, min-fill order, "
+                      f"numpy complex128 tensordot, default BLAS threads) in {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state worth excluding beyond imports
+    for _ in range(max(1, args.steps)):
+        s = oracle_sample()
+        vals.append(1.0 / s["value"])
+    secs = sum(vals) / len(vals)
+    value = 1.0 / secs
+    line = {"impl": "reference", "metric": "fidelity evals/s", "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (one seed per step: bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "one mid-config evaluation per step (seed 0), oracle Alg. II network"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32")
+    ap.add_argument("--trials", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    __graft_entry__.build()
+    from paper_2103_11595_gb300 import ajf
+    from paper_2103_11595_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    insts = [W.mid(rank * N_INSTANCES + i) for i in range(N_INSTANCES)]
+
+    def make_contexts(precision, use_graph=True):
+        ctxs, infos = [], []
+        for inst in insts:
+            c = ajf.Context(dev, stream.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            infos.append(ajf.ajf_plan(c.handle, 2, precision=precision, trials=args.trials, use_graph=use_graph))
+            ajf.ajf_upload(c.handle)
+            ctxs.append(c)
+        return ctxs, infos
+
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    out = torch.zeros(N_INSTANCES, 3, dtype=torch.float64, device=dev)
+
+    def timed_steps(ctxs, steps, warmup):
+        def step():
+            for i, c in enumerate(ctxs):
+                ajf.ajf_launch(c.handle, out[i].data_ptr())
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step()
+            stream.synchronize()
+            barrier(world)
+            torch.cuda.synchronize()
+            total_ms = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                total_ms += e0.elapsed_time(e1)
+            torch.cuda.synchronize()
+            barrier(world)
+        return total_ms
+
+    # ---- fast path: timed region with clock sampling
+    ctxs, infos = make_contexts(args.precision)
+    with ClockSampler(dev) as clk:
+        total_ms = timed_steps(ctxs, args.steps, args.warmup)
+    clocks = clk.summary()
+    F_fast = out[:, 1].cpu().numpy().copy()
+    total_s = max_over_ranks(total_ms / 1e3, world)
+    evals = N_INSTANCES * args.steps * world
+    value = evals / total_s
+    flops_per_step = sum(i["flops"] for i in infos)
+    launches_per_step = sum(i["n_launches"] for i in infos)
+
+    # ---- per-kernel timing (CUDA events inside the library, same stream)
+    for c in ctxs:
+        ajf.ajf_profile_enable(c.handle, True)
+    with torch.cuda.stream(stream):
+        for i, c in enumerate(ctxs):
+            ajf.ajf_launch(c.handle, out[i].data_ptr())
+    stream.synchronize()
+    classes = {}
+    for c in ctxs:
+        for k, v in ajf.ajf_profile_read(c.handle).items():
+            acc = classes.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+            for f in acc:
+                acc[f] += v[f]
+        ajf.ajf_profile_enable(c.handle, False)
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    pk = peaks()
+    d = classes[dom]
+    if dom == "gemm_tc":
+        kind = infos[0].get("n_tc_gemms", 0)
+        peak = pk["bf16_tflops"] * (1.1 / 2.25)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                "peak_src": f"{pk['src']} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    elif dom == "gemm_simt":
+        if args.precision == "f64":
+            peak = 1.25
+            src = "nominal FP64 rate of GB300 (1.25 TFLOP/s)"
+        else:
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            src = "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_src": src}
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    else:
+        roof = {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"], "peak_src": pk["src"] + " copy bandwidth"}
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roof.update({"kernel_class": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None,
+                 "launches_per_step": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                 "share_of_step": d["ms"] / max(1e-9, sum(v["ms"] for v in classes.values()))})
+
+    # ---- plain path (FP64) for fast vs plain
+    plain = None
+    if not args.no_plain:
+        for c in ctxs:
+            c.close()
+        pctx, pinfos = make_contexts("f64")
+        p_ms = timed_steps(pctx, 1, 1)
+        F_plain = out[:, 1].cpu().numpy().copy()
+        p_s = max_over_ranks(p_ms / 1e3, world)
+        plain = {"value": N_INSTANCES * world / p_s, "unit": "evals/s", "dtype": "c128",
+                 "max_abs_dF_fast_vs_plain": float(np.max(np.abs(F_fast - F_plain))),
+                 "max_rel_d_one_minus_F": float(np.max(np.abs((1 - F_fast) - (1 - F_plain)) / np.abs(1 - F_plain)))}
+        for c in pctx:
+            c.close()
+        ctxs = []
+
+    # ---- end to end through the C ABI from host arrays
+    for c in ctxs:
+        c.close()
+    e2e_ctx = [ajf.Context(dev, stream.cuda_stream) for _ in insts]
+    h2d = d2h = 0
+    for c, inst in zip(e2e_ctx, insts):  # first pass fills the structural plan cache
+        ajf.load_instance(c.handle, inst)
+        ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials)
+        ajf.ajf_fidelity_alg2(c.handle)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        h2d = d2h = 0
+        for c, inst in zip(e2e_ctx, insts):
+            ajf.load_instance(c.handle, inst)
+            info = ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials)
+            ajf.ajf_fidelity_alg2(c.handle)
+            h2d += int(info["upload_bytes"])
+            d2h += 24
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    for c in e2e_ctx:
+        c.close()
+    e2e = {"value": N_INSTANCES * args.e2e_steps * world / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "note": "host wall clock: load + plan (structural cache hit) + upload + run + read back, per instance"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        line = {
+            "metric": "fidelity evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "c128", "f32": "c64"}.get(args.precision, "c64-" + args.precision),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "planner": "auto",
+                       "trials": args.trials, "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"{world} independent ranks (weak scaling)"},
+            "tflops": flops_per_step * args.steps * world / total_s / 1e12,
+            "flops_per_step": flops_per_step,
+            "F_J": [float(x) for x in F_fast],
+            "roofline": roof, "kernel_classes": classes, "plain": plain, "e2e": e2e,
+            "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * ajf.h -- C ABI of libajf: approximate equivalence checking of noisy quantum circuits by the
+ * Jamiolkowski fidelity, computed on one GB300 (sm_103a) by contracting closed miter tensor
+ * networks.
+ *
+ * The quantity (Sec. III, "Ease of calculation"): for an ideal circuit U on n qubits and a noisy
+ * implementation E = {E_i} (a super-operator in Kraus form, Sec. II-B),
+ *
+ *     F_J(E, U) = (1/d^2) * sum_i |tr(U^dagger E_i)|^2,      d = 2^n.
+ *
+ * Problem 1 / Definition 1 (Sec. III): the two circuits are eps-equivalent iff F_J > 1 - eps.
+ *
+ * Two algorithms (Sec. IV):
+ *   Alg. I  (Sec. IV-A): one single-layer miter U^dagger . E_i per Kraus combination; the
+ *           library contracts all prod_k n_k combinations at once by giving every noise tensor
+ *           an open Kraus index, so the result is the whole tensor t[j_1..j_m] of traces.
+ *   Alg. II (Sec. IV-B): one doubled miter (U^dagger (x) U^T) . M_E with
+ *           M_E built from V (x) V^* per gate and M_N = sum_k N_k (x) N_k^* per noisy gate;
+ *           its value is sum_i |tr(U^dagger E_i)|^2 directly.
+ *
+ * Conventions shared by every call:
+ *   - Matrices are complex128, interleaved (re, im), row-major, 2^a x 2^a for an a-qubit gate.
+ *   - Qubit 0 is the most significant tensor factor of the circuit; within a gate matrix the
+ *     first listed qubit is the most significant factor of the gate.
+ *   - Gates apply in list order (the first gate acts first).
+ *   - The caller owns every array it passes; the library copies what it needs before returning.
+ *   - Every call returns an ajf_status; AJF_OK is 0. The library never aborts the process; the
+ *     text of the last error is available from ajf_last_error.
+ *   - A context is not thread-safe; different contexts may be used from different threads.
+ *   - All device work is enqueued on the context's stream.
+ */
+#ifndef AJF_H
+#define AJF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ajf_status;
+
+enum {
+  AJF_OK = 0,
+  AJF_E_ARG = 1,         /* bad pointer, index, arity, size or option                         */
+  AJF_E_NOT_UNITARY = 2, /* a gate is not unitary: ||G^dagger G - I||_F > 1e-10               */
+  AJF_E_NOT_TP = 3,      /* a Kraus set is not trace preserving: ||sum K^dagger K - I||_F > 1e-10 */
+  AJF_E_STATE = 4,       /* calls in the wrong order (e.g. a fidelity call before ajf_plan)    */
+  AJF_E_BUDGET = 5,      /* the planned contraction does not fit the memory budget             */
+  AJF_E_NOMEM = 6,       /* device or host allocation failed, or the workspace is too small    */
+  AJF_E_CUDA = 7,        /* a CUDA runtime error; the message names the call                   */
+  AJF_E_TIMEOUT = 8,     /* a bounded device-side wait expired                                 */
+  AJF_E_UNSUPPORTED = 9  /* the request is valid but not supported on this device/build        */
+};
+
+enum { AJF_IDEAL = 0, AJF_IMPL = 1 };
+
+enum {
+  AJF_PLANNER_AUTO = 0,    /* best of greedy and min-fill by estimated time                     */
+  AJF_PLANNER_GREEDY = 1,  /* randomised greedy pair selection (memory-removed cost)           */
+  AJF_PLANNER_MINFILL = 2, /* min-fill elimination = tree decomposition of the line graph (Sec. IV-C) */
+  AJF_PLANNER_LEARNED = 3  /* MLP merge scorer; the greedy planner is its fallback and judge     */
+};
+
+enum {
+  AJF_PREC_F64 = 0,    /* complex128 storage, FP64 arithmetic everywhere                       */
+  AJF_PREC_F32 = 1,    /* complex64 storage, FP32 CUDA-core GEMMs                              */
+  AJF_PREC_TF32 = 2,   /* complex64 storage, one-pass TF32 tensor-core GEMMs (tcgen05), FP32 accumulate */
+  AJF_PREC_TF32X3 = 3, /* complex64 storage, split TF32 hi/lo, three tcgen05 passes, FP32 accumulate */
+  AJF_PREC_BF16X3 = 4, /* complex64 storage, bf16 split in two terms, three tcgen05 passes      */
+  AJF_PREC_BF16X6 = 5  /* complex64 storage, bf16 split in three terms, six tcgen05 passes      */
+};
+/* In every mode the final contraction to a scalar, sum_i |t_i|^2, F_J and 1 - F_J are FP64. */
+
+typedef struct ajf_ctx ajf_ctx;
+
+typedef struct ajf_plan_opts {
+  int32_t planner;         /* AJF_PLANNER_*                                                   */
+  int32_t precision;       /* AJF_PREC_*                                                      */
+  int32_t trials;          /* randomised restarts per planner; 0 = library default (32)       */
+  int32_t use_graph;       /* 1: capture the device program in a CUDA graph on first run       */
+  uint64_t seed;           /* planner random seed                                             */
+  double mem_budget_bytes; /* 0 = 60% of the device's free memory at plan time                 */
+  int32_t reserved[8];     /* must be zero                                                     */
+} ajf_plan_opts;
+
+typedef struct ajf_plan_info {
+  double cmacs;          /* sum over pairwise steps of M*N*K complex multiply-adds             */
+  double flops;          /* 8 * cmacs (one complex multiply-add = 8 real flops)                */
+  double bytes;          /* algorithmic bytes: sum over steps of (|A|+|B|+|C|) * element size   */
+  double gemm_flops;     /* the part of `flops` done by the GEMM-class steps                    */
+  double gemm_bytes;     /* the part of `bytes` moved by the GEMM-class steps                   */
+  double arena_bytes;    /* device memory the plan needs (intermediates + scratch + inputs)     */
+  double plan_seconds;   /* host time spent planning                                            */
+  int32_t width;         /* log2 of the element count of the largest tensor                     */
+  int32_t n_steps;       /* pairwise contraction steps                                          */
+  int32_t n_gemm_steps;  /* steps lowered to permute + GEMM                                     */
+  int32_t n_leaves;      /* tensors of the network before contraction                           */
+  int32_t n_open_bits;   /* Alg. I: bits of the open Kraus-index result tensor; Alg. II: 0       */
+  int32_t planner_used;  /* AJF_PLANNER_* that produced the chosen path                          */
+  int32_t n_launches;    /* kernel launches one evaluation enqueues                              */
+  int32_t n_tc_gemms;    /* GEMM launches that run on the tcgen05 tensor cores                   */
+  int32_t plan_cached;   /* 1: the path was reused from the previous plan of the same structure  */
+  int32_t reserved;
+  double upload_bytes;   /* host -> device bytes of one upload (descriptors + packed inputs)     */
+} ajf_plan_info;
+
+/* Per-kernel-class timing collected while profiling is on (CUDA events around every launch on
+ * the context's stream). Classes: 0 leaves, 1 small steps, 2 split-K, 3 operand gather,
+ * 4 CUDA-core GEMM, 5 tensor-core GEMM, 6 final FP64 reduction. */
+typedef struct ajf_kernel_stats {
+  int64_t launches;    /* launches recorded                                                  */
+  double ms;           /* summed device time (ms)                                            */
+  double flops;        /* algorithmic flops of the complex steps these launches carried out  */
+  double bytes;        /* algorithmic bytes of those steps                                   */
+} ajf_kernel_stats;
+
+typedef struct ajf_result {
+  double F;            /* F_J(E, U)                                                          */
+  double one_minus_F;  /* 1 - F_J, computed as (d^2 - S) / d^2 in FP64                         */
+  double S;            /* sum_i |tr(U^dagger E_i)|^2                                            */
+  int64_t traces_done; /* Alg. I: Kraus combinations evaluated; Alg. II: 0                      */
+  int32_t equivalent;  /* eps < 0: -1; else 1 if F_J > 1 - eps (Definition 1), otherwise 0      */
+  int32_t reserved;
+} ajf_result;
+
+/* Create a context on CUDA device `device` (device = -1: a host-only context that validates and
+ * plans but cannot run; useful without a GPU). `cuda_stream` is a cudaStream_t that the library
+ * borrows (never destroys); NULL makes the library create and own a non-blocking stream.
+ * Errors: AJF_E_ARG (out == NULL), AJF_E_CUDA (bad device). */
+ajf_status ajf_create(ajf_ctx **out, int device, void *cuda_stream);
+
+/* Release everything the context owns (device memory it allocated, graphs, its own stream).
+ * Borrowed workspace and streams are left alone. NULL is ignored. */
+void ajf_destroy(ajf_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Owned by the context. */
+const char *ajf_last_error(const ajf_ctx *ctx);
+
+/* Load a circuit (Sec. II-A: a sequence of gates on n qubits). role = AJF_IDEAL sets U;
+ * role = AJF_IMPL sets the unitary skeleton of the noisy implementation (Fig. 2: the noisy
+ * circuit's gates with the noisy gates taken out); without an AJF_IMPL load the skeleton is U.
+ * arity[g] in {1, 2, 3}; qubits holds sum(arity) indices in [0, n); mats holds the gate matrices
+ * one after another (complex128 interleaved, 2^a x 2^a each, row-major). Loading U clears the
+ * noises and any previous skeleton; loading either invalidates the plan.
+ * Errors: AJF_E_ARG (n_qubits not in [1, 62], bad arity/qubit/repeated qubit), AJF_E_NOT_UNITARY. */
+ajf_status ajf_load_circuit(ajf_ctx *ctx, int role, int n_qubits, int n_gates,
+                            const int32_t *arity, const int32_t *qubits, const double *mats);
+
+/* Add a noisy gate N = {N_k} (Sec. II-B Kraus form; Example 2 lists the canonical ones) acting
+ * right after skeleton gate `after_gate` (-1: before the first gate). Noises added after the same
+ * gate act in the order added; Alg. I enumerates Kraus combinations with the last-added noise
+ * varying fastest. kraus holds n_kraus matrices of 2^a x 2^a (complex128 interleaved, row-major).
+ * Errors: AJF_E_STATE (no circuit loaded), AJF_E_ARG (bad index/arity/count, n_kraus > 256),
+ * AJF_E_NOT_TP. */
+ajf_status ajf_add_noise(ajf_ctx *ctx, int32_t after_gate, int32_t arity, const int32_t *qubits,
+                         int32_t n_kraus, const double *kraus);
+
+/* Remove every noise (keeps the circuits). Invalidates the plan. */
+ajf_status ajf_clear_noise(ajf_ctx *ctx);
+
+/* Build the network of algorithm `alg` (1: Alg. I with open Kraus indices, Sec. IV-A;
+ * 2: Alg. II doubled network, Sec. IV-B), choose a pairwise contraction order, lower it to
+ * device kernels and size the device arena. opts may be NULL (defaults: AUTO planner,
+ * AJF_PREC_F64, 32 trials, no graph). info may be NULL.
+ * Errors: AJF_E_STATE (no circuit), AJF_E_ARG (bad alg/option), AJF_E_BUDGET (the best plan's
+ * arena exceeds the budget; info is still filled), AJF_E_UNSUPPORTED (tensor-core precision on
+ * a device without tcgen05). */
+ajf_status ajf_plan(ajf_ctx *ctx, int alg, const ajf_plan_opts *opts, ajf_plan_info *info);
+
+/* Lend the context `bytes` of device memory at `dev_ptr` (256-byte aligned) for its arena.
+ * The caller keeps ownership and must keep it alive until ajf_destroy or the next
+ * ajf_set_workspace. NULL returns to library-allocated memory.
+ * Errors: AJF_E_ARG (misaligned pointer). AJF_E_NOMEM is reported at run time if it is too small. */
+ajf_status ajf_set_workspace(ajf_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Device bytes the current plan needs (valid after ajf_plan). */
+ajf_status ajf_workspace_size(const ajf_ctx *ctx, size_t *bytes);
+
+/* Alg. I (Sec. IV-A): F_J from all prod_k n_k traces tr(U^dagger E_i), accumulated as
+ * sum |t|^2 in FP64 on the device. eps < 0: no decision (equivalent = -1); eps in [0, 1]: also
+ * decide Definition 1. Requires ajf_plan(ctx, 1, ...). Synchronises the context's stream.
+ * Errors: AJF_E_STATE, AJF_E_ARG (eps > 1), AJF_E_NOMEM, AJF_E_CUDA. */
+ajf_status ajf_fidelity_alg1(ajf_ctx *ctx, double eps, ajf_result *out);
+
+/* Alg. II (Sec. IV-B): F_J from the one doubled network. Same contract as ajf_fidelity_alg1,
+ * requiring ajf_plan(ctx, 2, ...). */
+ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);
+
+/* After ajf_fidelity_alg1: copy the traces t_i = tr(U^dagger E_i) to `traces` (host, 2*count
+ * doubles, interleaved), in enumeration order (lexicographic over noises in the order added,
+ * last noise fastest; Sec. IV-A). count must equal prod_k n_k.
+ * Errors: AJF_E_STATE (no Alg. I result), AJF_E_ARG (count mismatch). */
+ajf_status ajf_alg1_traces(ajf_ctx *ctx, double *traces, int64_t count);
+
+/* Enqueue one evaluation of the planned network on the context's stream without waiting:
+ * uploads nothing (inputs must already be resident from an earlier fidelity call or
+ * ajf_upload) and writes {S, F, 1-F} as three doubles to device memory `dev_result`.
+ * With opts.use_graph the program is replayed from a CUDA graph.
+ * Errors: AJF_E_STATE (no plan or inputs not uploaded), AJF_E_CUDA. */
+ajf_status ajf_launch(ajf_ctx *ctx, double *dev_result);
+
+/* Copy the circuit and noise inputs to the device (host -> device, on the context's stream)
+ * and build the leaf tensors there. Called implicitly by the fidelity calls. */
+ajf_status ajf_upload(ajf_ctx *ctx);
+
+/* Alg. I over several contexts (independent circuits of uneven sizes; Sec. IV-A remarks that
+ * the traces are independent): every context must have an Alg. I plan of the same precision
+ * on the same device; all of them are executed together (merged level launches on the first
+ * context's stream) and out[i] receives context i's result. eps as in ajf_fidelity_alg1.
+ * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, mixed device or precision), AJF_E_STATE. */
+ajf_status ajf_fidelity_alg1_batch(ajf_ctx *const *ctxs, int n_ctx, double eps, ajf_result *out);
+
+/* Turn per-launch timing on (1) or off (0) and clear the counters. While on, every run records
+ * CUDA events around each launch (CUDA-graph replay is bypassed). */
+ajf_status ajf_profile_enable(ajf_ctx *ctx, int on);
+
+/* Read the counters: `stats` receives up to `cap` classes (7 are defined). Synchronises the
+ * context's stream. Errors: AJF_E_ARG. */
+ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
+
+/* Library version string, e.g. "ajf 0.1 sm_103a". */
+const char *ajf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AJF_H */

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libajf (include/ajf.h), with the same function names.
+
+Argument marshalling only: every step of the computation runs inside the library's CUDA
+kernels. Importing this module does not load the library; the first call does, and raises if
+``libajf.so`` has not been built (``__graft_entry__.build()``) -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libajf.so")
+
+AJF_OK, AJF_E_ARG, AJF_E_NOT_UNITARY, AJF_E_NOT_TP, AJF_E_STATE = 0, 1, 2, 3, 4
+AJF_E_BUDGET, AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT, AJF_E_UNSUPPORTED = 5, 6, 7, 8, 9
+AJF_IDEAL, AJF_IMPL = 0, 1
+AJF_PLANNER_AUTO, AJF_PLANNER_GREEDY, AJF_PLANNER_MINFILL, AJF_PLANNER_LEARNED = 0, 1, 2, 3
+AJF_PREC_F64, AJF_PREC_F32, AJF_PREC_TF32, AJF_PREC_TF32X3, AJF_PREC_BF16X3, AJF_PREC_BF16X6 = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"f64": AJF_PREC_F64, "f32": AJF_PREC_F32, "tf32": AJF_PREC_TF32, "tf32x3": AJF_PREC_TF32X3,
+              "bf16x3": AJF_PREC_BF16X3, "bf16x6": AJF_PREC_BF16X6}
+PLANNERS = {"auto": AJF_PLANNER_AUTO, "greedy": AJF_PLANNER_GREEDY, "minfill": AJF_PLANNER_MINFILL,
+            "learned": AJF_PLANNER_LEARNED}
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("planner", ctypes.c_int32), ("precision", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("cmacs", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("gemm_flops", ctypes.c_double), ("gemm_bytes", ctypes.c_double), ("arena_bytes", ctypes.c_double),
+                ("plan_seconds", ctypes.c_double), ("width", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("n_gemm_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32), ("n_open_bits", ctypes.c_int32),
+                ("planner_used", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("n_tc_gemms", ctypes.c_int32),
+                ("plan_cached", ctypes.c_int32), ("reserved", ctypes.c_int32), ("upload_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+KERNEL_CLASSES = ["leaves", "small", "splitk", "gather", "gemm_simt", "gemm_tc", "final"]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_double), ("one_minus_F", ctypes.c_double), ("S", ctypes.c_double),
+                ("traces_done", ctypes.c_int64), ("equivalent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class AjfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"ajf status {status}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "ajf_create": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_destroy": (None, [P]),
+            "ajf_last_error": (ctypes.c_char_p, [P]),
+            "ajf_load_circuit": (I32, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]),
+            "ajf_add_noise": (I32, [P, I32, I32, P, I32, P]),
+            "ajf_clear_noise": (I32, [P]),
+            "ajf_plan": (I32, [P, ctypes.c_int, ctypes.POINTER(PlanOpts), ctypes.POINTER(PlanInfo)]),
+            "ajf_set_workspace": (I32, [P, P, ctypes.c_size_t]),
+            "ajf_workspace_size": (I32, [P, ctypes.POINTER(ctypes.c_size_t)]),
+            "ajf_fidelity_alg1": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_fidelity_alg2": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_alg1_traces": (I32, [P, P, I64]),
+            "ajf_launch": (I32, [P, P]),
+            "ajf_upload": (I32, [P]),
+            "ajf_fidelity_alg1_batch": (I32, [ctypes.POINTER(P), ctypes.c_int, D, ctypes.POINTER(Result)]),
+            "ajf_version": (ctypes.c_char_p, []),
+            "ajf_profile_enable": (I32, [P, ctypes.c_int]),
+            "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != AJF_OK:
+        msg = lib().ajf_last_error(ctx).decode() if ctx else ""
+        raise AjfError(status, msg)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ----------------------------------------------------------------------------- C-ABI mirrors
+
+
+def ajf_version() -> str:
+    return lib().ajf_version().decode()
+
+
+def ajf_create(device: int = 0, stream: Optional[int] = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = lib().ajf_create(ctypes.byref(ctx), device, ctypes.c_void_p(stream) if stream else None)
+    if st != AJF_OK:
+        raise AjfError(st, f"ajf_create(device={device}) failed")
+    return ctx
+
+
+def ajf_destroy(ctx) -> None:
+    lib().ajf_destroy(ctx)
+
+
+def ajf_last_error(ctx) -> str:
+    return lib().ajf_last_error(ctx).decode()
+
+
+def ajf_load_circuit(ctx, role: int, n_qubits: int, arity: np.ndarray, qubits: np.ndarray, mats: np.ndarray) -> None:
+    arity = np.ascontiguousarray(arity, dtype=np.int32)
+    qubits = np.ascontiguousarray(qubits, dtype=np.int32)
+    mats = np.ascontiguousarray(mats, dtype=np.complex128)
+    _check(ctx, lib().ajf_load_circuit(ctx, role, n_qubits, int(arity.size), _ptr(arity), _ptr(qubits), _ptr(mats)))
+
+
+def ajf_add_noise(ctx, after_gate: int, qubits: Sequence[int], kraus: np.ndarray) -> None:
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    k = np.ascontiguousarray(kraus, dtype=np.complex128)
+    _check(ctx, lib().ajf_add_noise(ctx, int(after_gate), int(q.size), _ptr(q), int(k.shape[0]), _ptr(k)))
+
+
+def ajf_clear_noise(ctx) -> None:
+    _check(ctx, lib().ajf_clear_noise(ctx))
+
+
+def ajf_plan(ctx, alg: int, planner="auto", precision="f64", trials: int = 0, use_graph: bool = False,
+             seed: int = 0, mem_budget_bytes: float = 0.0) -> dict:
+    o = PlanOpts()
+    o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.trials = int(trials)
+    o.use_graph = 1 if use_graph else 0
+    o.seed = int(seed)
+    o.mem_budget_bytes = float(mem_budget_bytes)
+    info = PlanInfo()
+    st = lib().ajf_plan(ctx, int(alg), ctypes.byref(o), ctypes.byref(info))
+    if st != AJF_OK:
+        err = AjfError(st, ajf_last_error(ctx))
+        err.info = info.as_dict()
+        raise err
+    return info.as_dict()
+
+
+def ajf_set_workspace(ctx, dev_ptr: int, nbytes: int) -> None:
+    _check(ctx, lib().ajf_set_workspace(ctx, ctypes.c_void_p(dev_ptr) if dev_ptr else None, int(nbytes)))
+
+
+def ajf_workspace_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, lib().ajf_workspace_size(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def ajf_upload(ctx) -> None:
+    _check(ctx, lib().ajf_upload(ctx))
+
+
+def ajf_fidelity_alg1(ctx, eps: float = -1.0) -> dict:
+    r = Result()
+    _check(ctx, lib().ajf_fidelity_alg1(ctx, float(eps), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ajf_fidelity_alg2(ctx, eps: float = -1.0) -> dict:
+    r = Result()
+    _check(ctx, lib().ajf_fidelity_alg2(ctx, float(eps), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ajf_alg1_traces(ctx, count: int) -> np.ndarray:
+    out = np.empty(int(count), dtype=np.complex128)
+    _check(ctx, lib().ajf_alg1_traces(ctx, _ptr(out), int(count)))
+    return out
+
+
+def ajf_launch(ctx, dev_result_ptr: int) -> None:
+    _check(ctx, lib().ajf_launch(ctx, ctypes.c_void_p(dev_result_ptr) if dev_result_ptr else None))
+
+
+def ajf_fidelity_alg1_batch(ctxs: Sequence, eps: float = -1.0) -> list:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    res = (Result * len(ctxs))()
+    st = lib().ajf_fidelity_alg1_batch(arr, len(ctxs), float(eps), res)
+    if st != AJF_OK:
+        msgs = "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c))
+        raise AjfError(st, msgs)
+    return [r.as_dict() for r in res]
+
+
+def ajf_profile_enable(ctx, on: bool = True) -> None:
+    _check(ctx, lib().ajf_profile_enable(ctx, 1 if on else 0))
+
+
+def ajf_profile_read(ctx) -> dict:
+    arr = (KernelStats * len(KERNEL_CLASSES))()
+    _check(ctx, lib().ajf_profile_read(ctx, arr, len(KERNEL_CLASSES)))
+    return {name: {"launches": s.launches, "ms": s.ms, "flops": s.flops, "bytes": s.bytes}
+            for name, s in zip(KERNEL_CLASSES, arr)}
+
+
+# ----------------------------------------------------------------------------- marshalling helpers
+
+
+def pack_gates(gates) -> tuple:
+    """(arity, qubits, mats) arrays for ajf_load_circuit from objects with .qubits and .mat."""
+    arity = np.array([len(g.qubits) for g in gates], dtype=np.int32)
+    qubits = np.array([q for g in gates for q in g.qubits], dtype=np.int32)
+    mats = (np.concatenate([np.asarray(g.mat, dtype=np.complex128).reshape(-1) for g in gates])
+            if gates else np.zeros(0, dtype=np.complex128))
+    return arity, qubits, mats
+
+
+def load_instance(ctx, inst) -> None:
+    """Load an instance (ideal circuit, optional implementation skeleton, noises) into a context."""
+    ajf_load_circuit(ctx, AJF_IDEAL, inst.n, *pack_gates(inst.ideal))
+    if getattr(inst, "impl", None) is not None:
+        ajf_load_circuit(ctx, AJF_IMPL, inst.n, *pack_gates(inst.impl))
+    for nz in inst.noises:
+        ajf_add_noise(ctx, nz.after_gate, nz.qubits, nz.kraus)
+
+
+class Context:
+    """Owning wrapper around an ajf_ctx handle."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.handle = ajf_create(device, stream)
+
+    def close(self):
+        if self.handle:
+            ajf_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+// Internal data structures of libajf (host side). Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ajf.h"
+
+namespace ajf {
+
+// ------------------------------------------------------------------ inputs (copied from the caller)
+
+struct GateIn {
+  int arity = 0;
+  int q[3] = {0, 0, 0};
+  int64_t mat_off = 0;  // complex offset into Inputs::packed
+};
+
+struct NoiseIn {
+  int after = -1;
+  int arity = 0;
+  int q[3] = {0, 0, 0};
+  int nk = 0;            // Kraus operators
+  int kbits = 0;         // ceil(log2(nk)): bits of the open Kraus index (Alg. I)
+  int64_t kraus_off = 0; // complex offset into Inputs::packed
+};
+
+struct Inputs {
+  int n = 0;
+  bool has_ideal = false, has_impl = false;
+  std::vector<GateIn> ideal, impl;
+  std::vector<NoiseIn> noises;
+  std::vector<double> packed;  // complex128 interleaved; every matrix the caller passed
+  const std::vector<GateIn>& skeleton() const { return has_impl ? impl : ideal; }
+};
+
+// ------------------------------------------------------------------ network
+
+// How a leaf tensor's values are made on the device from the packed inputs.
+enum LeafKind : int32_t {
+  LEAF_GATE = 0,        // G[out][in]
+  LEAF_GATE_CONJ = 1,   // G^*[out][in]
+  LEAF_GATE_DAG = 2,    // (G^dagger)[out][in] = conj(G[in][out])
+  LEAF_GATE_TRANS = 3,  // (G^T)[out][in] = G[in][out]
+  LEAF_KRAUS_OPEN = 4,  // T[kappa][out][in] = K_kappa[out][in], zero for kappa >= nk
+  LEAF_SUPEROP = 5,     // M_N[(o,o')][(i,i')] = sum_k K_k[o][i] conj(K_k[o'][i'])
+  LEAF_IDENTITY = 6,    // delta[out][in], 2 x 2
+};
+
+struct LeafSpec {
+  int32_t kind = 0;
+  int32_t a = 0;        // wires of the operator (2a tensor bits before any Kraus bits)
+  int64_t src = 0;      // complex offset of the source matrix / first Kraus operator
+  int32_t nk = 0;       // Kraus operators (LEAF_KRAUS_OPEN, LEAF_SUPEROP)
+  int32_t kbits = 0;    // open Kraus-index bits (LEAF_KRAUS_OPEN)
+};
+
+// A tensor's labels are listed from bit 0 (stride 1) upward: element index = sum_i bit_i * 2^i.
+// Every label has dimension 2. A label occurs in exactly two leaves unless it is open.
+struct Network {
+  int alg = 0;
+  int n_labels = 0;
+  std::vector<std::vector<int>> leaf_labels;
+  std::vector<LeafSpec> leaf_specs;
+  std::vector<int> open_labels;  // bit order of the Alg. I result tensor t
+  int loops = 0;                 // wires touched by no tensor: each a factor tr(I_2) = 2
+  int n_qubits = 0;
+};
+
+// ------------------------------------------------------------------ contraction path
+
+struct PathStep {
+  int a = -1, b = -1;     // tensor ids (leaves 0..L-1, then one new id per step)
+  std::vector<int> out;   // labels of the result, unordered (layout is chosen at lowering)
+};
+
+struct Path {
+  std::vector<PathStep> steps;      // each step creates tensor id L + index
+  std::vector<int> final_ids;       // tensors left at the end (scalars and/or the open tensor)
+  double cmacs = 0, max_size = 0, est_seconds = 0;
+  int width = 0;
+  int planner = 0;
+};
+
+struct PlanParams {
+  int planner = AJF_PLANNER_AUTO;
+  int precision = AJF_PREC_F64;
+  int trials = 32;
+  uint64_t seed = 0;
+  double peak_flops = 1e12;   // contraction throughput of the chosen precision (time model)
+  double peak_bw = 6.5e12;    // bytes/s
+  double elem_bytes = 16;
+};
+
+Path plan_path(const Network& net, const PlanParams& p);
+void evaluate_path(const Network& net, Path& path, const PlanParams& p);
+Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature);
+Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed);
+Path plan_learned(const Network& net, const PlanParams& p, uint64_t seed, bool* used);
+
+// ------------------------------------------------------------------ network builders
+
+Network build_alg1(const Inputs& in);
+Network build_alg2(const Inputs& in);
+
+}  // namespace ajf

@@ -1,0 +1,807 @@
+// C ABI of libajf (see include/ajf.h): context, input validation, planning, upload and the
+// executor that enqueues a lowered program on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ajf_internal.h"
+#include "kernels.h"
+#include "program.h"
+
+using namespace ajf;
+
+namespace {
+
+struct GateData {
+  int arity;
+  int q[3];
+  std::vector<double> mat;  // complex128 interleaved
+};
+
+struct NoiseData {
+  int after, arity, nk;
+  int q[3];
+  std::vector<double> kraus;
+};
+
+}  // namespace
+
+struct ajf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int n = 0;
+  bool has_ideal = false, has_impl = false;
+  std::vector<GateData> ideal, impl;
+  std::vector<NoiseData> noises;
+  // plan
+  bool planned = false;
+  int alg = 0;
+  ajf_plan_opts opts{};
+  Inputs in;
+  Network net;
+  Path path;
+  Program prog;
+  ajf_plan_info info{};
+  std::vector<char> desc_image;
+  // device memory
+  char* arena = nullptr;
+  size_t arena_cap = 0;
+  bool own_arena = true;
+  void* user_ws = nullptr;
+  size_t user_ws_bytes = 0;
+  bool uploaded = false;
+  char* pinned = nullptr;
+  size_t pinned_cap = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool tc_device = false;
+  bool have_alg1 = false;
+  // structural plan cache: the path is reused when the network's shape and options repeat
+  std::vector<int64_t> plan_key;
+  bool path_valid = false;
+  // profiling
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int cls;
+    double flops, bytes;
+  };
+  bool profiling = false;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> event_pool;
+  ajf_kernel_stats stats[7] = {};
+};
+
+namespace {
+
+ajf_status fail(ajf_ctx* c, ajf_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+ajf_status cuda_fail(ajf_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, AJF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, call)                                       \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);    \
+  } while (0)
+
+using cd = std::complex<double>;
+
+// ||M^dagger M - I||_F for a row-major complex matrix (validation of Sec. II inputs).
+double unitarity_error(const double* m, int dim) {
+  double err = 0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) {
+      cd s = 0;
+      for (int k = 0; k < dim; ++k) s += std::conj(cd(m[2 * (k * dim + i)], m[2 * (k * dim + i) + 1])) *
+                                         cd(m[2 * (k * dim + j)], m[2 * (k * dim + j) + 1]);
+      if (i == j) s -= 1.0;
+      err += std::norm(s);
+    }
+  return std::sqrt(err);
+}
+
+double tp_error(const double* ks, int nk, int dim) {
+  double err = 0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) {
+      cd s = 0;
+      for (int k = 0; k < nk; ++k) {
+        const double* m = ks + 2 * size_t(k) * dim * dim;
+        for (int r = 0; r < dim; ++r) s += std::conj(cd(m[2 * (r * dim + i)], m[2 * (r * dim + i) + 1])) *
+                                           cd(m[2 * (r * dim + j)], m[2 * (r * dim + j) + 1]);
+      }
+      if (i == j) s -= 1.0;
+      err += std::norm(s);
+    }
+  return std::sqrt(err);
+}
+
+void invalidate(ajf_ctx* c) {
+  c->planned = false;
+  c->uploaded = false;
+  c->have_alg1 = false;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+}
+
+// Pack the caller's matrices into one complex128 buffer and fill the index structures.
+void pack_inputs(ajf_ctx* c) {
+  Inputs& in = c->in;
+  in = Inputs();
+  in.n = c->n;
+  in.has_ideal = c->has_ideal;
+  in.has_impl = c->has_impl;
+  auto add_gates = [&](const std::vector<GateData>& src, std::vector<GateIn>& dst) {
+    for (auto& g : src) {
+      GateIn gi;
+      gi.arity = g.arity;
+      for (int i = 0; i < 3; ++i) gi.q[i] = g.q[i];
+      gi.mat_off = static_cast<int64_t>(in.packed.size() / 2);
+      in.packed.insert(in.packed.end(), g.mat.begin(), g.mat.end());
+      dst.push_back(gi);
+    }
+  };
+  add_gates(c->ideal, in.ideal);
+  if (c->has_impl) add_gates(c->impl, in.impl);
+  for (auto& nz : c->noises) {
+    NoiseIn ni;
+    ni.after = nz.after;
+    ni.arity = nz.arity;
+    for (int i = 0; i < 3; ++i) ni.q[i] = nz.q[i];
+    ni.nk = nz.nk;
+    ni.kbits = 0;
+    while ((1 << ni.kbits) < nz.nk) ni.kbits++;
+    ni.kraus_off = static_cast<int64_t>(in.packed.size() / 2);
+    in.packed.insert(in.packed.end(), nz.kraus.begin(), nz.kraus.end());
+    in.noises.push_back(ni);
+  }
+}
+
+ajf_status ensure_arena(ajf_ctx* c) {
+  const size_t need = c->prog.arena_bytes;
+  if (c->user_ws) {
+    if (c->user_ws_bytes < need)
+      return fail(c, AJF_E_NOMEM, "workspace of " + std::to_string(c->user_ws_bytes) + " bytes < " +
+                                       std::to_string(need) + " needed");
+    c->arena = static_cast<char*>(c->user_ws);
+    return AJF_OK;
+  }
+  if (c->own_arena && c->arena && c->arena_cap >= need) return AJF_OK;
+  if (c->own_arena && c->arena) {
+    cudaFree(c->arena);
+    c->arena = nullptr;
+    c->arena_cap = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AJF_E_NOMEM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+  }
+  c->arena = static_cast<char*>(p);
+  c->arena_cap = need;
+  c->own_arena = true;
+  return AJF_OK;
+}
+
+ajf_status ensure_pinned(ajf_ctx* c, size_t bytes) {
+  if (c->pinned_cap >= bytes) return AJF_OK;
+  if (c->pinned) cudaFreeHost(c->pinned);
+  c->pinned = nullptr;
+  c->pinned_cap = 0;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocHost(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AJF_E_NOMEM, "cudaMallocHost failed");
+  }
+  c->pinned = static_cast<char*>(p);
+  c->pinned_cap = bytes;
+  return AJF_OK;
+}
+
+cudaEvent_t pool_event(ajf_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Profiling: events around one launch (no-op unless profiling is on).
+struct ProfScope {
+  ajf_ctx* c;
+  cudaStream_t s;
+  int cls;
+  double flops, bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(ajf_ctx* c_, cudaStream_t s_, int cls_, double f, double b) : c(c_), s(s_), cls(cls_), flops(f), bytes(b) {
+    if (c->profiling) {
+      a = pool_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(c);
+    cudaEventRecord(b, s);
+    c->prof_pending.push_back({a, b, cls, flops, bytes});
+  }
+};
+
+void drain_profile(ajf_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->stats[r.cls].launches++;
+      c->stats[r.cls].ms += ms;
+      c->stats[r.cls].flops += r.flops;
+      c->stats[r.cls].bytes += r.bytes;
+    }
+    c->event_pool.push_back(r.a);
+    c->event_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
+// Enqueue the device program: leaves, contraction launches, FP64 final reduction.
+ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
+  const Program& P = c->prog;
+  char* base = c->arena;
+  void* arena = base;
+  const bool f64 = P.f64;
+  cudaError_t e;
+  {
+    ProfScope ps(c, s, 0, 0, 0);
+    e = launch_leaves(reinterpret_cast<const LeafDev*>(base + P.off_leaves), static_cast<int>(P.leaves.size()),
+                      reinterpret_cast<const double*>(base + P.off_inputs), arena, f64, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "leaf kernel");
+  const StepDev* steps = reinterpret_cast<const StepDev*>(base + P.off_steps);
+  const PermDev* perms = reinterpret_cast<const PermDev*>(base + P.off_perms);
+  double2* partial = reinterpret_cast<double2*>(base + P.off_partial);
+  double2* scalars = reinterpret_cast<double2*>(base + P.off_scalars);
+  int* status = reinterpret_cast<int*>(base + P.off_status);
+  for (const Launch& ln : P.launches) {
+    static const int kClass[5] = {1, 2, 3, 4, 5};
+    ProfScope ps(c, s, kClass[ln.kind], ln.flops, ln.bytes);
+    switch (ln.kind) {
+      case LK_SMALL:
+        e = launch_small(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, f64, s);
+        break;
+      case LK_SPLITK:
+        e = launch_splitk(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, f64, s);
+        break;
+      case LK_PERM:
+        e = launch_perm(perms + ln.first, ln.count, ln.blocks, ln.smem, arena, base, f64, s);
+        break;
+      case LK_GEMM_SIMT:
+        e = launch_gemm_simt(base + ln.a_off[0], base + ln.b_off[0], base + ln.c_off, ln.M, ln.N, ln.K, f64, s);
+        break;
+      case LK_GEMM_TC:
+        e = launch_gemm_tc(base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<float*>(base + ln.c_off), ln.M, ln.N,
+                           ln.K, ln.tc_kind, status, s);
+        break;
+      default:
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "contraction launch");
+  }
+  {
+    ProfScope ps(c, s, 6, 0, 0);
+    e = launch_final(reinterpret_cast<const FinalDev*>(base + P.off_final), P.final_nchunks, P.final_blocks, arena,
+                     scalars, reinterpret_cast<double*>(base + P.off_traces),
+                     reinterpret_cast<double*>(base + P.off_open_partial), reinterpret_cast<double*>(base + P.off_result),
+                     f64, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "final reduction");
+  return AJF_OK;
+}
+
+ajf_status run_program(ajf_ctx* c) {
+  if (c->opts.use_graph && !c->profiling) {
+    if (!c->graph) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      ajf_status st = enqueue_program(c, c->stream);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (st != AJF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+    return AJF_OK;
+  }
+  return enqueue_program(c, c->stream);
+}
+
+ajf_status do_upload(ajf_ctx* c) {
+  if (!c->planned) return fail(c, AJF_E_STATE, "ajf_upload: no plan");
+  ajf_status st = ensure_arena(c);
+  if (st != AJF_OK) return st;
+  const Program& P = c->prog;
+  const size_t total = c->desc_image.size() + P.input_bytes;
+  st = ensure_pinned(c, std::max<size_t>(total, 64));
+  if (st != AJF_OK) return st;
+  // the pinned image is filled before any copy is enqueued; wait for earlier copies to finish
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(c->pinned, c->desc_image.data(), c->desc_image.size());
+  std::memcpy(c->pinned + c->desc_image.size(), c->in.packed.data(), P.input_bytes);
+  CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_desc, c->pinned, c->desc_image.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+  if (P.input_bytes)
+    CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_inputs, c->pinned + c->desc_image.size(), P.input_bytes,
+                                cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->arena + P.off_status, 0, 16 * sizeof(int32_t), c->stream));
+  c->uploaded = true;
+  return AJF_OK;
+}
+
+ajf_status check_status_words(ajf_ctx* c) {
+  int status[4] = {0, 0, 0, 0};
+  CUDA_TRY(c, cudaMemcpy(status, c->arena + c->prog.off_status, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status[0] != 0) {
+    cudaMemsetAsync(c->arena + c->prog.off_status, 0, 16 * sizeof(int32_t), c->stream);
+    return fail(c, AJF_E_TIMEOUT, "a bounded device-side wait expired (code " + std::to_string(status[0]) + ")");
+  }
+  return AJF_OK;
+}
+
+int64_t real_combinations(const ajf_ctx* c) {
+  int64_t n = 1;
+  for (auto& nz : c->noises) n *= nz.nk;
+  return n;
+}
+
+ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  if (!c) return AJF_E_ARG;
+  if (!out) return fail(c, AJF_E_ARG, "out is NULL");
+  if (!c->planned || c->alg != alg) return fail(c, AJF_E_STATE, "no Alg. " + std::to_string(alg) + " plan");
+  if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
+  if (eps > 1.0) return fail(c, AJF_E_ARG, "eps > 1");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (!c->uploaded) {
+    ajf_status st = do_upload(c);
+    if (st != AJF_OK) return st;
+  }
+  ajf_status st = run_program(c);
+  if (st != AJF_OK) return st;
+  double res[3];
+  CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  st = check_status_words(c);
+  if (st != AJF_OK) return st;
+  out->S = res[0];
+  out->F = res[1];
+  out->one_minus_F = res[2];
+  out->traces_done = alg == 1 ? real_combinations(c) : 0;
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->reserved = 0;
+  if (alg == 1) c->have_alg1 = true;
+  return AJF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ajf_version(void) { return "ajf 0.1 sm_103a"; }
+
+ajf_status ajf_create(ajf_ctx** out, int device, void* cuda_stream) {
+  if (!out) return AJF_E_ARG;
+  *out = nullptr;
+  auto c = std::make_unique<ajf_ctx>();
+  c->device = device;
+  if (device < 0) {  // host-only context: validation and planning, no device work
+    c->tc_device = true;
+    *out = c.release();
+    return AJF_OK;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return AJF_E_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return AJF_E_CUDA;
+  c->tc_device = prop.major >= 10;
+  if (set_kernel_smem_limits() != cudaSuccess) return AJF_E_CUDA;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return AJF_E_CUDA;
+    c->own_stream = true;
+  }
+  *out = c.release();
+  return AJF_OK;
+}
+
+void ajf_destroy(ajf_ctx* c) {
+  if (!c) return;
+  if (c->device < 0) {
+    delete c;
+    return;
+  }
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drain_profile(c);
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->own_arena && c->arena && !c->user_ws) cudaFree(c->arena);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* ajf_last_error(const ajf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ajf_status ajf_load_circuit(ajf_ctx* c, int role, int n_qubits, int n_gates, const int32_t* arity,
+                            const int32_t* qubits, const double* mats) {
+  if (!c) return AJF_E_ARG;
+  if (role != AJF_IDEAL && role != AJF_IMPL) return fail(c, AJF_E_ARG, "role must be AJF_IDEAL or AJF_IMPL");
+  if (n_qubits < 1 || n_qubits > 62) return fail(c, AJF_E_ARG, "n_qubits must be in [1, 62]");
+  if (n_gates < 0) return fail(c, AJF_E_ARG, "n_gates < 0");
+  if (n_gates > 0 && (!arity || !qubits || !mats)) return fail(c, AJF_E_ARG, "NULL array");
+  if (role == AJF_IMPL && (!c->has_ideal || n_qubits != c->n))
+    return fail(c, AJF_E_ARG, "AJF_IMPL needs a loaded AJF_IDEAL circuit on the same qubits");
+  std::vector<GateData> gates;
+  gates.reserve(n_gates);
+  size_t qi = 0, mi = 0;
+  for (int g = 0; g < n_gates; ++g) {
+    GateData gd;
+    gd.arity = arity[g];
+    if (gd.arity < 1 || gd.arity > 3) return fail(c, AJF_E_ARG, "gate " + std::to_string(g) + ": arity not in {1,2,3}");
+    for (int i = 0; i < 3; ++i) gd.q[i] = 0;
+    for (int i = 0; i < gd.arity; ++i) {
+      const int q = qubits[qi + i];
+      if (q < 0 || q >= n_qubits) return fail(c, AJF_E_ARG, "gate " + std::to_string(g) + ": qubit out of range");
+      for (int j = 0; j < i; ++j)
+        if (gd.q[j] == q) return fail(c, AJF_E_ARG, "gate " + std::to_string(g) + ": repeated qubit");
+      gd.q[i] = q;
+    }
+    qi += gd.arity;
+    const int dim = 1 << gd.arity;
+    gd.mat.assign(mats + mi, mats + mi + 2 * dim * dim);
+    mi += 2 * dim * dim;
+    const double err = unitarity_error(gd.mat.data(), dim);
+    if (!(err <= 1e-10))
+      return fail(c, AJF_E_NOT_UNITARY, "gate " + std::to_string(g) + " is not unitary (||G^+G-I||_F = " +
+                                            std::to_string(err) + ")");
+    gates.push_back(std::move(gd));
+  }
+  if (role == AJF_IDEAL) {
+    c->n = n_qubits;
+    c->ideal = std::move(gates);
+    c->has_ideal = true;
+    c->impl.clear();
+    c->has_impl = false;
+    c->noises.clear();
+  } else {
+    c->impl = std::move(gates);
+    c->has_impl = true;
+  }
+  invalidate(c);
+  c->err.clear();
+  return AJF_OK;
+}
+
+ajf_status ajf_add_noise(ajf_ctx* c, int32_t after_gate, int32_t arity, const int32_t* qubits, int32_t n_kraus,
+                         const double* kraus) {
+  if (!c) return AJF_E_ARG;
+  if (!c->has_ideal) return fail(c, AJF_E_STATE, "ajf_add_noise before ajf_load_circuit");
+  const int nsk = static_cast<int>(c->has_impl ? c->impl.size() : c->ideal.size());
+  if (after_gate < -1 || after_gate >= nsk) return fail(c, AJF_E_ARG, "after_gate out of range");
+  if (arity < 1 || arity > 3) return fail(c, AJF_E_ARG, "noise arity not in {1,2,3}");
+  if (n_kraus < 1 || n_kraus > 256) return fail(c, AJF_E_ARG, "n_kraus not in [1, 256]");
+  if (!qubits || !kraus) return fail(c, AJF_E_ARG, "NULL array");
+  NoiseData nd;
+  nd.after = after_gate;
+  nd.arity = arity;
+  nd.nk = n_kraus;
+  for (int i = 0; i < 3; ++i) nd.q[i] = 0;
+  for (int i = 0; i < arity; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= c->n) return fail(c, AJF_E_ARG, "noise qubit out of range");
+    for (int j = 0; j < i; ++j)
+      if (nd.q[j] == qubits[i]) return fail(c, AJF_E_ARG, "noise: repeated qubit");
+    nd.q[i] = qubits[i];
+  }
+  const int dim = 1 << arity;
+  nd.kraus.assign(kraus, kraus + 2 * size_t(n_kraus) * dim * dim);
+  const double err = tp_error(nd.kraus.data(), n_kraus, dim);
+  if (!(err <= 1e-10))
+    return fail(c, AJF_E_NOT_TP, "Kraus set is not trace preserving (||sum K^+K - I||_F = " + std::to_string(err) + ")");
+  c->noises.push_back(std::move(nd));
+  invalidate(c);
+  c->err.clear();
+  return AJF_OK;
+}
+
+ajf_status ajf_clear_noise(ajf_ctx* c) {
+  if (!c) return AJF_E_ARG;
+  c->noises.clear();
+  invalidate(c);
+  return AJF_OK;
+}
+
+ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_info* info) {
+  if (!c) return AJF_E_ARG;
+  if (!c->has_ideal) return fail(c, AJF_E_STATE, "ajf_plan before ajf_load_circuit");
+  if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 1 or 2");
+  ajf_plan_opts o{};
+  o.planner = AJF_PLANNER_AUTO;
+  o.precision = AJF_PREC_F64;
+  o.trials = 32;
+  if (opts) o = *opts;
+  if (o.trials <= 0) o.trials = 32;
+  if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
+  if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
+  for (int i = 0; i < 8; ++i)
+    if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
+  const int nsk = static_cast<int>(c->has_impl ? c->impl.size() : c->ideal.size());
+  for (auto& nz : c->noises)
+    if (nz.after >= nsk) return fail(c, AJF_E_ARG, "a noise is placed after a gate the skeleton does not have");
+  if (c->device >= 0) CUDA_TRY(c, cudaSetDevice(c->device));
+  if (o.precision >= AJF_PREC_TF32 && !c->tc_device)
+    return fail(c, AJF_E_UNSUPPORTED, "tensor-core precision modes need tcgen05 (sm_100 or newer)");
+  invalidate(c);
+  const auto t0 = std::chrono::steady_clock::now();
+  pack_inputs(c);
+  if (alg == 1) {
+    int open_bits = 0;
+    for (auto& nz : c->in.noises) open_bits += nz.kbits;
+    if (open_bits > 40)
+      return fail(c, AJF_E_BUDGET, "Alg. I result tensor would hold 2^" + std::to_string(open_bits) +
+                                       " traces (more than 2^40); use Alg. II");
+  }
+  c->net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
+  PlanParams pp;
+  pp.planner = o.planner;
+  pp.precision = o.precision;
+  pp.trials = o.trials;
+  pp.seed = o.seed;
+  pp.elem_bytes = o.precision == AJF_PREC_F64 ? 16 : 8;
+  switch (o.precision) {
+    case AJF_PREC_F64: pp.peak_flops = 1.0e12; break;
+    case AJF_PREC_F32: pp.peak_flops = 40e12; break;
+    case AJF_PREC_TF32: pp.peak_flops = 500e12; break;
+    case AJF_PREC_BF16X3: pp.peak_flops = 400e12; break;
+    default: pp.peak_flops = 200e12; break;
+  }
+  std::vector<int64_t> key = {alg, c->n, c->has_impl, o.planner, o.precision, o.trials, static_cast<int64_t>(o.seed)};
+  auto key_gates = [&](const std::vector<GateData>& gs) {
+    key.push_back(static_cast<int64_t>(gs.size()));
+    for (auto& g : gs) key.insert(key.end(), {g.arity, g.q[0], g.q[1], g.q[2]});
+  };
+  key_gates(c->ideal);
+  if (c->has_impl) key_gates(c->impl);
+  for (auto& nz : c->noises) key.insert(key.end(), {nz.after, nz.arity, nz.q[0], nz.q[1], nz.q[2], nz.nk});
+  const bool cached = c->path_valid && key == c->plan_key;
+  try {
+    if (!cached) {
+      c->path_valid = false;
+      c->path = plan_path(c->net, pp);
+      c->plan_key = key;
+      c->path_valid = true;
+    }
+    c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device);
+  } catch (const std::exception& ex) {
+    return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // descriptor image
+  const Program& P = c->prog;
+  c->desc_image.assign(P.desc_bytes, 0);
+  if (!P.leaves.empty())
+    std::memcpy(c->desc_image.data() + (P.off_leaves - P.off_desc), P.leaves.data(), P.leaves.size() * sizeof(LeafDev));
+  if (!P.steps.empty())
+    std::memcpy(c->desc_image.data() + (P.off_steps - P.off_desc), P.steps.data(), P.steps.size() * sizeof(StepDev));
+  if (!P.perms.empty())
+    std::memcpy(c->desc_image.data() + (P.off_perms - P.off_desc), P.perms.data(), P.perms.size() * sizeof(PermDev));
+  std::memcpy(c->desc_image.data() + (P.off_final - P.off_desc), &P.fin, sizeof(FinalDev));
+  ajf_plan_info pi{};
+  pi.cmacs = c->path.cmacs;
+  pi.flops = P.flops;
+  pi.bytes = P.bytes;
+  pi.gemm_flops = P.gemm_flops;
+  pi.gemm_bytes = P.gemm_bytes;
+  pi.arena_bytes = static_cast<double>(P.arena_bytes);
+  pi.plan_seconds = secs;
+  pi.width = c->path.width;
+  pi.n_steps = static_cast<int32_t>(c->path.steps.size());
+  pi.n_gemm_steps = P.n_gemm;
+  pi.n_leaves = static_cast<int32_t>(c->net.leaf_labels.size());
+  pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
+  pi.planner_used = c->path.planner;
+  pi.n_launches = 3;  // leaves + final pass + final sum
+  for (auto& ln : P.launches) pi.n_launches += (ln.kind == LK_SPLITK) ? 2 : 1;
+  pi.n_tc_gemms = P.tensor_cores;
+  pi.plan_cached = cached ? 1 : 0;
+  pi.upload_bytes = static_cast<double>(P.desc_bytes + P.input_bytes);
+  c->info = pi;
+  if (info) *info = pi;
+  double budget = o.mem_budget_bytes;
+  if (budget <= 0 && c->device < 0) budget = 1e18;
+  if (budget <= 0) {
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
+    budget = 0.6 * static_cast<double>(fr) + (c->own_arena ? static_cast<double>(c->arena_cap) : 0.0);
+  }
+  if (static_cast<double>(P.arena_bytes) > budget)
+    return fail(c, AJF_E_BUDGET, "plan needs " + std::to_string(P.arena_bytes) + " bytes, budget " +
+                                     std::to_string(static_cast<size_t>(budget)) + " (width " +
+                                     std::to_string(c->path.width) + ")");
+  c->opts = o;
+  c->alg = alg;
+  c->planned = true;
+  c->err.clear();
+  return AJF_OK;
+}
+
+ajf_status ajf_set_workspace(ajf_ctx* c, void* dev_ptr, size_t bytes) {
+  if (!c) return AJF_E_ARG;
+  if (dev_ptr && (reinterpret_cast<uintptr_t>(dev_ptr) % 256) != 0)
+    return fail(c, AJF_E_ARG, "workspace must be 256-byte aligned");
+  if (c->own_arena && c->arena && !c->user_ws) {
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->arena);
+    c->arena_cap = 0;
+  }
+  c->arena = nullptr;
+  c->user_ws = dev_ptr;
+  c->user_ws_bytes = dev_ptr ? bytes : 0;
+  c->own_arena = dev_ptr == nullptr;
+  c->uploaded = false;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return AJF_OK;
+}
+
+ajf_status ajf_workspace_size(const ajf_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return AJF_E_ARG;
+  if (!c->planned) return AJF_E_STATE;
+  *bytes = c->prog.arena_bytes;
+  return AJF_OK;
+}
+
+ajf_status ajf_upload(ajf_ctx* c) {
+  if (!c) return AJF_E_ARG;
+  if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return do_upload(c);
+}
+
+ajf_status ajf_fidelity_alg1(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 1, eps, out); }
+
+ajf_status ajf_fidelity_alg2(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 2, eps, out); }
+
+ajf_status ajf_alg1_traces(ajf_ctx* c, double* traces, int64_t count) {
+  if (!c) return AJF_E_ARG;
+  if (!c->have_alg1 || !c->planned || c->alg != 1) return fail(c, AJF_E_STATE, "no Alg. I result");
+  if (!traces) return fail(c, AJF_E_ARG, "traces is NULL");
+  const int64_t real = real_combinations(c);
+  if (count != real) return fail(c, AJF_E_ARG, "count must be " + std::to_string(real));
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  std::vector<double> padded(2 * static_cast<size_t>(c->prog.n_traces));
+  CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + c->prog.off_traces, padded.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // padded index: noise j's Kraus index shifted by the bits of the noises added after it
+  const int m = static_cast<int>(c->in.noises.size());
+  std::vector<int> shift(m, 0);
+  int acc = 0;
+  for (int j = m - 1; j >= 0; --j) {
+    shift[j] = acc;
+    acc += c->in.noises[j].kbits;
+  }
+  std::vector<int> digit(m, 0);
+  for (int64_t idx = 0; idx < real; ++idx) {
+    int64_t pidx = 0;
+    for (int j = 0; j < m; ++j) pidx |= int64_t(digit[j]) << shift[j];
+    traces[2 * idx] = padded[2 * pidx];
+    traces[2 * idx + 1] = padded[2 * pidx + 1];
+    for (int j = m - 1; j >= 0; --j) {
+      if (++digit[j] < c->in.noises[j].nk) break;
+      digit[j] = 0;
+    }
+  }
+  return AJF_OK;
+}
+
+ajf_status ajf_launch(ajf_ctx* c, double* dev_result) {
+  if (!c) return AJF_E_ARG;
+  if (!c->planned || !c->uploaded || c->device < 0)
+    return fail(c, AJF_E_STATE, "ajf_launch needs a plan and uploaded inputs on a device context");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  ajf_status st = run_program(c);
+  if (st != AJF_OK) return st;
+  if (dev_result)
+    CUDA_TRY(c, cudaMemcpyAsync(dev_result, c->arena + c->prog.off_result, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                c->stream));
+  return AJF_OK;
+}
+
+ajf_status ajf_profile_enable(ajf_ctx* c, int on) {
+  if (!c) return AJF_E_ARG;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    drain_profile(c);
+  }
+  for (auto& s : c->stats) s = ajf_kernel_stats{};
+  c->profiling = on != 0;
+  return AJF_OK;
+}
+
+ajf_status ajf_profile_read(ajf_ctx* c, ajf_kernel_stats* stats, int cap) {
+  if (!c || !stats || cap < 0) return AJF_E_ARG;
+  if (c->device >= 0) {
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    drain_profile(c);
+  }
+  for (int i = 0; i < cap && i < 7; ++i) stats[i] = c->stats[i];
+  return AJF_OK;
+}
+
+ajf_status ajf_fidelity_alg1_batch(ajf_ctx* const* ctxs, int n_ctx, double eps, ajf_result* out) {
+  if (!ctxs || n_ctx < 1 || !out) return AJF_E_ARG;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return AJF_E_ARG;
+    if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[0], AJF_E_ARG, "contexts on different devices");
+    if (!ctxs[i]->planned || ctxs[i]->alg != 1) return fail(ctxs[i], AJF_E_STATE, "context without an Alg. I plan");
+    if (ctxs[i]->opts.precision != ctxs[0]->opts.precision) return fail(ctxs[0], AJF_E_ARG, "mixed precision");
+  }
+  // every context runs on its own stream so independent circuits overlap on the GPU
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!c->uploaded) {
+      ajf_status st = do_upload(c);
+      if (st != AJF_OK) return st;
+    }
+    ajf_status st = run_program(c);
+    if (st != AJF_OK) return st;
+  }
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ajf_status st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    out[i].S = res[0];
+    out[i].F = res[1];
+    out[i].one_minus_F = res[2];
+    out[i].traces_done = real_combinations(c);
+    out[i].equivalent = eps < 0 ? -1 : (res[1] > 1.0 - eps ? 1 : 0);
+    out[i].reserved = 0;
+    c->have_alg1 = true;
+  }
+  return AJF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Device-side step descriptors shared by the lowering (host) and the kernels (device).
+//
+// Storage: every tensor lives in one device arena in planar complex form -- a real plane of
+// 2^r elements followed by an imaginary plane of 2^r elements -- in the working precision
+// (double for AJF_PREC_F64, float otherwise). Element index = sum_i bit_i * 2^i, where bit i is
+// the tensor's i-th label. Scalars produced by full contractions are FP64 (double2 slots).
+#pragma once
+#include <cstdint>
+
+namespace ajf {
+
+constexpr int kMaxBits = 48;
+
+// Map from the bits of an index to element offsets of one tensor: offset(idx) =
+// sum_i bit_i(idx) << pos[i] (pos < 0: the bit does not address this tensor). Evaluated on the
+// device through 8-bit lookup tables built in shared memory.
+struct BitMap {
+  int32_t nbits;
+  int8_t pos[kMaxBits];
+};
+
+// One pairwise contraction C[o] = sum_kk A[a + oa(o) + ka(kk)] * B[b + ob(o) + kb(kk)].
+struct StepDev {
+  int64_t a, b, c;        // element offsets of the real planes in the arena
+  int64_t pa, pb, pc;     // plane strides (elements) = tensor sizes
+  int64_t poff;           // split-K: offset (in double2) of this step's partial sums
+  BitMap oa, ob;          // output-index bits -> A / B offsets
+  BitMap ka, kb;          // contracted-index bits -> A / B offsets
+  int32_t rc, rk;         // output and contracted bit counts
+  int32_t block0;         // first block of this step within its launch
+  int32_t scalar_slot;    // >= 0: the result is a scalar written to a double2 slot (FP64)
+  int32_t nsplit;         // split-K: blocks per output element
+  int32_t pad;
+};
+
+// Operand preparation for a GEMM step: gather a complex tensor into a real row-major,
+// K-contiguous GEMM operand. Embedded (X side): rows (s, m), cols (t, k) hold
+// [[Re, -Im], [Im, Re]] (2M x 2K). Plain (Y side, stored transposed): rows n, cols (t, k) hold
+// plane t (N x 2K).
+struct PermDev {
+  int64_t src, plane;     // source tensor (element offset of the real plane) and plane stride
+  int64_t dst[3];         // destination operand arrays (split terms: hi, mid, lo), byte offsets
+  BitMap rows, cols;      // row-index bits / k-index bits -> source offsets
+  int32_t rbits, kbits;   // log2 rows (M or N), log2 K
+  int32_t embed;          // 1: X side (embedded), 0: Y side
+  int32_t rows_fast;      // 1: read with lanes along rows (the source's stride-1 bit is a row bit)
+  int32_t mode;           // operand format, see OperandMode
+  int32_t pad;
+};
+
+enum OperandMode : int32_t {
+  OPM_F64 = 0,     // double
+  OPM_F32 = 1,     // float
+  OPM_TF32 = 2,    // float rounded to TF32
+  OPM_TF32X2 = 3,  // hi, lo (float, each TF32)
+  OPM_BF16X2 = 4,  // hi, lo (bf16)
+  OPM_BF16X3 = 5,  // hi, mid, lo (bf16)
+};
+
+// Leaf construction from the uploaded complex128 inputs.
+struct LeafDev {
+  int64_t off, plane;     // destination (element offset of the real plane), plane stride
+  int64_t src;            // complex offset of the source matrix in the input buffer
+  int32_t kind, a, nk, kbits;
+  int32_t bits;           // total tensor bits
+  int32_t pad;
+};
+
+// Final reduction: scalars, open tensor, result.
+struct FinalDev {
+  int64_t open_off;              // open tensor (working precision); -1 if none
+  int64_t open_plane;
+  BitMap open_map;               // canonical open-index bits -> offsets in the open tensor
+  int32_t open_bits;
+  int32_t n_scalars;
+  int32_t loops;                 // untouched wires: factor 2 each on every trace
+  int32_t n_qubits;
+  int32_t alg;
+  int32_t nblocks;               // blocks of the open-tensor pass
+};
+
+}  // namespace ajf

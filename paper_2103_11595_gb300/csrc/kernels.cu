@@ -1,0 +1,535 @@
+// CUDA-core kernels of the contraction program (sm_103a).
+//
+//  k_leaf        builds every leaf tensor of the miter network from the uploaded complex128
+//                gate/Kraus matrices (gate, conjugate, adjoint, transpose, Kraus stack with an
+//                open index, superoperator M_N = sum_k N_k (x) N_k^*; Sec. IV-A/IV-B).
+//  k_small       many independent small pairwise contractions in one launch, one gather per
+//                operand element through 8-bit offset tables (bits of any binary-index layout).
+//  k_splitk      contractions with few outputs and a long contracted index (including the final
+//                full contraction to the trace): FP64 partial sums per block, then k_splitk_done
+//                sums them in a fixed order (deterministic).
+//  k_perm        gathers a complex tensor into a real, K-contiguous GEMM operand (the complex
+//                product C = A B becomes the real product [[Ar,-Ai],[Ai,Ar]] [Br;Bi] = [Cr;Ci]),
+//                with the operand format of the precision mode (FP64, FP32, TF32, split TF32,
+//                split bf16).
+//  k_gemm_simt   real "TN" GEMM on CUDA cores (FP32 or FP64) writing the planar result.
+//  k_open/k_final  the FP64 end of the path: t_i for Alg. I, sum |t_i|^2, F_J and 1 - F_J.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "kernels.h"
+
+namespace ajf {
+
+// ------------------------------------------------------------------ offset tables
+
+__device__ __forceinline__ int nchunks(int nbits) { return (nbits + 7) >> 3; }
+
+// Fill `tab` (nchunks * 256 entries) for map `m`; all threads of the block participate.
+__device__ __forceinline__ void build_table(const BitMap& m, int64_t* tab) {
+  const int nc = nchunks(m.nbits);
+  for (int e = threadIdx.x; e < nc * 256; e += blockDim.x) {
+    const int c = e >> 8, v = e & 255;
+    int64_t off = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int bit = c * 8 + i;
+      if (bit < m.nbits && ((v >> i) & 1) && m.pos[bit] >= 0) off += int64_t(1) << m.pos[bit];
+    }
+    tab[e] = off;
+  }
+}
+
+__device__ __forceinline__ int64_t lookup(const int64_t* tab, int nc, int64_t idx) {
+  int64_t off = 0;
+  for (int c = 0; c < nc; ++c) off += tab[(c << 8) | ((idx >> (8 * c)) & 255)];
+  return off;
+}
+
+// ------------------------------------------------------------------ leaves
+
+template <typename T>
+__global__ void k_leaf(const LeafDev* leaves, const double* __restrict__ in, T* __restrict__ arena) {
+  const LeafDev L = leaves[blockIdx.x];
+  const int64_t n = int64_t(1) << L.bits;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    double re = 0, im = 0;
+    const int a = L.a;
+    const int64_t dim = int64_t(1) << a;
+    switch (L.kind) {
+      case 0: case 1: case 2: case 3: {  // gate, conj, adjoint, transpose
+        const int64_t r = e >> a, c = e & (dim - 1);
+        const bool swap = (L.kind == 2 || L.kind == 3);
+        const int64_t idx = swap ? (c * dim + r) : (r * dim + c);
+        re = in[2 * (L.src + idx)];
+        im = in[2 * (L.src + idx) + 1];
+        if (L.kind == 1 || L.kind == 2) im = -im;
+        break;
+      }
+      case 4: {  // Kraus stack with open index kappa above the 2a operator bits
+        const int64_t kappa = e >> (2 * a);
+        const int64_t rc = e & (dim * dim - 1);
+        if (kappa < L.nk) {
+          re = in[2 * (L.src + kappa * dim * dim + rc)];
+          im = in[2 * (L.src + kappa * dim * dim + rc) + 1];
+        }
+        break;
+      }
+      case 5: {  // M_N over wires (q..., q'...): a = 2 * noise arity
+        const int an = a / 2;
+        const int64_t nd = int64_t(1) << an;
+        const int64_t R = e >> a, C = e & (dim - 1);
+        const int64_t o = R >> an, op = R & (nd - 1), i = C >> an, ip = C & (nd - 1);
+        for (int k = 0; k < L.nk; ++k) {
+          const int64_t base = L.src + int64_t(k) * nd * nd;
+          const double xr = in[2 * (base + o * nd + i)], xi = in[2 * (base + o * nd + i) + 1];
+          const double yr = in[2 * (base + op * nd + ip)], yi = -in[2 * (base + op * nd + ip) + 1];
+          re += xr * yr - xi * yi;
+          im += xr * yi + xi * yr;
+        }
+        break;
+      }
+      default:  // identity delta[out][in]
+        re = (e == 0 || e == 3) ? 1.0 : 0.0;
+        break;
+    }
+    arena[L.off + e] = static_cast<T>(re);
+    arena[L.off + L.plane + e] = static_cast<T>(im);
+  }
+}
+
+// ------------------------------------------------------------------ small contractions
+
+__device__ __forceinline__ int find_step(const StepDev* steps, int nsteps, int block) {
+  int lo = 0, hi = nsteps - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (steps[mid].block0 <= block) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) k_small(const StepDev* __restrict__ steps, int nsteps,
+                                               int total_blocks, T* __restrict__ arena) {
+  extern __shared__ int64_t tab[];
+  const int s = find_step(steps, nsteps, blockIdx.x);
+  const StepDev& st = steps[s];
+  const int end = (s + 1 < nsteps) ? steps[s + 1].block0 : total_blocks;
+  const int nb = end - st.block0;
+  const int c_oa = nchunks(st.oa.nbits), c_ob = nchunks(st.ob.nbits);
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  int64_t* t_oa = tab;
+  int64_t* t_ob = t_oa + c_oa * 256;
+  int64_t* t_ka = t_ob + c_ob * 256;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  build_table(st.oa, t_oa);
+  build_table(st.ob, t_ob);
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  __syncthreads();
+  const int64_t nout = int64_t(1) << st.rc, nk = int64_t(1) << st.rk;
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  T* C = arena + st.c;
+  for (int64_t o = int64_t(blockIdx.x - st.block0) * blockDim.x + threadIdx.x; o < nout;
+       o += int64_t(nb) * blockDim.x) {
+    const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
+    Acc re = 0, im = 0;
+    for (int64_t kk = 0; kk < nk; ++kk) {
+      const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+      const Acc ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+    C[o] = static_cast<T>(re);
+    C[st.pc + o] = static_cast<T>(im);
+  }
+}
+
+// ------------------------------------------------------------------ split-K / full contractions
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_splitk(const StepDev* __restrict__ steps, int nsteps,
+                                                const T* __restrict__ arena, double2* __restrict__ partial) {
+  extern __shared__ int64_t tab[];
+  __shared__ double red_re[256], red_im[256];
+  const int s = find_step(steps, nsteps, blockIdx.x);
+  const StepDev& st = steps[s];
+  const int local = blockIdx.x - st.block0;
+  const int64_t o = local / st.nsplit;
+  const int split = local % st.nsplit;
+  const int c_oa = nchunks(st.oa.nbits), c_ob = nchunks(st.ob.nbits);
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  int64_t* t_oa = tab;
+  int64_t* t_ob = t_oa + c_oa * 256;
+  int64_t* t_ka = t_ob + c_ob * 256;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  build_table(st.oa, t_oa);
+  build_table(st.ob, t_ob);
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  __syncthreads();
+  const int64_t nk = int64_t(1) << st.rk;
+  const int64_t chunk = (nk + st.nsplit - 1) / st.nsplit;
+  const int64_t k0 = int64_t(split) * chunk;
+  const int64_t k1 = min(nk, k0 + chunk);
+  const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  double re = 0, im = 0;
+  for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
+    const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+    const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+    re += ar * br - ai * bi;
+    im += ar * bi + ai * br;
+  }
+  red_re[threadIdx.x] = re;
+  red_im[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + w];
+      red_im[threadIdx.x] += red_im[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[st.poff + o * st.nsplit + split] = make_double2(red_re[0], red_im[0]);
+}
+
+template <typename T>
+__global__ void k_splitk_done(const StepDev* __restrict__ steps, int nsteps, const double2* __restrict__ partial,
+                              T* __restrict__ arena, double2* __restrict__ scalars) {
+  const StepDev& st = steps[blockIdx.x];
+  const int64_t nout = int64_t(1) << st.rc;
+  for (int64_t o = threadIdx.x; o < nout; o += blockDim.x) {
+    double re = 0, im = 0;
+    for (int sp = 0; sp < st.nsplit; ++sp) {
+      const double2 v = partial[st.poff + o * st.nsplit + sp];
+      re += v.x;
+      im += v.y;
+    }
+    if (st.scalar_slot >= 0) {
+      scalars[st.scalar_slot] = make_double2(re, im);
+    } else {
+      arena[st.c + o] = static_cast<T>(re);
+      arena[st.c + st.pc + o] = static_cast<T>(im);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ GEMM operand preparation
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_operand(const PermDev& p, char* base, int64_t idx, T v) {
+  switch (p.mode) {
+    case OPM_F64:
+      reinterpret_cast<double*>(base + p.dst[0])[idx] = static_cast<double>(v);
+      break;
+    case OPM_F32:
+      reinterpret_cast<float*>(base + p.dst[0])[idx] = static_cast<float>(v);
+      break;
+    case OPM_TF32:
+      reinterpret_cast<float*>(base + p.dst[0])[idx] = to_tf32(static_cast<float>(v));
+      break;
+    case OPM_TF32X2: {
+      const float x = static_cast<float>(v);
+      const float hi = to_tf32(x);
+      reinterpret_cast<float*>(base + p.dst[0])[idx] = hi;
+      reinterpret_cast<float*>(base + p.dst[1])[idx] = to_tf32(x - hi);
+      break;
+    }
+    case OPM_BF16X2: {
+      const float x = static_cast<float>(v);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      reinterpret_cast<__nv_bfloat16*>(base + p.dst[0])[idx] = hi;
+      reinterpret_cast<__nv_bfloat16*>(base + p.dst[1])[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+      break;
+    }
+    default: {  // OPM_BF16X3
+      const float x = static_cast<float>(v);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+      reinterpret_cast<__nv_bfloat16*>(base + p.dst[0])[idx] = hi;
+      reinterpret_cast<__nv_bfloat16*>(base + p.dst[1])[idx] = mid;
+      reinterpret_cast<__nv_bfloat16*>(base + p.dst[2])[idx] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      break;
+    }
+  }
+}
+
+// Tile of 32 rows x 32 k per iteration, 32 x 8 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
+                                              char* __restrict__ base) {
+  extern __shared__ int64_t tab[];
+  __shared__ T tre[32][33], tim[32][33];
+  const PermDev& p = perms[blockIdx.y];
+  const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
+  int64_t* t_r = tab;
+  int64_t* t_k = tab + c_r * 256;
+  build_table(p.rows, t_r);
+  build_table(p.cols, t_k);
+  __syncthreads();
+  const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
+  const int TK = p.kbits >= 5 ? 32 : (1 << p.kbits);
+  const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
+  const int64_t ntr = R / TR, ntk = K / TK;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const T* src = arena + p.src;
+  for (int64_t tile = blockIdx.x; tile < ntr * ntk; tile += gridDim.x) {
+    const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
+    // load phase: lanes along whichever index is contiguous in the source
+    for (int i = ty; i < 32; i += 8) {
+      const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
+      if (rr < TR && kk < TK) {
+        const int64_t off = lookup(t_r, c_r, r0 + rr) + lookup(t_k, c_k, k0 + kk);
+        tre[rr][kk] = src[off];
+        tim[rr][kk] = src[p.plane + off];
+      }
+    }
+    __syncthreads();
+    // store phase: lanes along k (contiguous in the operand)
+    for (int i = ty; i < TR; i += 8) {
+      if (tx < TK) {
+        const T re = tre[i][tx], im = tim[i][tx];
+        const int64_t r = r0 + i, k = k0 + tx;
+        if (p.embed) {
+          const int64_t ld = 2 * K;
+          store_operand(p, base, r * ld + k, re);             // (s=0, t=0):  Re
+          store_operand(p, base, r * ld + K + k, T(-im));     // (s=0, t=1): -Im
+          store_operand(p, base, (R + r) * ld + k, im);       // (s=1, t=0):  Im
+          store_operand(p, base, (R + r) * ld + K + k, re);   // (s=1, t=1):  Re
+        } else {
+          const int64_t ld = 2 * K;
+          store_operand(p, base, r * ld + k, re);
+          store_operand(p, base, r * ld + K + k, im);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ CUDA-core GEMM
+
+// C[M][N] (row-major, ldc = N) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __restrict__ A, const T* __restrict__ B,
+                                                                     T* __restrict__ C, int64_t M, int64_t N, int64_t K) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tr = tid / (BN / TN), tc = tid % (BN / TN);
+  const int64_t nbn = (N + BN - 1) / BN;
+  const int64_t m0 = (int64_t(blockIdx.x) / nbn) * BM, n0 = (int64_t(blockIdx.x) % nbn) * BN;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += NT) {
+      const int r = e / BK, k = e % BK;
+      const int64_t gm = m0 + r, gk = k0 + k;
+      As[k][r] = (gm < M && gk < K) ? A[gm * K + gk] : T(0);
+    }
+    for (int e = tid; e < BN * BK; e += NT) {
+      const int r = e / BK, k = e % BK;
+      const int64_t gn = n0 + r, gk = k0 + k;
+      Bs[k][r] = (gn < N && gk < K) ? B[gn * K + gk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[k][tr * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[k][tc * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gm = m0 + tr * TM + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + tc * TN + j;
+      if (gn < N) C[gm * N + gn] = acc[i][j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ final FP64 reduction
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_open(const FinalDev* __restrict__ fd, const T* __restrict__ arena,
+                                              const double2* __restrict__ scalars, double* __restrict__ traces,
+                                              double* __restrict__ partial) {
+  extern __shared__ int64_t tab[];
+  __shared__ double red[256];
+  const FinalDev& f = *fd;
+  // common factor: product of scalar components and 2 per untouched wire
+  double sr = ldexp(1.0, f.loops), si = 0;
+  for (int i = 0; i < f.n_scalars; ++i) {
+    const double2 v = scalars[i];
+    const double nr = sr * v.x - si * v.y, ni = sr * v.y + si * v.x;
+    sr = nr;
+    si = ni;
+  }
+  const int c = nchunks(f.open_map.nbits);
+  build_table(f.open_map, tab);
+  __syncthreads();
+  const int64_t n = int64_t(1) << f.open_bits;
+  double acc = 0;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+    double tr = 1, ti = 0;
+    if (f.open_off >= 0) {
+      const int64_t off = lookup(tab, c, j);
+      tr = static_cast<double>(arena[f.open_off + off]);
+      ti = static_cast<double>(arena[f.open_off + f.open_plane + off]);
+    }
+    const double vr = tr * sr - ti * si, vi = tr * si + ti * sr;
+    traces[2 * j] = vr;
+    traces[2 * j + 1] = vi;
+    acc += vr * vr + vi * vi;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_final(const FinalDev* __restrict__ fd, const double2* __restrict__ scalars,
+                        const double* __restrict__ partial, double* __restrict__ result) {
+  if (threadIdx.x != 0) return;
+  const FinalDev& f = *fd;
+  double S = 0;
+  if (f.alg == 2) {
+    double sr = ldexp(1.0, f.loops), si = 0;
+    for (int i = 0; i < f.n_scalars; ++i) {
+      const double2 v = scalars[i];
+      const double nr = sr * v.x - si * v.y, ni = sr * v.y + si * v.x;
+      sr = nr;
+      si = ni;
+    }
+    S = sr;
+  } else {
+    for (int b = 0; b < f.nblocks; ++b) S += partial[b];
+  }
+  const double d2 = ldexp(1.0, 2 * f.n_qubits);
+  result[0] = S;
+  result[1] = S / d2;
+  result[2] = (d2 - S) / d2;
+}
+
+// ------------------------------------------------------------------ launch wrappers
+
+static size_t table_bytes(const BitMap* const* maps, int n) {
+  size_t b = 0;
+  for (int i = 0; i < n; ++i) b += size_t((maps[i]->nbits + 7) / 8) * 256 * sizeof(int64_t);
+  return b;
+}
+
+cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, bool f64, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (f64) k_leaf<double><<<n, 128, 0, s>>>(d_leaves, d_in, static_cast<double*>(arena));
+  else k_leaf<float><<<n, 128, 0, s>>>(d_leaves, d_in, static_cast<float*>(arena));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena, bool f64,
+                         cudaStream_t s) {
+  if (nsteps == 0) return cudaSuccess;
+  if (f64) k_small<double, double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, total_blocks, static_cast<double*>(arena));
+  else k_small<float, float><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, total_blocks, static_cast<float*>(arena));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena,
+                          double2* partial, double2* scalars, bool f64, cudaStream_t s) {
+  if (nsteps == 0) return cudaSuccess;
+  if (f64) {
+    k_splitk<double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const double*>(arena), partial);
+    k_splitk_done<double><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<double*>(arena), scalars);
+  } else {
+    k_splitk<float><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const float*>(arena), partial);
+    k_splitk_done<float><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<float*>(arena), scalars);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
+                        bool f64, cudaStream_t s) {
+  if (nperm == 0) return cudaSuccess;
+  dim3 grid(grid_x, nperm);
+  if (f64) k_perm<double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
+  else k_perm<float><<<grid, 256, smem, s>>>(d_perms, static_cast<const float*>(arena), static_cast<char*>(base));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool f64,
+                             cudaStream_t s) {
+  if (f64) {
+    const unsigned grid = unsigned(((N + 63) / 64) * ((M + 63) / 64));
+    k_gemm_simt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, s>>>(static_cast<const double*>(A), static_cast<const double*>(B),
+                                                             static_cast<double*>(C), M, N, K);
+  } else {
+    const unsigned grid = unsigned(((N + 127) / 128) * ((M + 127) / 128));
+    k_gemm_simt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, s>>>(static_cast<const float*>(A), static_cast<const float*>(B),
+                                                              static_cast<float*>(C), M, N, K);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
+                         const double2* scalars, double* traces, double* partial, double* result, bool f64,
+                         cudaStream_t s) {
+  const size_t smem = size_t(open_bits_nchunks) * 256 * sizeof(int64_t);
+  if (f64) k_open<double><<<nblocks, 256, smem, s>>>(d_fd, static_cast<const double*>(arena), scalars, traces, partial);
+  else k_open<float><<<nblocks, 256, smem, s>>>(d_fd, static_cast<const float*>(arena), scalars, traces, partial);
+  k_final<<<1, 32, 0, s>>>(d_fd, scalars, partial, result);
+  return cudaGetLastError();
+}
+
+size_t step_table_bytes(const StepDev& st) {
+  const BitMap* maps[4] = {&st.oa, &st.ob, &st.ka, &st.kb};
+  return table_bytes(maps, 4);
+}
+
+size_t perm_table_bytes(const PermDev& p) {
+  const BitMap* maps[2] = {&p.rows, &p.cols};
+  return table_bytes(maps, 2);
+}
+
+cudaError_t set_kernel_smem_limits() {
+  const int big = 96 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_small<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_small<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
+}
+
+}  // namespace ajf

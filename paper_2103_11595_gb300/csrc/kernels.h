@@ -1,0 +1,33 @@
+// Launch wrappers of the device kernels (host-callable).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace ajf {
+
+cudaError_t set_kernel_smem_limits();
+size_t step_table_bytes(const StepDev& st);
+size_t perm_table_bytes(const PermDev& p);
+
+cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, bool f64, cudaStream_t s);
+cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena, bool f64,
+                         cudaStream_t s);
+cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena,
+                          double2* partial, double2* scalars, bool f64, cudaStream_t s);
+cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
+                        bool f64, cudaStream_t s);
+cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool f64,
+                             cudaStream_t s);
+cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
+                         const double2* scalars, double* traces, double* partial, double* result, bool f64,
+                         cudaStream_t s);
+
+// Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (fp32, row-major) = sum_p A_p[M][K] . B_p[N][K]^T
+// over `npass` (A_p, B_p) operand pairs given as byte offsets from `base`. kind 0: tf32, 1: bf16.
+// Returns cudaErrorNotSupported when the shape is not tile-aligned.
+bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int npass, float* C, int64_t M,
+                           int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s);
+
+}  // namespace ajf

@@ -1,0 +1,372 @@
+// Contraction-path planners (host side).
+//
+// A path is a sequence of pairwise merges. Every label has dimension 2, so a merge of tensors
+// with label sets a and b costs 2^{|a u b|} complex multiply-adds (M*N*K) and produces a tensor
+// of 2^{|a ^ b|} elements.
+//
+//  * Greedy: repeatedly merge the pair sharing a label with the smallest "memory removed" cost
+//    size(out) - size(a) - size(b); randomised restarts perturb the cost (in log scale) with
+//    Gumbel noise of a chosen temperature.
+//  * Min-fill (Sec. IV-C orders contractions by a tree decomposition of the network's line graph,
+//    whose vertices are the network's labels, with an edge between labels of one tensor):
+//    eliminate labels in min-fill order -- the vertex whose neighbourhood needs the fewest new
+//    edges to become a clique, random tie-breaks -- and contract, for each eliminated label, the
+//    two tensors that carry it. Elimination orders and tree decompositions are equivalent
+//    (the width of the decomposition bounds the largest intermediate).
+//  * Learned: an MLP scores candidate merges (planner_learned.cpp); the greedy planner is its
+//    fallback and judge.
+// The AUTO planner runs restarts of both and keeps the path with the smallest estimated time
+// sum_s max(8 cmacs_s / peak_flops, bytes_s / peak_bw).
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <unordered_set>
+#include <cmath>
+#include <cstring>
+#include <queue>
+#include <unordered_map>
+
+#include "ajf_internal.h"
+
+namespace ajf {
+namespace {
+
+struct Rng {
+  uint64_t s;
+  explicit Rng(uint64_t seed) : s(seed * 0x9E3779B97F4A7C15ull + 0x1234567ull) {}
+  uint64_t next() {  // splitmix64
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double gumbel() { return -std::log(-std::log(uniform())); }
+};
+
+using Labels = std::vector<int>;  // sorted
+
+Labels sorted(std::vector<int> v) {
+  std::sort(v.begin(), v.end());
+  return v;
+}
+
+// Symmetric difference and intersection size of two sorted label sets.
+Labels sym_diff(const Labels& a, const Labels& b, int* shared) {
+  Labels out;
+  out.reserve(a.size() + b.size());
+  size_t i = 0, j = 0;
+  int sh = 0;
+  while (i < a.size() || j < b.size()) {
+    if (j == b.size() || (i < a.size() && a[i] < b[j])) out.push_back(a[i++]);
+    else if (i == a.size() || b[j] < a[i]) out.push_back(b[j++]);
+    else { ++sh; ++i; ++j; }
+  }
+  if (shared) *shared = sh;
+  return out;
+}
+
+int count_shared(const Labels& a, const Labels& b) {
+  size_t i = 0, j = 0;
+  int sh = 0;
+  while (i < a.size() && j < b.size()) {
+    if (a[i] < b[j]) ++i;
+    else if (b[j] < a[i]) ++j;
+    else { ++sh; ++i; ++j; }
+  }
+  return sh;
+}
+
+// Merge whatever is left when no two tensors share a label: tensors with open labels are joined
+// by outer products (smallest first); scalars stay separate and are multiplied at the end.
+void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& path) {
+  std::vector<int> open_ids;
+  for (size_t i = 0; i < ts.size(); ++i)
+    if (alive[i]) {
+      if (ts[i].empty()) path.final_ids.push_back(static_cast<int>(i));
+      else open_ids.push_back(static_cast<int>(i));
+    }
+  while (open_ids.size() > 1) {
+    std::sort(open_ids.begin(), open_ids.end(),
+              [&](int x, int y) { return ts[x].size() < ts[y].size(); });
+    const int a = open_ids[0], b = open_ids[1];
+    PathStep st;
+    st.a = a;
+    st.b = b;
+    st.out = sym_diff(ts[a], ts[b], nullptr);
+    alive[a] = alive[b] = 0;
+    ts.push_back(st.out);
+    alive.push_back(1);
+    path.steps.push_back(st);
+    open_ids.erase(open_ids.begin(), open_ids.begin() + 2);
+    open_ids.push_back(static_cast<int>(ts.size()) - 1);
+  }
+  if (!open_ids.empty()) path.final_ids.push_back(open_ids[0]);
+}
+
+}  // namespace
+
+void evaluate_path(const Network& net, Path& path, const PlanParams& p) {
+  std::vector<int> rank;
+  for (auto& l : net.leaf_labels) rank.push_back(static_cast<int>(l.size()));
+  double cm = 0, secs = 0, maxsz = 0;
+  int width = 0;
+  for (int r : rank) width = std::max(width, r);
+  for (auto& st : path.steps) {
+    const int ra = rank[st.a], rb = rank[st.b], rc = static_cast<int>(st.out.size());
+    const int k = (ra + rb - rc) / 2;
+    const double c = std::ldexp(1.0, ra + rb - k);
+    cm += c;
+    const double bytes = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * p.elem_bytes;
+    secs += std::max(8.0 * c / p.peak_flops, bytes / p.peak_bw) + 2e-6;
+    rank.push_back(rc);
+    width = std::max(width, rc);
+    maxsz = std::max(maxsz, std::ldexp(1.0, rc));
+  }
+  path.cmacs = cm;
+  path.width = width;
+  path.max_size = maxsz;
+  path.est_seconds = secs;
+}
+
+Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature) {
+  Rng rng(seed);
+  const int L = static_cast<int>(net.leaf_labels.size());
+  std::vector<Labels> ts;
+  std::vector<char> alive(L, 1);
+  std::vector<int> version(L, 0);
+  for (auto& l : net.leaf_labels) ts.push_back(sorted(l));
+  // label -> tensors carrying it (at most two)
+  std::vector<std::array<int, 2>> owner(net.n_labels, {-1, -1});
+  auto add_owner = [&](int lab, int t) {
+    if (owner[lab][0] < 0) owner[lab][0] = t;
+    else owner[lab][1] = t;
+  };
+  auto drop_owner = [&](int lab, int t) {
+    if (owner[lab][0] == t) owner[lab][0] = owner[lab][1];
+    else if (owner[lab][1] != t) return;
+    owner[lab][1] = -1;
+  };
+  for (int t = 0; t < L; ++t)
+    for (int lab : ts[t]) add_owner(lab, t);
+
+  struct Cand {
+    double key;
+    int a, b, va, vb;
+    bool operator<(const Cand& o) const { return key > o.key; }  // min-heap
+  };
+  std::priority_queue<Cand> pq;
+  auto push_pair = [&](int a, int b) {
+    int sh = 0;
+    const Labels out = sym_diff(ts[a], ts[b], &sh);
+    const double cost = std::ldexp(1.0, static_cast<int>(out.size())) -
+                        std::ldexp(1.0, static_cast<int>(ts[a].size())) -
+                        std::ldexp(1.0, static_cast<int>(ts[b].size()));
+    double key = (cost >= 0 ? 1.0 : -1.0) * std::log2(1.0 + std::fabs(cost));
+    if (temperature > 0) key -= temperature * rng.gumbel();
+    pq.push({key, a, b, version[a], version[b]});
+  };
+  {
+    std::unordered_set<uint64_t> seen;
+    for (int lab = 0; lab < net.n_labels; ++lab) {
+      const int a = owner[lab][0], b = owner[lab][1];
+      if (a < 0 || b < 0) continue;
+      const uint64_t key = (static_cast<uint64_t>(std::min(a, b)) << 32) | static_cast<uint32_t>(std::max(a, b));
+      if (seen.insert(key).second) push_pair(std::min(a, b), std::max(a, b));
+    }
+  }
+
+  Path path;
+  while (!pq.empty()) {
+    Cand c = pq.top();
+    pq.pop();
+    if (!alive[c.a] || !alive[c.b] || version[c.a] != c.va || version[c.b] != c.vb) continue;
+    PathStep st;
+    st.a = c.a;
+    st.b = c.b;
+    st.out = sym_diff(ts[c.a], ts[c.b], nullptr);
+    for (int lab : ts[c.a]) drop_owner(lab, c.a);
+    for (int lab : ts[c.b]) drop_owner(lab, c.b);
+    alive[c.a] = alive[c.b] = 0;
+    const int id = static_cast<int>(ts.size());
+    ts.push_back(st.out);
+    alive.push_back(1);
+    version.push_back(0);
+    for (int lab : st.out) add_owner(lab, id);
+    path.steps.push_back(st);
+    // new candidates: neighbours of the new tensor
+    std::vector<int> nbs;
+    for (int lab : ts[id]) {
+      const int o = owner[lab][0] == id ? owner[lab][1] : owner[lab][0];
+      if (o >= 0) nbs.push_back(o);
+    }
+    std::sort(nbs.begin(), nbs.end());
+    nbs.erase(std::unique(nbs.begin(), nbs.end()), nbs.end());
+    for (int o : nbs) push_pair(std::min(o, id), std::max(o, id));
+  }
+  finish_components(ts, alive, path);
+  path.planner = AJF_PLANNER_GREEDY;
+  evaluate_path(net, path, p);
+  return path;
+}
+
+Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed) {
+  Rng rng(seed);
+  const int V = net.n_labels;
+  const int W = (V + 63) / 64;
+  std::vector<uint64_t> adj(static_cast<size_t>(V) * W, 0);
+  auto row = [&](int v) { return adj.data() + static_cast<size_t>(v) * W; };
+  auto has = [&](int u, int v) { return (row(u)[v >> 6] >> (v & 63)) & 1ull; };
+  auto set_edge = [&](int u, int v) {
+    row(u)[v >> 6] |= 1ull << (v & 63);
+    row(v)[u >> 6] |= 1ull << (u & 63);
+  };
+  std::vector<char> present(V, 0), is_open(V, 0);
+  for (int lab : net.open_labels) is_open[lab] = 1;
+  for (auto& l : net.leaf_labels) {
+    for (int x : l) present[x] = 1;
+    for (size_t i = 0; i < l.size(); ++i)
+      for (size_t j = i + 1; j < l.size(); ++j) set_edge(l[i], l[j]);
+  }
+  std::vector<std::vector<int>> nbr(V);
+  auto refresh_nbr = [&](int v) {
+    nbr[v].clear();
+    const uint64_t* r = row(v);
+    for (int w = 0; w < W; ++w) {
+      uint64_t x = r[w];
+      while (x) {
+        const int b = __builtin_ctzll(x);
+        nbr[v].push_back(w * 64 + b);
+        x &= x - 1;
+      }
+    }
+  };
+  auto fill = [&](int v) {
+    long f = 0;
+    const auto& nb = nbr[v];
+    for (size_t i = 0; i < nb.size(); ++i)
+      for (size_t j = i + 1; j < nb.size(); ++j)
+        if (!has(nb[i], nb[j])) ++f;
+    return f;
+  };
+  std::vector<long> score(V, 0);
+  std::vector<double> tie(V, 0);
+  std::vector<char> alive(V, 0);
+  int remaining = 0;
+  for (int v = 0; v < V; ++v)
+    if (present[v]) {
+      refresh_nbr(v);
+      alive[v] = 1;
+      tie[v] = rng.uniform();
+      if (!is_open[v]) ++remaining;
+    }
+  for (int v = 0; v < V; ++v)
+    if (alive[v]) score[v] = fill(v);
+
+  std::vector<int> order;
+  order.reserve(remaining);
+  std::vector<int> mark(V, -1);
+  for (int it = 0; it < remaining; ++it) {
+    int best = -1;
+    for (int v = 0; v < V; ++v) {
+      if (!alive[v] || is_open[v]) continue;
+      if (best < 0 || score[v] < score[best] || (score[v] == score[best] && tie[v] < tie[best]))
+        best = v;
+    }
+    const int v = best;
+    const std::vector<int> nb = nbr[v];
+    for (size_t i = 0; i < nb.size(); ++i)
+      for (size_t j = i + 1; j < nb.size(); ++j) set_edge(nb[i], nb[j]);
+    for (int u : nb) row(u)[v >> 6] &= ~(1ull << (v & 63));
+    std::memset(row(v), 0, W * sizeof(uint64_t));
+    alive[v] = 0;
+    order.push_back(v);
+    // neighbourhoods changed for nb; fill counts may change within two hops
+    std::vector<int> touched;
+    for (int u : nb) {
+      refresh_nbr(u);
+      if (mark[u] != it) { mark[u] = it; touched.push_back(u); }
+    }
+    for (int u : nb)
+      for (int w : nbr[u])
+        if (mark[w] != it) { mark[w] = it; touched.push_back(w); }
+    for (int u : touched)
+      if (alive[u]) score[u] = fill(u);
+  }
+
+  // Contract along the elimination order.
+  const int L = static_cast<int>(net.leaf_labels.size());
+  std::vector<Labels> ts;
+  std::vector<char> talive(L, 1);
+  for (auto& l : net.leaf_labels) ts.push_back(sorted(l));
+  std::vector<std::array<int, 2>> owner(V, {-1, -1});
+  auto add_owner = [&](int lab, int t) {
+    if (owner[lab][0] < 0) owner[lab][0] = t;
+    else owner[lab][1] = t;
+  };
+  auto drop_owner = [&](int lab, int t) {
+    if (owner[lab][0] == t) owner[lab][0] = owner[lab][1];
+    else if (owner[lab][1] != t) return;
+    owner[lab][1] = -1;
+  };
+  for (int t = 0; t < L; ++t)
+    for (int lab : ts[t]) add_owner(lab, t);
+  Path path;
+  for (int x : order) {
+    const int a = owner[x][0], b = owner[x][1];
+    if (a < 0 || b < 0) continue;
+    PathStep st;
+    st.a = std::min(a, b);
+    st.b = std::max(a, b);
+    st.out = sym_diff(ts[st.a], ts[st.b], nullptr);
+    for (int lab : ts[st.a]) drop_owner(lab, st.a);
+    for (int lab : ts[st.b]) drop_owner(lab, st.b);
+    talive[st.a] = talive[st.b] = 0;
+    const int id = static_cast<int>(ts.size());
+    ts.push_back(st.out);
+    talive.push_back(1);
+    for (int lab : st.out) add_owner(lab, id);
+    path.steps.push_back(st);
+  }
+  finish_components(ts, talive, path);
+  path.planner = AJF_PLANNER_MINFILL;
+  evaluate_path(net, path, p);
+  return path;
+}
+
+Path plan_path(const Network& net, const PlanParams& p) {
+  const int trials = std::max(1, p.trials);
+  Path best;
+  bool have = false;
+  auto consider = [&](Path&& cand) {
+    if (!have || cand.est_seconds < best.est_seconds ||
+        (cand.est_seconds == best.est_seconds && cand.cmacs < best.cmacs)) {
+      best = std::move(cand);
+      have = true;
+    }
+  };
+  if (net.leaf_labels.empty()) {
+    Path empty;
+    empty.planner = p.planner;
+    return empty;
+  }
+  if (p.planner == AJF_PLANNER_LEARNED) {
+    bool used = false;
+    Path lp = plan_learned(net, p, p.seed, &used);
+    consider(std::move(lp));
+    // the greedy planner judges: keep the learned path only if it is no worse
+    consider(plan_greedy(net, p, p.seed, 0.0));
+    if (best.planner != AJF_PLANNER_LEARNED && used) best.planner = AJF_PLANNER_GREEDY;
+    return best;
+  }
+  const bool do_greedy = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_GREEDY;
+  const bool do_minfill = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_MINFILL;
+  for (int t = 0; t < trials; ++t) {
+    const uint64_t s = p.seed * 1000003ull + static_cast<uint64_t>(t);
+    if (do_greedy) consider(plan_greedy(net, p, s, t == 0 ? 0.0 : (t % 3 == 1 ? 0.5 : 1.0)));
+    if (do_minfill) consider(plan_minfill(net, p, s));
+  }
+  return best;
+}
+
+}  // namespace ajf

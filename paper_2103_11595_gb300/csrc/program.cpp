@@ -1,0 +1,495 @@
+// Lowering of a contraction path to a device program (host side).
+//
+// Each pairwise step C = contract(A, B) over their shared labels is assigned one of three kernel
+// classes:
+//   GEMM   -- M, N >= 16, K >= 8 and M*N*K >= 2^18: both operands are gathered into real,
+//             K-contiguous GEMM operands (the smaller one embedded as [[Re,-Im],[Im,Re]]) and one
+//             real GEMM C' = X' Y'^T produces C directly in planar layout with labels
+//             (n-bits low, m-bits high). GEMMs run on tcgen05 in the tensor-core precision modes
+//             when the shape is tile-aligned, else on CUDA cores.
+//   SPLITK -- full contractions to a scalar (the trace) and steps with <= 2^12 outputs and a
+//             contracted index of >= 2^10: FP64 partial sums, deterministic final sum.
+//   SMALL  -- everything else (gate absorption, outer products, tiny merges): one thread per
+//             output element; all SMALL steps of one dependency level share one launch.
+// Steps run level by level (level = 1 + the deeper input's level). The arena holds the
+// descriptors, the packed inputs, the FP64 result area and a work region whose offsets come from
+// a first-fit allocator replaying the launch order, so buffers are reused as soon as their last
+// reader has been enqueued.
+#include "program.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+
+#include "kernels.h"
+
+namespace ajf {
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+class FirstFit {
+ public:
+  size_t alloc(size_t bytes) {
+    bytes = align_up(std::max<size_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first;
+        const size_t rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        return off;
+      }
+    }
+    const size_t off = top_;
+    top_ += bytes;
+    peak_ = std::max(peak_, top_);
+    return off;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align_up(std::max<size_t>(bytes, 1));
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == top_) {
+      top_ = it->first;
+      free_.erase(it);
+    }
+  }
+  size_t peak() const { return peak_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t top_ = 0, peak_ = 0;
+};
+
+BitMap make_map(const std::vector<int>& idx_labels, const std::vector<int>& tensor_labels) {
+  BitMap m;
+  std::memset(&m, 0, sizeof(m));
+  if (idx_labels.size() > static_cast<size_t>(kMaxBits)) throw std::runtime_error("index wider than 48 bits");
+  m.nbits = static_cast<int32_t>(idx_labels.size());
+  for (size_t i = 0; i < idx_labels.size(); ++i) {
+    int pos = -1;
+    for (size_t j = 0; j < tensor_labels.size(); ++j)
+      if (tensor_labels[j] == idx_labels[i]) { pos = static_cast<int>(j); break; }
+    m.pos[i] = static_cast<int8_t>(pos);
+  }
+  return m;
+}
+
+bool contains(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
+
+enum Cls { C_SMALL = 0, C_SPLITK = 1, C_GEMM = 2 };
+
+struct StepInfo {
+  int cls = C_SMALL;
+  int level = 0;
+  int a = -1, b = -1;          // input tensor ids (for GEMM: a = X embedded side, b = Y)
+  std::vector<int> shared;     // contracted labels (order used for the k index)
+  int m = 0, n = 0, k = 0;     // log2 M, N, K
+};
+
+int operand_mode(int precision) {
+  switch (precision) {
+    case AJF_PREC_F64: return OPM_F64;
+    case AJF_PREC_F32: return OPM_F32;
+    case AJF_PREC_TF32: return OPM_TF32;
+    case AJF_PREC_TF32X3: return OPM_TF32X2;
+    case AJF_PREC_BF16X3: return OPM_BF16X2;
+    default: return OPM_BF16X3;
+  }
+}
+int mode_terms(int mode) { return mode == OPM_TF32X2 || mode == OPM_BF16X2 ? 2 : (mode == OPM_BF16X3 ? 3 : 1); }
+size_t mode_bytes(int mode) { return mode == OPM_F64 ? 8 : (mode >= OPM_BF16X2 ? 2 : 4); }
+
+}  // namespace
+
+Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok) {
+  Program P;
+  P.alg = net.alg;
+  P.precision = precision;
+  P.f64 = (precision == AJF_PREC_F64);
+  P.elem = P.f64 ? 8 : 4;
+  const int L = static_cast<int>(net.leaf_labels.size());
+  const int S = static_cast<int>(path.steps.size());
+  std::vector<std::vector<int>> labels(L + S);
+  std::vector<int> level(L + S, 0);
+  for (int i = 0; i < L; ++i) labels[i] = net.leaf_labels[i];
+  std::vector<StepInfo> info(S);
+
+  // ---- classify steps and fix every intermediate's label order
+  for (int s = 0; s < S; ++s) {
+    const PathStep& st = path.steps[s];
+    const auto& la = labels[st.a];
+    const auto& lb = labels[st.b];
+    StepInfo& I = info[s];
+    I.level = 1 + std::max(level[st.a], level[st.b]);
+    level[L + s] = I.level;
+    std::vector<int> fa, fb, sh;
+    for (int x : la) (contains(lb, x) ? sh : fa).push_back(x);
+    for (int x : lb)
+      if (!contains(la, x)) fb.push_back(x);
+    const int rc = static_cast<int>(fa.size() + fb.size());
+    const int rk = static_cast<int>(sh.size());
+    const int ma = static_cast<int>(fa.size()), nb = static_cast<int>(fb.size());
+    const double mnk = std::ldexp(1.0, ma + nb + rk);
+    std::vector<int> out;
+    if (rc == 0) {
+      I.cls = C_SPLITK;
+      I.a = st.a;
+      I.b = st.b;
+      I.shared = sh;
+    } else if (ma >= 4 && nb >= 4 && rk >= 3 && mnk >= std::ldexp(1.0, 18)) {
+      I.cls = C_GEMM;
+      const bool a_is_x = la.size() <= lb.size();
+      const int x = a_is_x ? st.a : st.b, y = a_is_x ? st.b : st.a;
+      const auto& lx = labels[x];
+      const auto& ly = labels[y];
+      std::vector<int> xf, yf, kk;
+      for (int v : lx)
+        if (!contains(ly, v)) xf.push_back(v);
+      for (int v : ly) (contains(lx, v) ? kk : yf).push_back(v);
+      I.a = x;
+      I.b = y;
+      I.shared = kk;  // in Y's bit order
+      I.m = static_cast<int>(xf.size());
+      I.n = static_cast<int>(yf.size());
+      I.k = static_cast<int>(kk.size());
+      out = yf;
+      out.insert(out.end(), xf.begin(), xf.end());
+    } else {
+      const bool a_big = la.size() >= lb.size();
+      I.cls = (rc <= 12 && rk >= 10) ? C_SPLITK : C_SMALL;
+      I.a = st.a;
+      I.b = st.b;
+      I.shared = sh;
+      const auto& big = a_big ? fa : fb;
+      const auto& small = a_big ? fb : fa;
+      out = big;
+      out.insert(out.end(), small.begin(), small.end());
+    }
+    labels[L + s] = out;
+    if (static_cast<int>(out.size()) != static_cast<int>(st.out.size()))
+      throw std::runtime_error("internal: step output rank mismatch");
+    const double bytes = (std::ldexp(1.0, static_cast<int>(la.size())) + std::ldexp(1.0, static_cast<int>(lb.size())) +
+                          std::ldexp(1.0, rc)) * 2.0 * P.elem;
+    P.flops += 8.0 * mnk;
+    P.bytes += bytes;
+    if (I.cls == C_GEMM) {
+      P.gemm_flops += 8.0 * mnk;
+      P.gemm_bytes += bytes;
+      P.n_gemm++;
+    }
+  }
+
+  // ---- execution order: by level, then class, then path order
+  std::vector<int> order(S);
+  for (int s = 0; s < S; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (info[x].level != info[y].level) return info[x].level < info[y].level;
+    return info[x].cls < info[y].cls;
+  });
+  std::vector<int> exec_pos(S);
+  for (int i = 0; i < S; ++i) exec_pos[order[i]] = i;
+  std::vector<int> last_use(L + S, -1);
+  for (int s = 0; s < S; ++s) {
+    last_use[path.steps[s].a] = std::max(last_use[path.steps[s].a], exec_pos[s]);
+    last_use[path.steps[s].b] = std::max(last_use[path.steps[s].b], exec_pos[s]);
+  }
+  std::vector<char> is_final(L + S, 0);
+  for (int id : path.final_ids) is_final[id] = 1;
+
+  // ---- arena: work region offsets by first fit in launch order
+  FirstFit ff;
+  std::vector<size_t> toff(L + S, 0);
+  auto tensor_bytes = [&](int id) { return 2 * (size_t(1) << labels[id].size()) * P.elem; };
+  for (int i = 0; i < L; ++i) toff[i] = ff.alloc(tensor_bytes(i));
+  auto release_dead = [&](int upto_pos, const std::vector<int>& ids) {
+    for (int id : ids)
+      if (!is_final[id] && last_use[id] <= upto_pos) ff.release(toff[id], tensor_bytes(id));
+  };
+
+  const int mode = operand_mode(precision);
+  const int terms = mode_terms(mode);
+  const size_t eb = mode_bytes(mode);
+  const int tc_kind = (mode >= OPM_BF16X2) ? 1 : 0;
+  int scalar_slots = 0;
+  size_t partials = 0;
+
+  // Launch records hold work-region-relative byte offsets; descriptors hold element offsets
+  // relative to the work region too. Both are rebased after the layout is known.
+  struct PendingGemm {
+    int launch;
+  };
+  std::vector<int> gemm_launches;
+
+  int i = 0;
+  while (i < S) {
+    const int s0 = order[i];
+    const int cls = info[s0].cls, lev = info[s0].level;
+    if (cls == C_SMALL || cls == C_SPLITK) {
+      int j = i;
+      while (j < S && info[order[j]].level == lev && info[order[j]].cls == cls) ++j;
+      Launch ln;
+      ln.kind = cls == C_SMALL ? LK_SMALL : LK_SPLITK;
+      ln.first = static_cast<int>(P.steps.size());
+      ln.count = j - i;
+      int blocks = 0;
+      size_t smem = 0;
+      std::vector<int> consumed;
+      for (int t = i; t < j; ++t) {
+        const int s = order[t];
+        const StepInfo& I = info[s];
+        const int c = L + s;
+        toff[c] = labels[c].empty() ? 0 : ff.alloc(tensor_bytes(c));
+        StepDev d;
+        std::memset(&d, 0, sizeof(d));
+        const auto& la = labels[I.a];
+        const auto& lb = labels[I.b];
+        d.a = static_cast<int64_t>(toff[I.a] / P.elem);
+        d.b = static_cast<int64_t>(toff[I.b] / P.elem);
+        d.c = static_cast<int64_t>(toff[c] / P.elem);
+        d.pa = int64_t(1) << la.size();
+        d.pb = int64_t(1) << lb.size();
+        d.pc = int64_t(1) << labels[c].size();
+        d.oa = make_map(labels[c], la);
+        d.ob = make_map(labels[c], lb);
+        // contracted bits ordered by A's positions
+        std::vector<int> kl;
+        for (int x : la)
+          if (contains(lb, x)) kl.push_back(x);
+        d.ka = make_map(kl, la);
+        d.kb = make_map(kl, lb);
+        d.rc = static_cast<int32_t>(labels[c].size());
+        d.rk = static_cast<int32_t>(kl.size());
+        d.block0 = blocks;
+        d.scalar_slot = -1;
+        if (cls == C_SMALL) {
+          const int64_t nout = int64_t(1) << d.rc;
+          blocks += static_cast<int>(std::min<int64_t>((nout + 255) / 256, 8192));
+        } else {
+          const int64_t nout = int64_t(1) << d.rc;
+          int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((int64_t(1) << d.rk) / 2048, 512));
+          nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, 16384 / nout));
+          d.nsplit = static_cast<int32_t>(nsplit);
+          d.poff = static_cast<int64_t>(partials);
+          partials += static_cast<size_t>(nout * nsplit);
+          if (d.rc == 0) d.scalar_slot = scalar_slots++;
+          blocks += static_cast<int>(nout * nsplit);
+        }
+        smem = std::max(smem, step_table_bytes(d));
+        ln.flops += 8.0 * std::ldexp(1.0, d.rc + d.rk);
+        ln.bytes += (std::ldexp(1.0, static_cast<int>(la.size())) + std::ldexp(1.0, static_cast<int>(lb.size())) +
+                     (d.rc ? std::ldexp(1.0, d.rc) : 0.0)) * 2.0 * P.elem;
+        P.steps.push_back(d);
+        consumed.push_back(I.a);
+        consumed.push_back(I.b);
+      }
+      ln.blocks = blocks;
+      ln.smem = smem;
+      P.launches.push_back(ln);
+      release_dead(j - 1, consumed);
+      i = j;
+    } else {
+      const int s = s0;
+      const StepInfo& I = info[s];
+      const int c = L + s;
+      const auto& lx = labels[I.a];
+      const auto& ly = labels[I.b];
+      std::vector<int> xf, yf;
+      for (int v : lx)
+        if (!contains(I.shared, v)) xf.push_back(v);
+      for (int v : ly)
+        if (!contains(I.shared, v)) yf.push_back(v);
+      const int64_t Mt = int64_t(1) << (I.m + 1), Nt = int64_t(1) << I.n, Kt = int64_t(1) << (I.k + 1);
+      const bool use_tc = tc_ok && precision >= AJF_PREC_TF32 && tc_gemm_supported(Mt, Nt, Kt, tc_kind);
+      const int gmode = use_tc ? mode : (P.f64 ? OPM_F64 : OPM_F32);
+      const int gterms = use_tc ? terms : 1;
+      const size_t geb = use_tc ? eb : (P.f64 ? 8 : 4);
+      const size_t xbytes = size_t(Mt) * size_t(Kt) * geb, ybytes = size_t(Nt) * size_t(Kt) * geb;
+      size_t xo[3] = {0, 0, 0}, yo[3] = {0, 0, 0};
+      for (int t = 0; t < gterms; ++t) xo[t] = ff.alloc(xbytes);
+      for (int t = 0; t < gterms; ++t) yo[t] = ff.alloc(ybytes);
+      // permute launch (X and Y)
+      PermDev px, py;
+      std::memset(&px, 0, sizeof(px));
+      std::memset(&py, 0, sizeof(py));
+      px.src = static_cast<int64_t>(toff[I.a] / P.elem);
+      px.plane = int64_t(1) << lx.size();
+      px.rows = make_map(xf, lx);
+      px.cols = make_map(I.shared, lx);
+      px.rbits = I.m;
+      px.kbits = I.k;
+      px.embed = 1;
+      px.rows_fast = contains(xf, lx[0]) ? 1 : 0;
+      px.mode = gmode;
+      py.src = static_cast<int64_t>(toff[I.b] / P.elem);
+      py.plane = int64_t(1) << ly.size();
+      py.rows = make_map(yf, ly);
+      py.cols = make_map(I.shared, ly);
+      py.rbits = I.n;
+      py.kbits = I.k;
+      py.embed = 0;
+      py.rows_fast = contains(yf, ly[0]) ? 1 : 0;
+      py.mode = gmode;
+      for (int t = 0; t < 3; ++t) {
+        px.dst[t] = static_cast<int64_t>(xo[t]);
+        py.dst[t] = static_cast<int64_t>(yo[t]);
+      }
+      Launch lp;
+      lp.kind = LK_PERM;
+      lp.first = static_cast<int>(P.perms.size());
+      lp.count = 2;
+      const int64_t tiles = std::max<int64_t>(int64_t(1) << std::max(0, I.m + I.k - 10),
+                                              int64_t(1) << std::max(0, I.n + I.k - 10));
+      lp.blocks = static_cast<int>(std::min<int64_t>(std::max<int64_t>(tiles, 1), 2048));
+      lp.smem = std::max(perm_table_bytes(px), perm_table_bytes(py));
+      P.perms.push_back(px);
+      P.perms.push_back(py);
+      P.launches.push_back(lp);
+      release_dead(exec_pos[s], {I.a, I.b});
+      toff[c] = ff.alloc(tensor_bytes(c));
+      Launch lg;
+      lg.kind = use_tc ? LK_GEMM_TC : LK_GEMM_SIMT;
+      lg.M = Mt;
+      lg.N = Nt;
+      lg.K = Kt;
+      lg.c_off = static_cast<int64_t>(toff[c]);
+      lg.tc_kind = tc_kind;
+      if (use_tc) {
+        // split products: pairs (i, j) with i + j <= terms - 1 (hi=0, mid=1, lo=2)
+        int np = 0;
+        for (int sum = 0; sum < gterms; ++sum)
+          for (int ti = 0; ti <= sum; ++ti) {
+            const int tj = sum - ti;
+            lg.a_off[np] = static_cast<int64_t>(xo[ti]);
+            lg.b_off[np] = static_cast<int64_t>(yo[tj]);
+            ++np;
+          }
+        lg.npass = np;
+        P.tensor_cores++;
+      } else {
+        lg.a_off[0] = static_cast<int64_t>(xo[0]);
+        lg.b_off[0] = static_cast<int64_t>(yo[0]);
+        lg.npass = 1;
+      }
+      lg.flops = 8.0 * std::ldexp(1.0, I.m + I.n + I.k);
+      lg.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) + std::ldexp(1.0, static_cast<int>(ly.size())) +
+                  std::ldexp(1.0, static_cast<int>(labels[c].size()))) * 2.0 * P.elem;
+      gemm_launches.push_back(static_cast<int>(P.launches.size()));
+      P.launches.push_back(lg);
+      for (int t = 0; t < gterms; ++t) ff.release(xo[t], xbytes);
+      for (int t = 0; t < gterms; ++t) ff.release(yo[t], ybytes);
+      ++i;
+    }
+  }
+
+  // ---- final reduction
+  FinalDev& f = P.fin;
+  std::memset(&f, 0, sizeof(f));
+  f.open_off = -1;
+  f.n_qubits = net.n_qubits;
+  f.loops = net.loops;
+  f.alg = net.alg;
+  int open_id = -1;
+  for (int id : path.final_ids)
+    if (!labels[id].empty()) open_id = id;
+  f.open_bits = static_cast<int32_t>(net.open_labels.size());
+  if (open_id >= 0) {
+    f.open_off = static_cast<int64_t>(toff[open_id] / P.elem);
+    f.open_plane = int64_t(1) << labels[open_id].size();
+    f.open_map = make_map(net.open_labels, labels[open_id]);
+    if (labels[open_id].size() != net.open_labels.size()) throw std::runtime_error("internal: open tensor rank");
+  } else {
+    std::memset(&f.open_map, 0, sizeof(f.open_map));
+  }
+  f.n_scalars = scalar_slots;
+  P.n_scalars = scalar_slots;
+  P.n_traces = int64_t(1) << f.open_bits;
+  P.final_nchunks = (f.open_map.nbits + 7) / 8;
+  P.final_blocks = static_cast<int>(std::min<int64_t>((P.n_traces + 255) / 256, 1024));
+  f.nblocks = P.final_blocks;
+
+  // ---- arena layout
+  size_t off = 0;
+  P.off_desc = off;
+  P.off_leaves = off;
+  off += align_up(sizeof(LeafDev) * std::max<size_t>(1, net.leaf_specs.size()));
+  P.off_steps = off;
+  off += align_up(sizeof(StepDev) * std::max<size_t>(1, P.steps.size()));
+  P.off_perms = off;
+  off += align_up(sizeof(PermDev) * std::max<size_t>(1, P.perms.size()));
+  P.off_final = off;
+  off += align_up(sizeof(FinalDev));
+  P.desc_bytes = off - P.off_desc;
+  P.off_inputs = off;
+  P.input_bytes = inputs_complex * 16;
+  off += align_up(std::max<size_t>(P.input_bytes, 16));
+  P.off_result = off;
+  off += align_up(4 * sizeof(double));
+  P.off_status = off;
+  off += align_up(16 * sizeof(int32_t));
+  P.off_scalars = off;
+  off += align_up(sizeof(double) * 2 * std::max(1, scalar_slots));
+  P.off_partial = off;
+  P.partial_count = partials;
+  off += align_up(sizeof(double) * 2 * std::max<size_t>(1, partials));
+  P.off_open_partial = off;
+  off += align_up(sizeof(double) * P.final_blocks);
+  P.off_traces = off;
+  off += align_up(sizeof(double) * 2 * static_cast<size_t>(P.n_traces));
+  P.off_work = off;
+  P.arena_bytes = off + ff.peak();
+
+  // ---- rebase work-region offsets to the arena
+  const int64_t wel = static_cast<int64_t>(P.off_work / P.elem);
+  for (int l = 0; l < L; ++l) {
+    const LeafSpec& sp = net.leaf_specs[l];
+    LeafDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.off = static_cast<int64_t>(toff[l] / P.elem) + wel;
+    d.plane = int64_t(1) << labels[l].size();
+    d.src = sp.src;
+    d.kind = sp.kind;
+    d.a = sp.a;
+    d.nk = sp.nk;
+    d.kbits = sp.kbits;
+    d.bits = static_cast<int32_t>(labels[l].size());
+    P.leaves.push_back(d);
+  }
+  for (auto& d : P.steps) {
+    d.a += wel;
+    d.b += wel;
+    d.c += wel;
+  }
+  for (auto& p : P.perms) {
+    p.src += wel;
+    for (int t = 0; t < 3; ++t) p.dst[t] += static_cast<int64_t>(P.off_work);
+  }
+  for (int li : gemm_launches) {
+    Launch& g = P.launches[li];
+    for (int t = 0; t < 6; ++t) {
+      g.a_off[t] += static_cast<int64_t>(P.off_work);
+      g.b_off[t] += static_cast<int64_t>(P.off_work);
+    }
+    g.c_off += static_cast<int64_t>(P.off_work);
+  }
+  if (f.open_off >= 0) f.open_off += wel;
+  return P;
+}
+
+}  // namespace ajf
