@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "ajf_upload": (I32, [P]),
             "ajf_fidelity_alg1_batch": (I32, [ctypes.POINTER(P), ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_version": (ctypes.c_char_p, []),
+            "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
         }
@@ -216,6 +217,19 @@ def ajf_fidelity_alg1_batch(ctxs: Sequence, eps: float = -1.0) -> list:
         msgs = "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c))
         raise AjfError(st, msgs)
     return [r.as_dict() for r in res]
+
+
+def ajf_selftest_gemm(device: int, kind: int, A: np.ndarray, B: np.ndarray, M: int, N: int, K: int) -> np.ndarray:
+    """Tensor-core GEMM self-test: A (npass, M, K), B (npass, N, K) as float32 (kind 0) or bf16 bit
+    patterns in uint16 (kind 1); returns sum_p A_p B_p^T as float64."""
+    A = np.ascontiguousarray(A)
+    B = np.ascontiguousarray(B)
+    npass = A.shape[0]
+    C = np.empty((M, N), dtype=np.float64)
+    st = lib().ajf_selftest_gemm(device, kind, npass, M, N, K, _ptr(A), _ptr(B), _ptr(C))
+    if st != AJF_OK:
+        raise AjfError(st, "ajf_selftest_gemm failed")
+    return C
 
 
 def ajf_profile_enable(ctx, on: bool = True) -> None:

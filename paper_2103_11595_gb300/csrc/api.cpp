@@ -294,10 +294,11 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
         e = launch_perm(perms + ln.first, ln.count, ln.blocks, ln.smem, arena, base, f64, s);
         break;
       case LK_GEMM_SIMT:
-        e = launch_gemm_simt(base + ln.a_off[0], base + ln.b_off[0], base + ln.c_off, ln.M, ln.N, ln.K, f64, s);
+        e = launch_gemm_simt(base + ln.a_off[0], base + ln.b_off[0], base + ln.c_off, ln.M, ln.N, ln.K, ln.op_f64 != 0,
+                             s);
         break;
       case LK_GEMM_TC:
-        e = launch_gemm_tc(base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<float*>(base + ln.c_off), ln.M, ln.N,
+        e = launch_gemm_tc(base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<double*>(base + ln.c_off), ln.M, ln.N,
                            ln.K, ln.tc_kind, status, s);
         break;
       default:
@@ -744,6 +745,41 @@ ajf_status ajf_launch(ajf_ctx* c, double* dev_result) {
     CUDA_TRY(c, cudaMemcpyAsync(dev_result, c->arena + c->prog.off_result, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
                                 c->stream));
   return AJF_OK;
+}
+
+ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t N, int64_t K, const void* A,
+                             const void* B, double* C) {
+  if (!A || !B || !C || npass < 1 || npass > 6 || (kind != 0 && kind != 1) || M <= 0 || N <= 0 || K <= 0)
+    return AJF_E_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
+  if (!tc_gemm_supported(M, N, K, kind)) return AJF_E_UNSUPPORTED;
+  const size_t es = kind == 1 ? 2 : 4;
+  const size_t abytes = size_t(npass) * M * K * es, bbytes = size_t(npass) * N * K * es, cbytes = size_t(M) * N * 8;
+  char* d = nullptr;
+  const size_t off_b = (abytes + 255) / 256 * 256, off_c = off_b + (bbytes + 255) / 256 * 256;
+  const size_t off_s = off_c + (cbytes + 255) / 256 * 256;
+  if (cudaMalloc(&d, off_s + 256) != cudaSuccess) return AJF_E_NOMEM;
+  ajf_status st = AJF_OK;
+  int status = 0;
+  int64_t ao[6], bo[6];
+  for (int p = 0; p < npass; ++p) {
+    ao[p] = static_cast<int64_t>(p * M * K * es);
+    bo[p] = static_cast<int64_t>(off_b + p * N * K * es);
+  }
+  if (cudaMemcpy(d, A, abytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d + off_b, B, bbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d + off_s, 0, 256) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, npass, reinterpret_cast<double*>(d + off_c), M, N, K, kind,
+                                     reinterpret_cast<int*>(d + off_s), 0) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
+  if (st == AJF_OK && (cudaMemcpy(C, d + off_c, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(&status, d + off_s, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && status != 0) st = AJF_E_TIMEOUT;
+  cudaFree(d);
+  return st;
 }
 
 ajf_status ajf_profile_enable(ajf_ctx* c, int on) {

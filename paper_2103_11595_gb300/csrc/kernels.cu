@@ -320,10 +320,12 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
 
 // ------------------------------------------------------------------ CUDA-core GEMM
 
-// C[M][N] (row-major, ldc = N) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous.
+// C[M][N] (row-major, ldc = N, FP64) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous;
+// operands and accumulation in T (FP32 or FP64).
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __restrict__ A, const T* __restrict__ B,
-                                                                     T* __restrict__ C, int64_t M, int64_t N, int64_t K) {
+                                                                     double* __restrict__ C, int64_t M, int64_t N,
+                                                                     int64_t K) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t gn = n0 + tc * TN + j;
-      if (gn < N) C[gm * N + gn] = acc[i][j];
+      if (gn < N) C[gm * N + gn] = static_cast<double>(acc[i][j]);
     }
   }
 }
@@ -494,7 +496,7 @@ cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, i
   } else {
     const unsigned grid = unsigned(((N + 127) / 128) * ((M + 127) / 128));
     k_gemm_simt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, s>>>(static_cast<const float*>(A), static_cast<const float*>(B),
-                                                              static_cast<float*>(C), M, N, K);
+                                                              static_cast<double*>(C), M, N, K);
   }
   return cudaGetLastError();
 }

@@ -122,8 +122,8 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   Program P;
   P.alg = net.alg;
   P.precision = precision;
-  P.f64 = (precision == AJF_PREC_F64);
-  P.elem = P.f64 ? 8 : 4;
+  P.f64 = true;  // tensors are FP64 in HBM in every mode; the precision mode sets the GEMM operands
+  P.elem = 8;
   const int L = static_cast<int>(net.leaf_labels.size());
   const int S = static_cast<int>(path.steps.size());
   std::vector<std::vector<int>> labels(L + S);
@@ -317,9 +317,10 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
         if (!contains(I.shared, v)) yf.push_back(v);
       const int64_t Mt = int64_t(1) << (I.m + 1), Nt = int64_t(1) << I.n, Kt = int64_t(1) << (I.k + 1);
       const bool use_tc = tc_ok && precision >= AJF_PREC_TF32 && tc_gemm_supported(Mt, Nt, Kt, tc_kind);
-      const int gmode = use_tc ? mode : (P.f64 ? OPM_F64 : OPM_F32);
+      const bool op_f64 = !use_tc && precision == AJF_PREC_F64;
+      const int gmode = use_tc ? mode : (op_f64 ? OPM_F64 : OPM_F32);
       const int gterms = use_tc ? terms : 1;
-      const size_t geb = use_tc ? eb : (P.f64 ? 8 : 4);
+      const size_t geb = use_tc ? eb : (op_f64 ? 8 : 4);
       const size_t xbytes = size_t(Mt) * size_t(Kt) * geb, ybytes = size_t(Nt) * size_t(Kt) * geb;
       size_t xo[3] = {0, 0, 0}, yo[3] = {0, 0, 0};
       for (int t = 0; t < gterms; ++t) xo[t] = ff.alloc(xbytes);
@@ -365,6 +366,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       toff[c] = ff.alloc(tensor_bytes(c));
       Launch lg;
       lg.kind = use_tc ? LK_GEMM_TC : LK_GEMM_SIMT;
+      lg.op_f64 = op_f64 ? 1 : 0;
       lg.M = Mt;
       lg.N = Nt;
       lg.K = Kt;

@@ -19,6 +19,7 @@ struct Launch {
   int64_t a_off[6] = {0, 0, 0, 0, 0, 0}, b_off[6] = {0, 0, 0, 0, 0, 0};
   int32_t npass = 0;
   int32_t tc_kind = 0;           // 0 tf32, 1 bf16
+  int32_t op_f64 = 1;            // CUDA-core GEMM: FP64 (1) or FP32 (0) operands
   int64_t c_off = 0;             // byte offset of C
   int64_t M = 0, N = 0, K = 0;
   double flops = 0, bytes = 0;   // algorithmic work of the complex step this launch belongs to

@@ -1,13 +1,336 @@
-// Tensor-core GEMM on tcgen05 (placeholder until the sm_103a kernel lands).
+// Tensor-core GEMM on sm_103a: tcgen05.mma with TMEM accumulators, TMA-fed shared-memory stages.
+//
+//   C[M][N] (FP64, row-major) = sum_{p < npass} A_p[M][K] . B_p[N][K]^T
+//
+// A_p and B_p are K-contiguous (K-major) operands in TF32 (FP32 containers, pre-rounded) or bf16.
+// Several passes accumulate split operands into one FP32 accumulator: hi*hi + hi*lo + lo*hi for
+// the 3-pass TF32 split (the smaller terms are added first by the caller's pass order), up to six
+// passes for the 3-term bf16 split. The complex contraction step arrives here as one real GEMM
+// (the caller embedded the complex operand as [[Re,-Im],[Im,Re]]).
+//
+// Kernel structure (one CTA per 128 x BN output tile, 192 threads):
+//   warp 0, lane 0 : TMA producer -- 2D tiled loads of A (128 rows x 128 B) and B (BN rows x 128 B)
+//                    with 128-byte swizzle into a ring of shared-memory stages (mbarrier
+//                    expect-tx / complete-tx);
+//   warp 1         : allocates BN TMEM columns; lane 0 issues tcgen05.mma (M=128, N=BN, K=32 B
+//                    per instruction) and tcgen05.commit to release stages and signal the epilogue;
+//   warps 2..5     : epilogue -- tcgen05.ld 32 lanes x 32 columns per warp quarter, FP32 -> FP64,
+//                    stored to C.
+// Every wait is bounded by the global timer (2 s); on expiry the kernel records a status code,
+// stops issuing work, releases TMEM and returns, so the host sees AJF_E_TIMEOUT instead of a hang.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace ajf {
+namespace {
 
-bool tc_gemm_supported(int64_t, int64_t, int64_t, int) { return false; }
+constexpr int kBM = 128;            // rows per tile (UMMA M)
+constexpr int kRowBytes = 128;      // bytes of K per stage row (one 128-byte swizzle span)
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr int kMaxPass = 6;
+constexpr unsigned long long kWaitNs = 2000000000ull;
 
-cudaError_t launch_gemm_tc(char*, const int64_t*, const int64_t*, int, float*, int64_t, int64_t, int64_t, int, int*,
-                           cudaStream_t) {
-  return cudaErrorNotSupported;
+struct TcParams {
+  CUtensorMap amap[kMaxPass];
+  CUtensorMap bmap[kMaxPass];
+  double* C;
+  int* status;
+  int64_t N;
+  int32_t npass, bn, kblocks, ntn;
+  uint32_t idesc;
+  uint32_t stage_bytes;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and status set) if the phase did not complete within kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t n = 1;; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 255) == 0 && globaltimer() - t0 > kWaitNs) {
+      atomicExch(status, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFF);        // start address
+  d |= static_cast<uint64_t>(1) << 16;                      // leading byte offset (unused for SW128 K-major)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+  d |= static_cast<uint64_t>(1) << 46;                      // descriptor version for tcgen05
+  d |= static_cast<uint64_t>(2) << 61;                      // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bn = p.bn;
+  const uint32_t a_bytes = kBM * kRowBytes;
+  uint8_t* bars = smem + kStages * p.stage_bytes;
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = full0 + 8 * kStages;
+  const uint32_t done_bar = empty0 + 8 * kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kStages + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kStages + 12);
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x / p.ntn) * kBM;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x % p.ntn) * bn;
+  const uint32_t ncols = bn < 32 ? 32u : static_cast<uint32_t>(bn);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int iters = p.kblocks * p.npass;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % kStages;
+      const uint32_t ph = static_cast<uint32_t>(it / kStages) & 1u;
+      if (*abort_flag || !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, 11)) {
+        *abort_flag = 1;
+        break;
+      }
+      const int kb = it / p.npass, pass = it % p.npass;
+      const uint32_t sa = smem_u32(smem + s * p.stage_bytes);
+      const uint32_t sb = sa + a_bytes;
+      const int32_t kx = kb * (kRowBytes / (kBF16 ? 2 : 4));
+      mbar_expect_tx(full0 + 8 * s, a_bytes + static_cast<uint32_t>(bn) * kRowBytes);
+      tma_load_2d(sa, &p.amap[pass], kx, static_cast<int32_t>(m0), full0 + 8 * s);
+      tma_load_2d(sb, &p.bmap[pass], kx, static_cast<int32_t>(n0), full0 + 8 * s);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    bool ok = true;
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % kStages;
+      const uint32_t ph = static_cast<uint32_t>(it / kStages) & 1u;
+      if (*abort_flag || !mbar_wait(full0 + 8 * s, ph, p.status, 12)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * p.stage_bytes);
+      const uint32_t sb = sa + a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {  // 4 instructions x 32 bytes of K
+        const uint64_t da = smem_desc(sa + 32 * kk), db = smem_desc(sb + 32 * kk);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        if (kBF16) mma_f16(tmem, da, db, p.idesc, acc);
+        else mma_tf32(tmem, da, db, p.idesc, acc);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    if (ok) mma_commit(done_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM -> registers -> FP64 C
+    const int q = warp & 3;
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait(done_bar, 0, p.status, 13);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (ok && !*abort_flag) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t row = m0 + 32 * q + lane;
+      double* crow = p.C + row * p.N + n0;
+      for (int c0 = 0; c0 < bn; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c0), r);
+        double2* dst = reinterpret_cast<double2*>(crow + c0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          dst[j] = make_double2(static_cast<double>(__uint_as_float(r[2 * j])),
+                                static_cast<double>(__uint_as_float(r[2 * j + 1])));
+      }
+    } else {
+      *abort_flag = 1;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(f);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box_rows, bool bf16) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  const size_t es = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(k * es)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / es), box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tile_n(int64_t N) { return N >= 256 ? 256 : static_cast<int>(N); }
+
+size_t smem_bytes(int bn) {
+  const size_t stage = size_t(kBM) * kRowBytes + size_t(bn) * kRowBytes;
+  return kStages * stage + 1024 /* barriers */ + 1024 /* alignment */;
+}
+
+}  // namespace
+
+bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind) {
+  const int64_t bk = kind == 1 ? 64 : 32;  // elements per 128-byte row
+  return M >= kBM && (M % kBM) == 0 && N >= 32 && (N & (N - 1)) == 0 && K >= bk && (K % bk) == 0 &&
+         M * N <= (int64_t(1) << 40);
+}
+
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int npass, double* C, int64_t M,
+                           int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s) {
+  if (!tc_gemm_supported(M, N, K, kind) || npass < 1 || npass > kMaxPass) return cudaErrorNotSupported;
+  const bool bf16 = kind == 1;
+  const int bn = tile_n(N);
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  for (int i = 0; i < npass; ++i) {
+    if (!make_map(&p.amap[i], base + a_off[i], M, K, kBM, bf16)) return cudaErrorInvalidValue;
+    if (!make_map(&p.bmap[i], base + b_off[i], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
+  }
+  p.C = C;
+  p.status = d_status;
+  p.N = N;
+  p.npass = npass;
+  p.bn = bn;
+  p.kblocks = static_cast<int32_t>(K / (kRowBytes / (bf16 ? 2 : 4)));
+  p.ntn = static_cast<int32_t>(N / bn);
+  // instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major, N >> 3, M >> 4
+  const uint32_t fmt = bf16 ? 1u : 2u;
+  p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(bn >> 3) << 17) |
+            (static_cast<uint32_t>(kBM >> 4) << 24);
+  p.stage_bytes = static_cast<uint32_t>(kBM * kRowBytes + bn * kRowBytes);
+  const size_t smem = smem_bytes(bn);
+  const int64_t tiles = (M / kBM) * (N / bn);
+  if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  if (bf16) {
+    cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    k_gemm_tc<true><<<static_cast<unsigned>(tiles), kThreads, smem, s>>>(p);
+  } else {
+    cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    k_gemm_tc<false><<<static_cast<unsigned>(tiles), kThreads, smem, s>>>(p);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace ajf

@@ -1,0 +1,70 @@
+"""The tcgen05 tensor-core GEMM alone, against float64 products of the same (exactly representable)
+inputs. TF32 and bf16 products of representable inputs are exact in FP32, so the only error is the
+FP32 accumulation: |dC| <= K * 2^-23 * sum |a||b| is checked with margin."""
+import numpy as np
+import pytest
+
+from paper_2103_11595_gb300 import ajf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def tf32(x):
+    """Round float32 to TF32 (10 explicit mantissa bits), nearest-even on the bit pattern."""
+    b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0xFFF + ((b >> 13) & 1)) & ~np.uint64(0x1FFF)
+    return b.astype(np.uint32).view(np.float32)
+
+
+def bf16_bits(x):
+    b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return b.astype(np.uint16)
+
+
+def bits_to_f64(b):
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+SHAPES = [(128, 32, 32, 1), (128, 64, 64, 1), (256, 128, 128, 3), (128, 256, 64, 2), (512, 512, 256, 3),
+          (1024, 256, 512, 1)]
+
+
+@pytest.mark.parametrize("M,N,K,npass", SHAPES)
+def test_tf32_gemm(M, N, K, npass):
+    rng = np.random.default_rng(M + N + K + npass)
+    A = tf32(rng.standard_normal((npass, M, K)).astype(np.float32))
+    B = tf32(rng.standard_normal((npass, N, K)).astype(np.float32))
+    C = ajf.ajf_selftest_gemm(0, 0, A, B, M, N, K)
+    ref = sum(A[p].astype(np.float64) @ B[p].astype(np.float64).T for p in range(npass))
+    bound = sum(np.abs(A[p]).astype(np.float64) @ np.abs(B[p]).astype(np.float64).T for p in range(npass))
+    assert np.all(np.abs(C - ref) <= 4 * K * npass * 2.0 ** -23 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("M,N,K,npass", [(128, 32, 64, 1), (256, 128, 128, 3), (512, 256, 256, 6)])
+def test_bf16_gemm(M, N, K, npass):
+    rng = np.random.default_rng(7 * M + N + K)
+    A = bf16_bits(rng.standard_normal((npass, M, K)))
+    B = bf16_bits(rng.standard_normal((npass, N, K)))
+    C = ajf.ajf_selftest_gemm(0, 1, A, B, M, N, K)
+    Af, Bf = bits_to_f64(A), bits_to_f64(B)
+    ref = sum(Af[p] @ Bf[p].T for p in range(npass))
+    bound = sum(np.abs(Af[p]) @ np.abs(Bf[p]).T for p in range(npass))
+    assert np.all(np.abs(C - ref) <= 4 * K * npass * 2.0 ** -23 * bound + 1e-30)
+
+
+def test_unsupported_shape_is_reported():
+    A = np.zeros((1, 64, 32), dtype=np.float32)
+    B = np.zeros((1, 32, 32), dtype=np.float32)
+    with pytest.raises(ajf.AjfError) as e:
+        ajf.ajf_selftest_gemm(0, 0, A, B, 64, 32, 32)
+    assert e.value.status == ajf.AJF_E_UNSUPPORTED
