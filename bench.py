@@ -170,12 +170,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32")
+    ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--trials", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--instances", type=int, default=N_INSTANCES,
+                    help="mid-config seeds per step (small values for profiler captures)")
     args = ap.parse_args()
+    n_inst = args.instances
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -195,7 +198,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    insts = [W.mid(rank * N_INSTANCES + i) for i in range(N_INSTANCES)]
+    insts = [W.mid(rank * n_inst + i) for i in range(n_inst)]
 
     def make_contexts(precision, use_graph=True):
         ctxs, infos = [], []
@@ -208,7 +211,7 @@ def main():
         return ctxs, infos
 
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
-    out = torch.zeros(N_INSTANCES, 3, dtype=torch.float64, device=dev)
+    out = torch.zeros(n_inst, 3, dtype=torch.float64, device=dev)
 
     def timed_steps(ctxs, steps, warmup):
         def step():
@@ -241,7 +244,7 @@ def main():
     clocks = clk.summary()
     F_fast = out[:, 1].cpu().numpy().copy()
     total_s = max_over_ranks(total_ms / 1e3, world)
-    evals = N_INSTANCES * args.steps * world
+    evals = n_inst * args.steps * world
     value = evals / total_s
     flops_per_step = sum(i["flops"] for i in infos)
     launches_per_step = sum(i["n_launches"] for i in infos)
@@ -264,11 +267,16 @@ def main():
     pk = peaks()
     d = classes[dom]
     if dom == "gemm_tc":
-        kind = infos[0].get("n_tc_gemms", 0)
-        peak = pk["bf16_tflops"] * (1.1 / 2.25)
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                "peak_src": f"{pk['src']} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+        passes = {"tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6}[args.precision]
+        if args.precision.startswith("bf16"):
+            peak = pk["bf16_tflops"]
+            src = f"{pk['src']} bf16 dense burst (MEASURED_PEAKS.json)"
+        else:
+            peak = pk["bf16_tflops"] * (1.1 / 2.25)
+            src = f"{pk['src']} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_src": src, "passes": passes}
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        roof["hw_tensor_frac"] = passes * achieved / peak
     elif dom == "gemm_simt":
         if args.precision == "f64":
             peak = 1.25
@@ -294,7 +302,7 @@ def main():
         p_ms = timed_steps(pctx, 1, 1)
         F_plain = out[:, 1].cpu().numpy().copy()
         p_s = max_over_ranks(p_ms / 1e3, world)
-        plain = {"value": N_INSTANCES * world / p_s, "unit": "evals/s", "dtype": "c128",
+        plain = {"value": n_inst * world / p_s, "unit": "evals/s", "dtype": "c128",
                  "max_abs_dF_fast_vs_plain": float(np.max(np.abs(F_fast - F_plain))),
                  "max_rel_d_one_minus_F": float(np.max(np.abs((1 - F_fast) - (1 - F_plain)) / np.abs(1 - F_plain)))}
         for c in pctx:
@@ -324,7 +332,7 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     for c in e2e_ctx:
         c.close()
-    e2e = {"value": N_INSTANCES * args.e2e_steps * world / e2e_s, "unit": "evals/s",
+    e2e = {"value": n_inst * args.e2e_steps * world / e2e_s, "unit": "evals/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "note": "host wall clock: load + plan (structural cache hit) + upload + run + read back, per instance"}
 
@@ -337,9 +345,10 @@ def main():
             "metric": "fidelity evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f64": "c128", "f32": "c64"}.get(args.precision, "c64-" + args.precision),
+            "dtype": {"f64": "f64", "f32": "f32"}.get(args.precision, args.precision) +
+                     (" (GEMM operands; FP32 accumulate; FP64 tensors, trace and F)" if args.precision != "f64" else ""),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "planner": "auto",
+            "config": {"workload": WORKLOAD if n_inst == N_INSTANCES else WORKLOAD + f" (only {n_inst} seeds)", "precision": args.precision, "planner": "auto",
                        "trials": args.trials, "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"{world} independent ranks (weak scaling)"},
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,

@@ -16,7 +16,7 @@ from paper_2103_11595_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6}
+TOL = {"f64": 1e-12, "f32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-6, "bf16x6": 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -237,20 +237,20 @@ def mid0_oracle():
     return inst, network.alg2_fidelity(inst, order="minfill")
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "tf32x3", "bf16x3", "bf16x6"])
 def test_mid_config_alg2(mid0_oracle, precision):
     """n=16 line, 200 gates, 10 mixed noises: Alg. II on the GPU vs the oracle's own network."""
     inst, ref = mid0_oracle
     r, _, info = run(inst, 2, precision, trials=16)
     assert info["width"] <= 28
-    if precision in ("tf32x3", "bf16x6"):
+    if precision in ("tf32x3", "bf16x3", "bf16x6"):
         assert info["n_tc_gemms"] > 0
     check(r, ref, TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["tf32"])
 def test_mid_config_low_precision_error_is_bounded(mid0_oracle, precision):
-    """One-pass TF32 and two-term bf16 cannot reach 1e-6; their error is measured and bounded."""
+    """One-pass TF32 (10-bit mantissa) cannot reach 1e-6; its error is measured and bounded."""
     inst, ref = mid0_oracle
     r, _, info = run(inst, 2, precision, trials=16)
     assert info["n_tc_gemms"] > 0
