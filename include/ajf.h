@@ -221,13 +221,14 @@ ajf_status ajf_profile_enable(ajf_ctx *ctx, int on);
 ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
 
 /* Self-test of the tensor-core GEMM kernel alone (no paper counterpart; used by the test suite):
- * C[M][N] = sum_{p < npass} A_p[M][K] . B_p[N][K]^T on device `device`, FP32 accumulation.
- * kind 0: A and B hold npass * M * K (resp. N * K) FP32 values (read as TF32); kind 1: bf16 bit
+ * C[M][N] = sum_{i + j < terms} A_i[M][K] . B_j[N][K]^T on device `device` for split operand
+ * terms A_0..A_{terms-1}, B_0..B_{terms-1} (terms 1..3), FP32 accumulation promoted per K block.
+ * kind 0: A and B hold terms * M * K (resp. N * K) FP32 values (read as TF32); kind 1: bf16 bit
  * patterns (uint16). All pointers are host memory; C receives M * N doubles. The call allocates
  * and frees its own device memory and synchronises the device.
  * Errors: AJF_E_ARG, AJF_E_UNSUPPORTED (shape not tile-aligned: M % 128, N power of two >= 32,
  * K a multiple of 128 bytes), AJF_E_CUDA, AJF_E_TIMEOUT. */
-ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t N, int64_t K, const void *A,
+ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t N, int64_t K, const void *A,
                              const void *B, double *C);
 
 /* Library version string, e.g. "ajf 0.1 sm_103a". */

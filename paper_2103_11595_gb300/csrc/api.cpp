@@ -749,7 +749,7 @@ ajf_status ajf_launch(ajf_ctx* c, double* dev_result) {
 
 ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t N, int64_t K, const void* A,
                              const void* B, double* C) {
-  if (!A || !B || !C || npass < 1 || npass > 6 || (kind != 0 && kind != 1) || M <= 0 || N <= 0 || K <= 0)
+  if (!A || !B || !C || npass < 1 || npass > 3 || (kind != 0 && kind != 1) || M <= 0 || N <= 0 || K <= 0)
     return AJF_E_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
   if (!tc_gemm_supported(M, N, K, kind)) return AJF_E_UNSUPPORTED;

@@ -23,11 +23,12 @@ cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblock
                          const double2* scalars, double* traces, double* partial, double* result, bool f64,
                          cudaStream_t s);
 
-// Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (FP64, row-major) = sum_p A_p[M][K] . B_p[N][K]^T
-// over `npass` (A_p, B_p) operand pairs given as byte offsets from `base`, accumulated in FP32.
-// kind 0: tf32, 1: bf16. Returns cudaErrorNotSupported when the shape is not tile-aligned.
+// Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (FP64, row-major) =
+// sum_{i + j < terms} A_i[M][K] . B_j[N][K]^T for the split terms A_t, B_t (byte offsets from
+// `base`), FP32 accumulation promoted per K block. kind 0: tf32, 1: bf16.
+// Returns cudaErrorNotSupported when the shape is not tile-aligned.
 bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
-cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int npass, double* C, int64_t M,
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s);
 
 }  // namespace ajf

@@ -373,16 +373,12 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       lg.c_off = static_cast<int64_t>(toff[c]);
       lg.tc_kind = tc_kind;
       if (use_tc) {
-        // split products: pairs (i, j) with i + j <= terms - 1 (hi=0, mid=1, lo=2)
-        int np = 0;
-        for (int sum = 0; sum < gterms; ++sum)
-          for (int ti = 0; ti <= sum; ++ti) {
-            const int tj = sum - ti;
-            lg.a_off[np] = static_cast<int64_t>(xo[ti]);
-            lg.b_off[np] = static_cast<int64_t>(yo[tj]);
-            ++np;
-          }
-        lg.npass = np;
+        // split terms (hi=0, mid=1, lo=2); the kernel forms every product with i + j < terms
+        for (int t = 0; t < gterms; ++t) {
+          lg.a_off[t] = static_cast<int64_t>(xo[t]);
+          lg.b_off[t] = static_cast<int64_t>(yo[t]);
+        }
+        lg.npass = gterms;
         P.tensor_cores++;
       } else {
         lg.a_off[0] = static_cast<int64_t>(xo[0]);

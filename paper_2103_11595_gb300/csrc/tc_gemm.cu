@@ -1,34 +1,37 @@
 // Tensor-core GEMM on sm_103a: tcgen05.mma with TMEM accumulators, TMA-fed shared-memory stages,
 // and promotion of partial sums to round-to-nearest FP32 on the CUDA cores.
 //
-//   C[M][N] (FP64, row-major) = sum_{p < npass} A_p[M][K] . B_p[N][K]^T
+//   C[M][N] (FP64, row-major) = sum_{i + j < T} A_i[M][K] . B_j[N][K]^T
 //
-// A_p and B_p are K-contiguous (K-major) operands in TF32 (FP32 containers, pre-rounded) or bf16.
-// Pass 0 multiplies the leading split terms (hi x hi); passes 1.. multiply the correction terms
-// (hi x lo, lo x hi, ...), which are 2^-11 (TF32) or 2^-8 (bf16) smaller.
+// A_t and B_t (t < T) are the terms of a split operand -- x = x_0 + x_1 (+ x_2) -- stored
+// K-contiguous (K-major) in TF32 (FP32 containers, pre-rounded) or bf16. T = 1 is a plain
+// one-pass product; T = 2 is the three-product split (hi.hi + hi.lo + lo.hi); T = 3 the
+// six-product split. The complex contraction step arrives here as one real GEMM (the caller
+// embedded the complex operand as [[Re,-Im],[Im,Re]]).
 //
 // Why promotion: the tensor core's FP32 accumulation truncates. Measured on GB300 with positive
 // operands, the mean relative error of a TMEM accumulation over K is about -(K/8) * 2^-24 (one
-// half-ulp per MMA instruction, always toward zero), so a long K yields a bias far above what
-// round-to-nearest FP32 gives. Here the leading pass of every 128-byte K block is written into
-// fresh TMEM partial accumulators -- one per K slice (SL slices of 4/SL instructions each) -- and
-// the epilogue warps add those partials into FP32 registers with round-to-nearest, double
-// buffered so draining one block overlaps the MMAs of the next. The correction passes accumulate
-// in one TMEM region over the whole K; their truncation bias is scaled down by the split ratio.
+// half-ulp per MMA instruction, always toward zero), a bias far above what round-to-nearest FP32
+// gives. Here every 128-byte K block is accumulated into fresh TMEM partials, two slices of two
+// leading-term instructions each; the small correction products of the block are issued first
+// into slice 0 (while its magnitude is still small), and the epilogue warps add both slices into
+// FP32 registers with round-to-nearest. Partials are double buffered (2 blocks x 2 slices x BN
+// columns = 512 TMEM columns at BN = 128), so draining one block overlaps the MMAs of the next.
 //
-// Kernel structure (one CTA per 128 x BN output tile, 192 threads):
-//   warp 0, lane 0 : TMA producer -- 2D tiled loads of A (128 rows x 128 B) and B (BN rows x 128 B)
-//                    with 128-byte swizzle into a ring of shared-memory stages;
+// Kernel structure (one CTA per 128 x BN output tile, 320 threads):
+//   warp 0, lane 0 : TMA producer -- per K block, the T terms of the A tile (128 rows x 128 B) and
+//                    of the B tile (BN rows x 128 B), 128-byte swizzle, loaded once each into one
+//                    shared-memory slot of a ring (mbarrier expect-tx / complete-tx);
 //   warp 1         : allocates TMEM; lane 0 issues tcgen05.mma (M=128, N=BN, 32 B of K each) and
-//                    tcgen05.commit to release stages and hand partials to the epilogue;
-//   warps 2..5     : epilogue -- tcgen05.ld of the partials (lane quarter = warp % 4), FP32
-//                    round-to-nearest accumulation in registers, FP64 store of C.
+//                    tcgen05.commit to release slots and hand partials to the epilogue;
+//   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
+//                    the BN columns: tcgen05.ld, FP32 round-to-nearest accumulation in registers,
+//                    FP64 store of C.
 // Every wait is bounded by the global timer (2 s); on expiry the kernel records a status code,
 // stops issuing work, releases TMEM and returns, so the host sees AJF_E_TIMEOUT instead of a hang.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -37,22 +40,24 @@
 namespace ajf {
 namespace {
 
-constexpr int kBM = 128;            // rows per tile (UMMA M)
-constexpr int kRowBytes = 128;      // bytes of K per stage row (one 128-byte swizzle span)
-constexpr int kStages = 6;
-constexpr int kThreads = 192;
-constexpr int kMaxPass = 6;
+constexpr int kBM = 128;             // rows per tile (UMMA M)
+constexpr int kRowBytes = 128;       // bytes of K per tile row (one 128-byte swizzle span)
+constexpr int kMaxSlots = 6;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kMaxTerms = 3;
+constexpr uint32_t kSmemBudget = 192 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct TcParams {
-  CUtensorMap amap[kMaxPass];
-  CUtensorMap bmap[kMaxPass];
+  CUtensorMap amap[kMaxTerms];
+  CUtensorMap bmap[kMaxTerms];
   double* C;
   int* status;
   int64_t N;
-  int32_t npass, kblocks, ntn, pad;
+  int32_t terms, kblocks, ntn, slots;
   uint32_t idesc;
-  uint32_t stage_bytes;
+  uint32_t slot_bytes;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -143,54 +148,46 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN, int SL>
-__host__ __device__ constexpr uint32_t tmem_cols() {
-  constexpr int need = (2 * SL + 1) * BN;
-  return need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
-}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int BN, int SL, bool kBF16>
+template <int BN, bool kBF16>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
-  static_assert((2 * SL + 1) * BN <= 512, "TMEM columns");
-  static_assert(SL == 1 || SL == 2 || SL == 4, "slices");
+  static_assert(BN == 32 || BN == 64 || BN == 128, "tile width");
+  constexpr uint32_t ncols = 4 * BN;  // 2 buffers x 2 slices
+  constexpr int HALF = BN / 2;        // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr uint32_t a_bytes = kBM * kRowBytes;
-  constexpr uint32_t ncols = tmem_cols<BN, SL>();
-  uint8_t* bars = smem + kStages * p.stage_bytes;
+  constexpr uint32_t a_bytes = kBM * kRowBytes, b_bytes = BN * kRowBytes;
+  const int S = p.slots, T = p.terms;
+  uint8_t* bars = smem + S * p.slot_bytes;
   const uint32_t full0 = smem_u32(bars);
-  const uint32_t empty0 = full0 + 8 * kStages;
-  const uint32_t accf0 = empty0 + 8 * kStages;  // partial buffer b ready (MMA -> epilogue)
-  const uint32_t acce0 = accf0 + 16;            // partial buffer b drained (epilogue -> MMA)
-  const uint32_t done_bar = acce0 + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kStages + 40);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kStages + 44);
+  const uint32_t empty0 = full0 + 8 * kMaxSlots;
+  const uint32_t accf0 = empty0 + 8 * kMaxSlots;  // partial buffer b ready (MMA -> epilogue)
+  const uint32_t acce0 = accf0 + 16;              // partial buffer b drained (epilogue -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 32);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 36);
   const int64_t m0 = static_cast<int64_t>(blockIdx.x / p.ntn) * kBM;
   const int64_t n0 = static_cast<int64_t>(blockIdx.x % p.ntn) * BN;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 4);
+      mbar_init(acce0 + 8 * b, kEpiWarps);
     }
-    mbar_init(done_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -204,74 +201,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int npass = p.npass, kblocks = p.kblocks;
-  const uint32_t corr_col = 2 * SL * BN;
+  const int kblocks = p.kblocks;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: iterations (k block, pass), pass fastest
-    const int iters = kblocks * npass;
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % kStages;
-      const uint32_t ph = static_cast<uint32_t>(it / kStages) & 1u;
+    // ---- TMA producer: one slot per K block holds every term of A and B
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % S;
+      const uint32_t ph = static_cast<uint32_t>(kb / S) & 1u;
       if (*abort_flag || !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, 11)) {
         *abort_flag = 1;
         break;
       }
-      const int kb = it / npass, pass = it % npass;
-      const uint32_t sa = smem_u32(smem + s * p.stage_bytes);
-      const uint32_t sb = sa + a_bytes;
+      const uint32_t base = smem_u32(smem + s * p.slot_bytes);
       const int32_t kx = kb * (kRowBytes / (kBF16 ? 2 : 4));
-      mbar_expect_tx(full0 + 8 * s, a_bytes + static_cast<uint32_t>(BN) * kRowBytes);
-      tma_load_2d(sa, &p.amap[pass], kx, static_cast<int32_t>(m0), full0 + 8 * s);
-      tma_load_2d(sb, &p.bmap[pass], kx, static_cast<int32_t>(n0), full0 + 8 * s);
+      mbar_expect_tx(full0 + 8 * s, static_cast<uint32_t>(T) * (a_bytes + b_bytes));
+      for (int t = 0; t < T; ++t) {
+        const uint32_t sa = base + t * (a_bytes + b_bytes);
+        tma_load_2d(sa, &p.amap[t], kx, static_cast<int32_t>(m0), full0 + 8 * s);
+        tma_load_2d(sa + a_bytes, &p.bmap[t], kx, static_cast<int32_t>(n0), full0 + 8 * s);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    bool ok = true, corr_started = false;
-    int it = 0;
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
+    bool ok = true;
+    for (int kb = 0; kb < kblocks; ++kb) {
       const int b = kb & 1;
-      if (*abort_flag || !mbar_wait(acce0 + 8 * b, (static_cast<uint32_t>(kb >> 1) & 1u) ^ 1u, p.status, 14)) {
+      const int s = kb % S;
+      if (*abort_flag || !mbar_wait(acce0 + 8 * b, (static_cast<uint32_t>(kb >> 1) & 1u) ^ 1u, p.status, 14) ||
+          !mbar_wait(full0 + 8 * s, static_cast<uint32_t>(kb / S) & 1u, p.status, 12)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int pass = 0; pass < npass; ++pass, ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = static_cast<uint32_t>(it / kStages) & 1u;
-        if (*abort_flag || !mbar_wait(full0 + 8 * s, ph, p.status, 12)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(smem + s * p.stage_bytes);
-        const uint32_t sb = sa + a_bytes;
+      const uint32_t base = smem_u32(smem + s * p.slot_bytes);
+      const uint32_t slice0 = tmem + static_cast<uint32_t>((2 * b) * BN);
+      const uint32_t slice1 = slice0 + BN;
+      uint32_t acc0 = 0;
+      // correction products (i + j >= 1), smallest first, into slice 0
+      for (int sum = T - 1; sum >= 1; --sum)
+        for (int i = 0; i <= sum; ++i) {
+          const int j = sum - i;
+          const uint32_t sa = base + i * (a_bytes + b_bytes);
+          const uint32_t sb = base + j * (a_bytes + b_bytes) + a_bytes;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {  // 4 instructions x 32 bytes of K
-          const uint64_t da = smem_desc(sa + 32 * kk), db = smem_desc(sb + 32 * kk);
-          if (pass == 0) {
-            constexpr int per = 4 / SL;  // instructions per slice
-            const uint32_t col = static_cast<uint32_t>((b * SL + kk / per) * BN);
-            mma<kBF16>(tmem + col, da, db, p.idesc, (kk % per) != 0 ? 1u : 0u);
-          } else {
-            mma<kBF16>(tmem + corr_col, da, db, p.idesc, corr_started ? 1u : 0u);
-            corr_started = true;
+          for (int kk = 0; kk < 4; ++kk) {
+            mma<kBF16>(slice0, smem_desc(sa + 32 * kk), smem_desc(sb + 32 * kk), p.idesc, acc0);
+            acc0 = 1;
           }
         }
-        mma_commit(empty0 + 8 * s);
+      // leading product: instructions 0-1 into slice 0, 2-3 into slice 1
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t da = smem_desc(base + 32 * kk), db = smem_desc(base + a_bytes + 32 * kk);
+        if (kk < 2) {
+          mma<kBF16>(slice0, da, db, p.idesc, acc0);
+          acc0 = 1;
+        } else {
+          mma<kBF16>(slice1, da, db, p.idesc, kk == 3 ? 1u : 0u);
+        }
       }
-      if (!ok) break;
+      mma_commit(empty0 + 8 * s);
       mma_commit(accf0 + 8 * b);
     }
-    if (ok) mma_commit(done_bar);
-    else *abort_flag = 1;
+    if (!ok) *abort_flag = 1;
   } else if (warp >= 2) {
     // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP64
-    const int q = warp & 3;
+    const int q = warp & 3, h = (warp - 2) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
-    float acc[BN];
+    float acc[HALF];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+    for (int j = 0; j < HALF; ++j) acc[j] = 0.0f;
     bool ok = true;
     for (int kb = 0; kb < kblocks; ++kb) {
       const int b = kb & 1;
@@ -284,39 +283,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int sl = 0; sl < SL; ++sl) {
+      for (int sl = 0; sl < 2; ++sl) {
+        const uint32_t col = static_cast<uint32_t>((2 * b + sl) * BN + h * HALF);
+        uint32_t r[HALF];
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(tmem + lane_base + static_cast<uint32_t>((b * SL + sl) * BN + c0), r);
+        for (int c0 = 0; c0 < HALF; c0 += 16)
+          tmem_ld16(tmem + lane_base + col + c0, *reinterpret_cast<uint32_t(*)[16]>(&r[c0]));
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
-        }
+        for (int j = 0; j < HALF; ++j) acc[j] += __uint_as_float(r[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
-    if (ok) {
-      int w = 1;
-      if (lane == 0) w = mbar_wait(done_bar, 0, p.status, 15) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, w, 0) != 0;
-    }
     if (ok && !*abort_flag) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (npass > 1) {
-#pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(tmem + lane_base + corr_col + static_cast<uint32_t>(c0), r);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
-        }
-      }
       const int64_t row = m0 + 32 * q + lane;
-      double2* dst = reinterpret_cast<double2*>(p.C + row * p.N + n0);
+      double2* dst = reinterpret_cast<double2*>(p.C + row * p.N + n0 + h * HALF);
 #pragma unroll
-      for (int j = 0; j < BN / 2; ++j)
+      for (int j = 0; j < HALF / 2; ++j)
         dst[j] = make_double2(static_cast<double>(acc[2 * j]), static_cast<double>(acc[2 * j + 1]));
     } else {
       *abort_flag = 1;
@@ -360,37 +345,23 @@ bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tile variant: (BN, slices). 0: (128, 1), 1: (64, 2), 2: (32, 4). Split modes (npass > 1) use
-// two slices per 128-byte K block (measured mean bias -6e-8 relative on positive data, against
-// -1.2e-7 with one slice); the one-pass TF32 mode, whose rounding error is far larger anyway,
-// uses the widest tile. AJF_TC_VARIANT overrides the choice (tuning experiments).
-int variant_for(int64_t N, int npass) {
-  static int forced = [] {
-    const char* e = std::getenv("AJF_TC_VARIANT");
-    return e ? std::atoi(e) : -1;
-  }();
-  int v = forced >= 0 && forced <= 2 ? forced : (npass > 1 ? 1 : 0);
-  const int bn = v == 0 ? 128 : (v == 1 ? 64 : 32);
-  if (N < bn) v = N >= 64 ? 1 : 2;
-  return v;
-}
-
-template <int BN, int SL, bool BF16>
-cudaError_t launch_variant(const TcParams& p, int64_t M, int64_t N, cudaStream_t s) {
-  const size_t stage = size_t(kBM) * kRowBytes + size_t(BN) * kRowBytes;
-  const size_t smem = kStages * stage + 1024 + 1024;
+template <int BN, bool BF16>
+cudaError_t launch_tile(TcParams p, int64_t M, int64_t N, cudaStream_t s) {
+  p.slot_bytes = static_cast<uint32_t>(p.terms) * (kBM + BN) * kRowBytes;
+  p.slots = static_cast<int32_t>(kSmemBudget / p.slot_bytes);
+  if (p.slots > kMaxSlots) p.slots = kMaxSlots;
+  if (p.slots < 1) return cudaErrorInvalidValue;
+  const size_t smem = size_t(p.slots) * p.slot_bytes + 1024 /* barriers */ + 1024 /* alignment */;
   const int64_t tiles = (M / kBM) * (N / BN);
   if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  TcParams q = p;
-  q.ntn = static_cast<int32_t>(N / BN);
-  q.stage_bytes = static_cast<uint32_t>(stage);
+  p.ntn = static_cast<int32_t>(N / BN);
   const uint32_t fmt = BF16 ? 1u : 2u;  // A/B type: TF32 = 2, BF16 = 1; D = F32; both K-major
-  q.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
+  p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
             (static_cast<uint32_t>(kBM >> 4) << 24);
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, SL, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_gemm_tc<BN, SL, BF16><<<static_cast<unsigned>(tiles), kThreads, smem, s>>>(q);
+  k_gemm_tc<BN, BF16><<<static_cast<unsigned>(tiles), kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -402,31 +373,30 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind) {
          M * N <= (int64_t(1) << 40);
 }
 
-cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int npass, double* C, int64_t M,
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s) {
-  if (!tc_gemm_supported(M, N, K, kind) || npass < 1 || npass > kMaxPass) return cudaErrorNotSupported;
+  if (!tc_gemm_supported(M, N, K, kind) || terms < 1 || terms > kMaxTerms) return cudaErrorNotSupported;
   const bool bf16 = kind == 1;
-  const int v = variant_for(N, npass);
-  const uint32_t bn = v == 0 ? 128 : (v == 1 ? 64 : 32);
+  const int bn = N >= 128 ? 128 : static_cast<int>(N);
   TcParams p;
   std::memset(&p, 0, sizeof(p));
-  for (int i = 0; i < npass; ++i) {
-    if (!make_map(&p.amap[i], base + a_off[i], M, K, kBM, bf16)) return cudaErrorInvalidValue;
-    if (!make_map(&p.bmap[i], base + b_off[i], N, K, bn, bf16)) return cudaErrorInvalidValue;
+  for (int t = 0; t < terms; ++t) {
+    if (!make_map(&p.amap[t], base + a_off[t], M, K, kBM, bf16)) return cudaErrorInvalidValue;
+    if (!make_map(&p.bmap[t], base + b_off[t], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
   }
   p.C = C;
   p.status = d_status;
   p.N = N;
-  p.npass = npass;
+  p.terms = terms;
   p.kblocks = static_cast<int32_t>(K / (kRowBytes / (bf16 ? 2 : 4)));
   if (bf16) {
-    if (v == 0) return launch_variant<128, 1, true>(p, M, N, s);
-    if (v == 1) return launch_variant<64, 2, true>(p, M, N, s);
-    return launch_variant<32, 4, true>(p, M, N, s);
+    if (bn == 128) return launch_tile<128, true>(p, M, N, s);
+    if (bn == 64) return launch_tile<64, true>(p, M, N, s);
+    return launch_tile<32, true>(p, M, N, s);
   }
-  if (v == 0) return launch_variant<128, 1, false>(p, M, N, s);
-  if (v == 1) return launch_variant<64, 2, false>(p, M, N, s);
-  return launch_variant<32, 4, false>(p, M, N, s);
+  if (bn == 128) return launch_tile<128, false>(p, M, N, s);
+  if (bn == 64) return launch_tile<64, false>(p, M, N, s);
+  return launch_tile<32, false>(p, M, N, s);
 }
 
 }  // namespace ajf
