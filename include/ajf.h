@@ -188,6 +188,27 @@ ajf_status ajf_fidelity_alg1(ajf_ctx *ctx, double eps, ajf_result *out);
  * requiring ajf_plan(ctx, 2, ...). */
 ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);
 
+/* Evaluate a planned context without allocating anything (the paper has no counterpart).
+ * For callers that cannot allocate device memory: code whose device memory is reserved up front
+ * and owned by another allocator, processes running under a hard device-memory cap, or paths
+ * that must not enter the allocator (its latency and failure modes) once set up.
+ * It runs the same device program as ajf_fidelity_alg1 (alg = 1) / ajf_fidelity_alg2 (alg = 2),
+ * with the same results, but in a fixed device arena of 64 MiB that libajf declares as a static
+ * __device__ array: every GPU that loads the library holds those 64 MiB until the process exits.
+ * It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine; inputs are copied
+ * from the context's host memory and the result is read back synchronously. The context's own
+ * arena, CUDA graph and Alg. I trace buffer are not touched (ajf_alg1_traces still returns the
+ * last ajf_fidelity_alg1 result).
+ * The first call on a device looks up the arena's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture on the device.
+ * All calls on a device share the one arena and it keeps the last call's contents (the call
+ * rewrites everything it reads, and zeroes its status words first). Calls whose device work
+ * overlaps -- from different threads or different streams of one device -- race on the arena
+ * and must be serialised by the caller.
+ * Errors: AJF_E_ARG (alg, eps or out), AJF_E_STATE (no plan for `alg`, host-only context),
+ * AJF_E_NOMEM (the plan's arena, ajf_workspace_size, exceeds 64 MiB), AJF_E_CUDA, AJF_E_TIMEOUT. */
+ajf_status ajf_fidelity_noalloc(ajf_ctx *ctx, int alg, double eps, ajf_result *out);
+
 /* After ajf_fidelity_alg1: copy the traces t_i = tr(U^dagger E_i) to `traces` (host, 2*count
  * doubles, interleaved), in enumeration order (lexicographic over noises in the order added,
  * last noise fastest; Sec. IV-A). count must equal prod_k n_k.

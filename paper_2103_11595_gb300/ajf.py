@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "ajf_fidelity_alg1_batch": (I32, [ctypes.POINTER(P), ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_version": (ctypes.c_char_p, []),
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
+            "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
         }
@@ -196,6 +197,14 @@ def ajf_fidelity_alg1(ctx, eps: float = -1.0) -> dict:
 def ajf_fidelity_alg2(ctx, eps: float = -1.0) -> dict:
     r = Result()
     _check(ctx, lib().ajf_fidelity_alg2(ctx, float(eps), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ajf_fidelity_noalloc(ctx, alg: int, eps: float = -1.0) -> dict:
+    """Same evaluation as ajf_fidelity_alg1/alg2, in the library's fixed 64 MiB device arena,
+    without any allocation (for callers that cannot allocate device memory)."""
+    r = Result()
+    _check(ctx, lib().ajf_fidelity_noalloc(ctx, int(alg), float(eps), ctypes.byref(r)))
     return r.as_dict()
 
 

@@ -701,6 +701,57 @@ ajf_status ajf_fidelity_alg1(ajf_ctx* c, double eps, ajf_result* out) { return f
 
 ajf_status ajf_fidelity_alg2(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 2, eps, out); }
 
+ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  if (!c) return AJF_E_ARG;
+  if (!out) return fail(c, AJF_E_ARG, "out is NULL");
+  if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 1 or 2");
+  if (!c->planned || c->alg != alg) return fail(c, AJF_E_STATE, "no Alg. " + std::to_string(alg) + " plan");
+  if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
+  if (eps > 1.0) return fail(c, AJF_E_ARG, "eps > 1");
+  const Program& P = c->prog;
+  if (P.arena_bytes > kStaticArenaBytes)
+    return fail(c, AJF_E_NOMEM, "plan needs " + std::to_string(P.arena_bytes) + " bytes of device memory; the fixed " +
+                                    "arena of ajf_fidelity_noalloc holds " + std::to_string(kStaticArenaBytes) + " bytes");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  void* sa = nullptr;
+  CUDA_TRY(c, static_arena_address(c->device, &sa));
+  // Run the same device program with the fixed arena as its base; the context's own arena, its
+  // CUDA graph and its profiling state are left untouched.
+  char* const own_arena = c->arena;
+  const bool own_profiling = c->profiling;
+  c->arena = static_cast<char*>(sa);
+  c->profiling = false;
+  ajf_status st = AJF_OK;
+  double res[3] = {0, 0, 0};
+  int status[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(c->arena + P.off_desc, c->desc_image.data(), c->desc_image.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && P.input_bytes)
+    e = cudaMemcpyAsync(c->arena + P.off_inputs, c->in.packed.data(), P.input_bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->arena + P.off_status, 0, 16 * sizeof(int32_t), c->stream);
+  if (e != cudaSuccess) st = cuda_fail(c, e, "ajf_fidelity_noalloc upload");
+  if (st == AJF_OK) st = enqueue_program(c, c->stream);
+  if (st == AJF_OK) {
+    e = cudaMemcpyAsync(res, c->arena + P.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(status, c->arena + P.off_status, sizeof(status), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "ajf_fidelity_noalloc read-back");
+  }
+  c->arena = own_arena;
+  c->profiling = own_profiling;
+  if (st != AJF_OK) return st;
+  if (status[0] != 0)
+    return fail(c, AJF_E_TIMEOUT, "a bounded device-side wait expired (code " + std::to_string(status[0]) + ")");
+  out->S = res[0];
+  out->F = res[1];
+  out->one_minus_F = res[2];
+  out->traces_done = alg == 1 ? real_combinations(c) : 0;
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->reserved = 0;
+  return AJF_OK;
+}
+
 ajf_status ajf_alg1_traces(ajf_ctx* c, double* traces, int64_t count) {
   if (!c) return AJF_E_ARG;
   if (!c->have_alg1 || !c->planned || c->alg != 1) return fail(c, AJF_E_STATE, "no Alg. I result");
