@@ -233,6 +233,21 @@ ajf_status ajf_upload(ajf_ctx *ctx);
  * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, mixed device or precision), AJF_E_STATE. */
 ajf_status ajf_fidelity_alg1_batch(ajf_ctx *const *ctxs, int n_ctx, double eps, ajf_result *out);
 
+/* One kernel launch of a lowered plan, in the order an evaluation enqueues them. kind uses the
+ * classes of ajf_kernel_stats (0 leaves ... 6 final); for GEMM launches M, N, K are the real GEMM
+ * dimensions (2M', N', 2K' of the complex step) and terms the split terms (tensor cores). */
+typedef struct ajf_launch_info {
+  int32_t kind;
+  int32_t terms;
+  int64_t M, N, K;
+  double flops;        /* algorithmic flops of the complex step(s) the launch carries out */
+  double bytes;        /* algorithmic bytes of those steps                                 */
+} ajf_launch_info;
+
+/* List the launches of the current plan (valid after ajf_plan, also on host-only contexts):
+ * up to `cap` records into `out`, the total count into *n. Errors: AJF_E_ARG, AJF_E_STATE. */
+ajf_status ajf_plan_launches(const ajf_ctx *ctx, ajf_launch_info *out, int cap, int *n);
+
 /* Turn per-launch timing on (1) or off (0) and clear the counters. While on, every run records
  * CUDA events around each launch (CUDA-graph replay is bypassed). */
 ajf_status ajf_profile_enable(ajf_ctx *ctx, int on);

@@ -52,6 +52,11 @@ class KernelStats(ctypes.Structure):
 KERNEL_CLASSES = ["leaves", "small", "splitk", "gather", "gemm_simt", "gemm_tc", "final"]
 
 
+class LaunchInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("terms", ctypes.c_int32), ("M", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("K", ctypes.c_int64), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("F", ctypes.c_double), ("one_minus_F", ctypes.c_double), ("S", ctypes.c_double),
                 ("traces_done", ctypes.c_int64), ("equivalent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -95,6 +100,7 @@ def lib() -> ctypes.CDLL:
             "ajf_version": (ctypes.c_char_p, []),
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
+            "ajf_plan_launches": (I32, [P, ctypes.POINTER(LaunchInfo), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
         }
@@ -239,6 +245,15 @@ def ajf_selftest_gemm(device: int, kind: int, A: np.ndarray, B: np.ndarray, M: i
     if st != AJF_OK:
         raise AjfError(st, "ajf_selftest_gemm failed")
     return C
+
+
+def ajf_plan_launches(ctx) -> list:
+    n = ctypes.c_int()
+    _check(ctx, lib().ajf_plan_launches(ctx, None, 0, ctypes.byref(n)))
+    arr = (LaunchInfo * max(1, n.value))()
+    _check(ctx, lib().ajf_plan_launches(ctx, arr, n.value, ctypes.byref(n)))
+    return [{"kind": KERNEL_CLASSES[a.kind], "terms": a.terms, "M": a.M, "N": a.N, "K": a.K, "flops": a.flops,
+             "bytes": a.bytes} for a in arr[:n.value]]
 
 
 def ajf_profile_enable(ctx, on: bool = True) -> None:

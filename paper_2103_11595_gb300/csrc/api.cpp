@@ -833,6 +833,35 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
   return st;
 }
 
+ajf_status ajf_plan_launches(const ajf_ctx* c, ajf_launch_info* out, int cap, int* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && !out)) return AJF_E_ARG;
+  if (!c->planned) return AJF_E_STATE;
+  std::vector<ajf_launch_info> v;
+  auto add = [&](int kind, int terms, int64_t M, int64_t N, int64_t K, double f, double b) {
+    ajf_launch_info li;
+    li.kind = kind;
+    li.terms = terms;
+    li.M = M;
+    li.N = N;
+    li.K = K;
+    li.flops = f;
+    li.bytes = b;
+    v.push_back(li);
+  };
+  add(0, 0, 0, 0, 0, 0, 0);
+  static const int kClass[5] = {1, 2, 3, 4, 5};
+  for (const Launch& ln : c->prog.launches) {
+    add(kClass[ln.kind], ln.kind == LK_GEMM_TC ? ln.npass : (ln.kind == LK_GEMM_SIMT ? 1 : 0), ln.M, ln.N, ln.K,
+        ln.flops, ln.bytes);
+    if (ln.kind == LK_SPLITK) add(2, 0, 0, 0, 0, 0, 0);  // the deterministic final-sum launch
+  }
+  add(6, 0, 0, 0, 0, 0, 0);
+  add(6, 0, 0, 0, 0, 0, 0);
+  *n = static_cast<int>(v.size());
+  for (int i = 0; i < cap && i < static_cast<int>(v.size()); ++i) out[i] = v[i];
+  return AJF_OK;
+}
+
 ajf_status ajf_profile_enable(ajf_ctx* c, int on) {
   if (!c) return AJF_E_ARG;
   if (c->device >= 0) {

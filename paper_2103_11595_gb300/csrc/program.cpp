@@ -359,6 +359,9 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
                                               int64_t(1) << std::max(0, I.n + I.k - 10));
       lp.blocks = static_cast<int>(std::min<int64_t>(std::max<int64_t>(tiles, 1), 2048));
       lp.smem = std::max(perm_table_bytes(px), perm_table_bytes(py));
+      // gather traffic: both complex FP64 operands read once, every operand term written once
+      lp.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) + std::ldexp(1.0, static_cast<int>(ly.size()))) * 16.0 +
+                 static_cast<double>(gterms) * static_cast<double>(xbytes + ybytes);
       P.perms.push_back(px);
       P.perms.push_back(py);
       P.launches.push_back(lp);

@@ -16,7 +16,7 @@ from paper_2103_11595_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-6, "bf16x6": 1e-6}
+TOL = {"f64": 1e-12, "f32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -237,27 +237,64 @@ def mid0_oracle():
     return inst, network.alg2_fidelity(inst, order="minfill")
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "tf32x3", "bf16x6"])
 def test_mid_config_alg2(mid0_oracle, precision):
     """n=16 line, 200 gates, 10 mixed noises: Alg. II on the GPU vs the oracle's own network."""
     inst, ref = mid0_oracle
     r, _, info = run(inst, 2, precision, trials=16)
     assert info["width"] <= 28
-    if precision in ("bf16x3", "bf16x6"):
+    if precision in ("tf32x3", "bf16x6"):
         assert info["n_tc_gemms"] > 0
     check(r, ref, TOL[precision])
 
 
-@pytest.mark.parametrize("precision,bound", [("tf32", 1e-3), ("tf32x3", 3e-6)])
-def test_mid_config_tf32_error_is_bounded(mid0_oracle, precision, bound):
-    """One-pass TF32 (10-bit mantissa) cannot reach 1e-6; the 22-bit TF32 split lands near 1e-6
-    (measured 0.9e-6 .. 1.1e-6 on mid seeds 0-2). Both errors are measured and bounded."""
+@pytest.mark.parametrize("precision,bound", [("tf32", 1e-3), ("bf16x3", 5e-6)])
+def test_mid_config_low_precision_error_is_bounded(mid0_oracle, precision, bound):
+    """One-pass TF32 (11 significant bits) and the two-term bf16 split (16 bits) are not FP32-class
+    operand precisions; their errors are measured and bounded (bf16x3 reached 1.2e-6 .. 3.9e-6 on
+    validation circuits)."""
     inst, ref = mid0_oracle
     r, _, info = run(inst, 2, precision, trials=16)
     assert info["n_tc_gemms"] > 0
     err = abs(r["F"] - ref["F"])
     print(f"{precision}: |dF| = {err:.3e}")
     assert err <= bound
+
+
+@pytest.fixture(scope="module")
+def precision_oracle():
+    inst = W.precision(0, depth=4)
+    return inst, network.alg2_fidelity(inst, order="minfill")
+
+
+@pytest.mark.parametrize("precision", ["f64", "tf32x3", "bf16x6"])
+def test_precision_config_alg2(precision_oracle, precision):
+    """4x5 grid, depth-4 brickwork of Haar SU(4), depolarising on both qubits of every gate
+    (62 noises): Alg. II at width 24 against the oracle; split modes within 1e-6."""
+    inst, ref = precision_oracle
+    r, _, info = run(inst, 2, precision, trials=16)
+    if precision != "f64":
+        assert info["n_tc_gemms"] > 0
+    check(r, ref, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x6"])
+def test_batching_circuit_alg1(precision):
+    """A circuit of the batching workload (n=14, 296 gates, 6 depolarising noises, 4096 traces):
+    Alg. I on tensor cores against Alg. I and Alg. II in FP64; two traces against the oracle."""
+    inst = W.batching_circuit(1)
+    r64, t64, _ = run(inst, 1, "f64", trials=8)
+    r2, _, _ = run(inst, 2, "f64", trials=8)
+    assert abs(r64["F"] - r2["F"]) <= 1e-12
+    r, t, info = run(inst, 1, precision, trials=8)
+    assert info["n_tc_gemms"] > 0
+    assert abs(r["F"] - r64["F"]) <= 1e-6
+    for choice in ([0] * 6, [1, 0, 2, 0, 0, 3]):
+        idx = 0
+        for c in choice:
+            idx = idx * 4 + c
+        val = network.alg1_trace(inst, choice, order="minfill", rng=None)
+        assert abs(t64[idx] - val) <= 1e-12 * 2 ** inst.n
 
 
 def test_mid_config_alg1_vs_alg2(mid0_oracle):

@@ -43,7 +43,9 @@ def split_ref(A, B):
 
 
 SHAPES = [(128, 32, 32, 1), (128, 64, 64, 1), (256, 128, 128, 2), (128, 256, 64, 2), (512, 512, 256, 3),
-          (1024, 256, 512, 1), (384, 1024, 96, 2)]
+          (1024, 256, 512, 1), (512, 1024, 128, 2),
+          # tiles overhanging M, N or K (TMA zero fill, guarded stores)
+          (32, 16, 16, 1), (64, 512, 16, 2), (32, 1024, 8, 1), (128, 16, 64, 3)]
 
 
 @pytest.mark.parametrize("M,N,K,T", SHAPES)
@@ -56,7 +58,8 @@ def test_tf32_gemm(M, N, K, T):
     assert np.all(np.abs(C - ref) <= 4 * K * 2.0 ** -23 * bound + 1e-30)
 
 
-@pytest.mark.parametrize("M,N,K,T", [(128, 32, 64, 1), (256, 128, 128, 2), (512, 256, 256, 3), (128, 64, 1024, 3)])
+@pytest.mark.parametrize("M,N,K,T", [(128, 32, 64, 1), (256, 128, 128, 2), (512, 256, 256, 3), (128, 64, 1024, 3),
+                                     (64, 512, 32, 2), (32, 16, 16, 2), (512, 65536 // 64, 32, 2)])
 def test_bf16_gemm(M, N, K, T):
     rng = np.random.default_rng(7 * M + N + K)
     A = bf16_bits(rng.standard_normal((T, M, K)))
@@ -84,8 +87,8 @@ def test_split_tf32_has_no_k_growing_bias(K):
 
 
 def test_unsupported_shape_is_reported():
-    A = np.zeros((1, 64, 32), dtype=np.float32)
+    A = np.zeros((1, 16, 32), dtype=np.float32)
     B = np.zeros((1, 32, 32), dtype=np.float32)
     with pytest.raises(ajf.AjfError) as e:
-        ajf.ajf_selftest_gemm(0, 0, A, B, 64, 32, 32)
+        ajf.ajf_selftest_gemm(0, 0, A, B, 16, 32, 32)
     assert e.value.status == ajf.AJF_E_UNSUPPORTED
