@@ -267,6 +267,24 @@ ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
 ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t N, int64_t K, const void *A,
                              const void *B, double *C);
 
+/* Alg. I (alg = 1) or Alg. II (alg = 2) over several contexts at once: each context's device
+ * program is enqueued on that context's own stream (give each context its own stream for the
+ * circuits to overlap on the GPU), then all results are read back; out[i] receives context i's.
+ * Contexts may differ in circuit size and precision. Sec. IV-A notes that the traces -- and so
+ * the circuits -- are independent.
+ * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, bad alg, contexts on different devices),
+ * AJF_E_STATE (a context without a plan for `alg`), plus those of ajf_fidelity_alg1/alg2. */
+ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out);
+
+/* Self-test of the failure path of the device-side waits (no paper counterpart; used by the test
+ * suite): runs the tensor-core GEMM kernel on a 128 x 32 x 32 problem with every wait bounded by
+ * `wait_ms` and its producer told to issue no loads, so nothing ever completes the barriers the
+ * other warps wait on. The kernel must give up after the bound, record which wait expired in
+ * *code, release its TMEM and return; the device stays usable.
+ * Returns AJF_E_TIMEOUT (the expected outcome, *code != 0) or AJF_OK (the waits did not report);
+ * AJF_E_ARG (wait_ms not in (0, 10000], code NULL), AJF_E_NOMEM, AJF_E_CUDA. */
+ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t *code);
+
 /* Library version string, e.g. "ajf 0.1 sm_103a". */
 const char *ajf_version(void);
 

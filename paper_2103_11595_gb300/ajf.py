@@ -97,9 +97,11 @@ def lib() -> ctypes.CDLL:
             "ajf_launch": (I32, [P, P]),
             "ajf_upload": (I32, [P]),
             "ajf_fidelity_alg1_batch": (I32, [ctypes.POINTER(P), ctypes.c_int, D, ctypes.POINTER(Result)]),
+            "ajf_fidelity_batch": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_version": (ctypes.c_char_p, []),
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
+            "ajf_selftest_wait_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
             "ajf_plan_launches": (I32, [P, ctypes.POINTER(LaunchInfo), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
@@ -256,6 +258,14 @@ def ajf_plan_launches(ctx) -> list:
              "bytes": a.bytes} for a in arr[:n.value]]
 
 
+def ajf_selftest_wait_timeout(device: int, wait_ms: float) -> tuple:
+    """Returns (status, code): AJF_E_TIMEOUT and the expired wait's code when the bounded-wait
+    failure path works."""
+    code = ctypes.c_int32()
+    st = lib().ajf_selftest_wait_timeout(device, float(wait_ms), ctypes.byref(code))
+    return st, code.value
+
+
 def ajf_profile_enable(ctx, on: bool = True) -> None:
     _check(ctx, lib().ajf_profile_enable(ctx, 1 if on else 0))
 
@@ -265,6 +275,16 @@ def ajf_profile_read(ctx) -> dict:
     _check(ctx, lib().ajf_profile_read(ctx, arr, len(KERNEL_CLASSES)))
     return {name: {"launches": s.launches, "ms": s.ms, "flops": s.flops, "bytes": s.bytes}
             for name, s in zip(KERNEL_CLASSES, arr)}
+
+
+def ajf_fidelity_batch(ctxs: Sequence, alg: int, eps: float = -1.0) -> list:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    res = (Result * len(ctxs))()
+    st = lib().ajf_fidelity_batch(arr, len(ctxs), int(alg), float(eps), res)
+    if st != AJF_OK:
+        msgs = "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c))
+        raise AjfError(st, msgs)
+    return [r.as_dict() for r in res]
 
 
 # ----------------------------------------------------------------------------- marshalling helpers

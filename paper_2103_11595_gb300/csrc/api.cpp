@@ -281,9 +281,12 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
   double2* scalars = reinterpret_cast<double2*>(base + P.off_scalars);
   int* status = reinterpret_cast<int*>(base + P.off_status);
   for (const Launch& ln : P.launches) {
-    static const int kClass[5] = {1, 2, 3, 4, 5};
+    static const int kClass[6] = {1, 2, 3, 4, 5, 2};
     ProfScope ps(c, s, kClass[ln.kind], ln.flops, ln.bytes);
     switch (ln.kind) {
+      case LK_DOT:
+        e = launch_dot(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, s);
+        break;
       case LK_SMALL:
         e = launch_small(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, f64, s);
         break;
@@ -637,7 +640,7 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
   pi.planner_used = c->path.planner;
   pi.n_launches = 3;  // leaves + final pass + final sum
-  for (auto& ln : P.launches) pi.n_launches += (ln.kind == LK_SPLITK) ? 2 : 1;
+  for (auto& ln : P.launches) pi.n_launches += (ln.kind == LK_SPLITK || ln.kind == LK_DOT) ? 2 : 1;
   pi.n_tc_gemms = P.tensor_cores;
   pi.plan_cached = cached ? 1 : 0;
   pi.upload_bytes = static_cast<double>(P.desc_bytes + P.input_bytes);
@@ -849,17 +852,42 @@ ajf_status ajf_plan_launches(const ajf_ctx* c, ajf_launch_info* out, int cap, in
     v.push_back(li);
   };
   add(0, 0, 0, 0, 0, 0, 0);
-  static const int kClass[5] = {1, 2, 3, 4, 5};
+  static const int kClass[6] = {1, 2, 3, 4, 5, 2};
   for (const Launch& ln : c->prog.launches) {
     add(kClass[ln.kind], ln.kind == LK_GEMM_TC ? ln.npass : (ln.kind == LK_GEMM_SIMT ? 1 : 0), ln.M, ln.N, ln.K,
         ln.flops, ln.bytes);
-    if (ln.kind == LK_SPLITK) add(2, 0, 0, 0, 0, 0, 0);  // the deterministic final-sum launch
+    if (ln.kind == LK_SPLITK || ln.kind == LK_DOT) add(2, 0, 0, 0, 0, 0, 0);  // the deterministic final-sum launch
   }
   add(6, 0, 0, 0, 0, 0, 0);
   add(6, 0, 0, 0, 0, 0, 0);
   *n = static_cast<int>(v.size());
   for (int i = 0; i < cap && i < static_cast<int>(v.size()); ++i) out[i] = v[i];
   return AJF_OK;
+}
+
+ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t* code) {
+  if (!code || !(wait_ms > 0) || wait_ms > 10000) return AJF_E_ARG;
+  *code = 0;
+  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
+  const int64_t M = 128, N = 32, K = 32;
+  char* d = nullptr;
+  const size_t off_b = M * K * 4, off_c = off_b + N * K * 4, off_s = off_c + M * N * 8;
+  if (cudaMalloc(&d, off_s + 256) != cudaSuccess) return AJF_E_NOMEM;
+  ajf_status st = AJF_OK;
+  const int64_t ao[1] = {0}, bo[1] = {static_cast<int64_t>(off_b)};
+  if (cudaMemset(d, 0, off_s + 256) != cudaSuccess) st = AJF_E_CUDA;
+  if (st == AJF_OK &&
+      launch_gemm_tc_ex(d, ao, bo, 1, reinterpret_cast<double*>(d + off_c), M, N, K, 0, reinterpret_cast<int*>(d + off_s),
+                        0, static_cast<unsigned long long>(wait_ms * 1e6), 1) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
+  int status = 0;
+  if (st == AJF_OK && cudaMemcpy(&status, d + off_s, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = AJF_E_CUDA;
+  cudaFree(d);
+  if (st != AJF_OK) return st;
+  *code = status;
+  return status != 0 ? AJF_E_TIMEOUT : AJF_OK;
 }
 
 ajf_status ajf_profile_enable(ajf_ctx* c, int on) {
@@ -880,6 +908,45 @@ ajf_status ajf_profile_read(ajf_ctx* c, ajf_kernel_stats* stats, int cap) {
     drain_profile(c);
   }
   for (int i = 0; i < cap && i < 7; ++i) stats[i] = c->stats[i];
+  return AJF_OK;
+}
+
+ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out) {
+  if (!ctxs || n_ctx < 1 || !out || (alg != 1 && alg != 2)) return AJF_E_ARG;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return AJF_E_ARG;
+    if (ctxs[i]->device != ctxs[0]->device || ctxs[i]->device < 0)
+      return fail(ctxs[0], AJF_E_ARG, "contexts must share one device");
+    if (!ctxs[i]->planned || ctxs[i]->alg != alg)
+      return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
+    if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
+  }
+  // every context runs on its own stream so independent circuits overlap on the GPU
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!c->uploaded) {
+      ajf_status st = do_upload(c);
+      if (st != AJF_OK) return st;
+    }
+    ajf_status st = run_program(c);
+    if (st != AJF_OK) return st;
+  }
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ajf_status st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    out[i].S = res[0];
+    out[i].F = res[1];
+    out[i].one_minus_F = res[2];
+    out[i].traces_done = alg == 1 ? real_combinations(c) : 0;
+    out[i].equivalent = eps < 0 ? -1 : (res[1] > 1.0 - eps ? 1 : 0);
+    out[i].reserved = 0;
+    if (alg == 1) c->have_alg1 = true;
+  }
   return AJF_OK;
 }
 

@@ -30,7 +30,9 @@ struct StepDev {
   int32_t block0;         // first block of this step within its launch
   int32_t scalar_slot;    // >= 0: the result is a scalar written to a double2 slot (FP64)
   int32_t nsplit;         // split-K: blocks per output element
-  int32_t pad;
+  int32_t ntl;            // tiled dot: bits of a tile (<= 10)
+  int8_t tl[16];          // tiled dot: contracted-index bits of a tile, ordered by A position
+  int8_t tlb[16];         // tiled dot: the same bits ordered by B position
 };
 
 // Operand preparation for a GEMM step: gather a complex tensor into a real row-major,

@@ -197,11 +197,138 @@ __global__ void __launch_bounds__(256) k_splitk(const StepDev* __restrict__ step
   if (threadIdx.x == 0) partial[st.poff + o * st.nsplit + split] = make_double2(red_re[0], red_im[0]);
 }
 
+// Full contraction S = sum_kk A[a(kk)] B[b(kk)] of two tensors (the trace of a closed network),
+// tiled so that both operands are read along their contiguous bits. A tile fixes all contracted
+// bits but ntl of them: the ones on A's lowest positions and the ones on B's lowest positions.
+// Phase 1 stages the tile of A in shared memory in A order (lanes along A's contiguous bits);
+// phase 2 streams the tile of B in B order and multiplies with the staged A values. FP64 partial
+// sums per block; k_splitk_done adds them in a fixed order.
 template <typename T>
-__global__ void k_splitk_done(const StepDev* __restrict__ steps, int nsteps, const double2* __restrict__ partial,
-                              T* __restrict__ arena, double2* __restrict__ scalars) {
+__global__ void __launch_bounds__(256) k_dot(const StepDev* __restrict__ steps, int nsteps,
+                                             const T* __restrict__ arena, double2* __restrict__ partial) {
+  extern __shared__ int64_t tab[];
+  __shared__ double red_re[256], red_im[256];
+  const int s = find_step(steps, nsteps, blockIdx.x);
+  const StepDev& st = steps[s];
+  const int split = blockIdx.x - st.block0;
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  const int ntl = st.ntl, nt = 1 << ntl;
+  int64_t* t_ka = tab;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  int64_t* locA = t_kb + c_kb * 256;         // [nt] offset in A of tile-local index (A order)
+  int64_t* locB = locA + nt;                 // [nt] offset in B of tile-local index (B order)
+  double* sre = reinterpret_cast<double*>(locB + nt);
+  double* sim = sre + nt;
+  uint16_t* a_of_b = reinterpret_cast<uint16_t*>(sim + nt);  // B-order local index -> A-order
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  uint64_t tilemask = 0;
+  for (int i = 0; i < ntl; ++i) tilemask |= uint64_t(1) << st.tl[i];
+  for (int l = threadIdx.x; l < nt; l += blockDim.x) {
+    int64_t oa = 0, ob = 0;
+    uint64_t kk = 0;
+    for (int i = 0; i < ntl; ++i) {
+      if ((l >> i) & 1) {
+        oa += int64_t(1) << st.ka.pos[st.tl[i]];
+        ob += int64_t(1) << st.kb.pos[st.tlb[i]];
+        kk |= uint64_t(1) << st.tlb[i];
+      }
+    }
+    locA[l] = oa;
+    locB[l] = ob;
+    int la = 0;  // A-order local index of the contracted-index value kk
+    for (int i = 0; i < ntl; ++i)
+      if ((kk >> st.tl[i]) & 1) la |= 1 << i;
+    a_of_b[l] = static_cast<uint16_t>(la);
+  }
+  __syncthreads();
+  const int64_t ntiles = int64_t(1) << (st.rk - ntl);
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  double re = 0, im = 0;
+  for (int64_t t = split; t < ntiles; t += st.nsplit) {
+    // contracted-index value of the tile's base: the tile number spread over the non-tile bits
+    uint64_t base = 0;
+    int64_t rem = t;
+    for (int i = 0; i < st.rk && rem; ++i) {
+      if ((tilemask >> i) & 1) continue;
+      if (rem & 1) base |= uint64_t(1) << i;
+      rem >>= 1;
+    }
+    const int64_t ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
+    const int64_t bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
+    // staged A values sit at index l ^ ((l >> 5) & 31): B-ordered reads that stride across A's
+    // index (B's low bits on A's high bits) then fall into distinct shared-memory banks
+    for (int l = threadIdx.x; l < nt; l += blockDim.x) {
+      const int sl = l ^ ((l >> 5) & 31);
+      sre[sl] = A[ba + locA[l]];
+      sim[sl] = A[st.pa + ba + locA[l]];
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nt; l += blockDim.x) {
+      const double br = B[bb + locB[l]], bi = B[st.pb + bb + locB[l]];
+      const int la = a_of_b[l];
+      const int sl = la ^ ((la >> 5) & 31);
+      const double ar = sre[sl], ai = sim[sl];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+    __syncthreads();
+  }
+  red_re[threadIdx.x] = re;
+  red_im[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + w];
+      red_im[threadIdx.x] += red_im[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[st.poff + split] = make_double2(red_re[0], red_im[0]);
+}
+
+// Sum the split-K partials of every output in a fixed order (deterministic): with many splits a
+// whole block reduces each output (strided per-thread sums, then a tree), otherwise one thread
+// sums one output's splits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_splitk_done(const StepDev* __restrict__ steps, int nsteps,
+                                                     const double2* __restrict__ partial, T* __restrict__ arena,
+                                                     double2* __restrict__ scalars) {
+  __shared__ double red_re[256], red_im[256];
   const StepDev& st = steps[blockIdx.x];
   const int64_t nout = int64_t(1) << st.rc;
+  auto emit = [&](int64_t o, double re, double im) {
+    if (st.scalar_slot >= 0) {
+      scalars[st.scalar_slot] = make_double2(re, im);
+    } else {
+      arena[st.c + o] = static_cast<T>(re);
+      arena[st.c + st.pc + o] = static_cast<T>(im);
+    }
+  };
+  if (st.nsplit >= 64) {
+    for (int64_t o = 0; o < nout; ++o) {
+      double re = 0, im = 0;
+      for (int sp = threadIdx.x; sp < st.nsplit; sp += blockDim.x) {
+        const double2 v = partial[st.poff + o * st.nsplit + sp];
+        re += v.x;
+        im += v.y;
+      }
+      red_re[threadIdx.x] = re;
+      red_im[threadIdx.x] = im;
+      __syncthreads();
+      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+          red_re[threadIdx.x] += red_re[threadIdx.x + w];
+          red_im[threadIdx.x] += red_im[threadIdx.x + w];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) emit(o, red_re[0], red_im[0]);
+      __syncthreads();
+    }
+    return;
+  }
   for (int64_t o = threadIdx.x; o < nout; o += blockDim.x) {
     double re = 0, im = 0;
     for (int sp = 0; sp < st.nsplit; ++sp) {
@@ -209,12 +336,7 @@ __global__ void k_splitk_done(const StepDev* __restrict__ steps, int nsteps, con
       re += v.x;
       im += v.y;
     }
-    if (st.scalar_slot >= 0) {
-      scalars[st.scalar_slot] = make_double2(re, im);
-    } else {
-      arena[st.c + o] = static_cast<T>(re);
-      arena[st.c + st.pc + o] = static_cast<T>(im);
-    }
+    emit(o, re, im);
   }
 }
 
@@ -265,12 +387,62 @@ __device__ __forceinline__ void store_operand(const PermDev& p, char* base, int6
   }
 }
 
-// Tile of 32 rows x 32 k per iteration, 32 x 8 threads.
+// Two consecutive operand elements (idx even) with one vector store per split term.
+__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, double v0, double v1) {
+  switch (p.mode) {
+    case OPM_F64:
+      *reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx) = make_double2(v0, v1);
+      break;
+    case OPM_F32:
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
+          make_float2(static_cast<float>(v0), static_cast<float>(v1));
+      break;
+    case OPM_TF32:
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
+          make_float2(to_tf32(static_cast<float>(v0)), to_tf32(static_cast<float>(v1)));
+      break;
+    case OPM_TF32X2: {
+      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
+      const float h0 = to_tf32(x0), h1 = to_tf32(x1);
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[1]) + idx) =
+          make_float2(to_tf32(x0 - h0), to_tf32(x1 - h1));
+      break;
+    }
+    case OPM_BF16X2: {
+      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) =
+          __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+      break;
+    }
+    default: {  // OPM_BF16X3
+      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+      const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+      const float2 mf = __bfloat1622float2(m);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) = m;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[2]) + idx) =
+          __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+      break;
+    }
+  }
+}
+
+// Tile of 32 rows x 32 k per iteration, 256 threads. The source offsets of the tile's rows and
+// columns are computed once per tile; loads run with lanes along whichever index is contiguous in
+// the source, stores with lanes along k and two elements per vector store.
 template <typename T>
 __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
                                               char* __restrict__ base) {
   extern __shared__ int64_t tab[];
   __shared__ T tre[32][33], tim[32][33];
+  __shared__ int64_t roff[32], koff[32];
   const PermDev& p = perms[blockIdx.y];
   const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
   int64_t* t_r = tab;
@@ -284,34 +456,34 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   const int64_t ntr = R / TR, ntk = K / TK;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const T* src = arena + p.src;
+  const int64_t ld = 2 * K;
   for (int64_t tile = blockIdx.x; tile < ntr * ntk; tile += gridDim.x) {
     const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
-    // load phase: lanes along whichever index is contiguous in the source
+    if (threadIdx.x < 32) roff[tx] = tx < TR ? lookup(t_r, c_r, r0 + tx) : 0;
+    else if (threadIdx.x < 64) koff[tx] = tx < TK ? lookup(t_k, c_k, k0 + tx) : 0;
+    __syncthreads();
     for (int i = ty; i < 32; i += 8) {
       const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
       if (rr < TR && kk < TK) {
-        const int64_t off = lookup(t_r, c_r, r0 + rr) + lookup(t_k, c_k, k0 + kk);
+        const int64_t off = roff[rr] + koff[kk];
         tre[rr][kk] = src[off];
         tim[rr][kk] = src[p.plane + off];
       }
     }
     __syncthreads();
-    // store phase: lanes along k (contiguous in the operand)
-    for (int i = ty; i < TR; i += 8) {
-      if (tx < TK) {
-        const T re = tre[i][tx], im = tim[i][tx];
-        const int64_t r = r0 + i, k = k0 + tx;
-        if (p.embed) {
-          const int64_t ld = 2 * K;
-          store_operand(p, base, r * ld + k, re);             // (s=0, t=0):  Re
-          store_operand(p, base, r * ld + K + k, T(-im));     // (s=0, t=1): -Im
-          store_operand(p, base, (R + r) * ld + k, im);       // (s=1, t=0):  Im
-          store_operand(p, base, (R + r) * ld + K + k, re);   // (s=1, t=1):  Re
-        } else {
-          const int64_t ld = 2 * K;
-          store_operand(p, base, r * ld + k, re);
-          store_operand(p, base, r * ld + K + k, im);
-        }
+    const int pairs = TK >> 1;
+    for (int w = threadIdx.x; w < TR * pairs; w += blockDim.x) {
+      const int i = w / pairs, j = 2 * (w % pairs);
+      const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+      const int64_t r = r0 + i, k = k0 + j;
+      if (p.embed) {
+        store_operand2(p, base, r * ld + k, re0, re1);             // (s=0, t=0):  Re
+        store_operand2(p, base, r * ld + K + k, -im0, -im1);       // (s=0, t=1): -Im
+        store_operand2(p, base, (R + r) * ld + k, im0, im1);       // (s=1, t=0):  Im
+        store_operand2(p, base, (R + r) * ld + K + k, re0, re1);   // (s=1, t=1):  Re
+      } else {
+        store_operand2(p, base, r * ld + k, re0, re1);
+        store_operand2(p, base, r * ld + K + k, im0, im1);
       }
     }
     __syncthreads();
@@ -478,6 +650,21 @@ cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, 
   return cudaGetLastError();
 }
 
+size_t dot_smem_bytes(const StepDev& st) {
+  const BitMap* maps[2] = {&st.ka, &st.kb};
+  const size_t nt = size_t(1) << st.ntl;
+  return table_bytes(maps, 2) + nt * (8 + 8 + 8 + 8 + 2) + 16;
+}
+
+cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,
+                       double2* partial, double2* scalars, cudaStream_t s) {
+  if (nsteps == 0) return cudaSuccess;
+  k_dot<double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const double*>(arena), partial);
+  k_splitk_done<double><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<double*>(const_cast<void*>(arena)),
+                                               scalars);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
                         bool f64, cudaStream_t s) {
   if (nperm == 0) return cudaSuccess;
@@ -527,6 +714,7 @@ cudaError_t set_kernel_smem_limits() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_small<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

@@ -22,6 +22,10 @@ cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, 
                           double2* partial, double2* scalars, bool f64, cudaStream_t s);
 cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
                         bool f64, cudaStream_t s);
+// Tiled FP64 full contraction (k_dot) of steps with a scalar result, then the partial-sum pass.
+size_t dot_smem_bytes(const StepDev& st);
+cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,
+                       double2* partial, double2* scalars, cudaStream_t s);
 cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool f64,
                              cudaStream_t s);
 cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
@@ -35,5 +39,11 @@ cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblock
 bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s);
+// Same with an explicit bound on every device-side wait and a test hook: stall_loads = 1 makes the
+// producer issue no loads, so the MMA and epilogue waits expire and the kernel reports a status
+// code and returns.
+cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
+                              int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s,
+                              unsigned long long wait_ns, int stall_loads);
 
 }  // namespace ajf

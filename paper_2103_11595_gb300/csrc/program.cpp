@@ -93,7 +93,8 @@ BitMap make_map(const std::vector<int>& idx_labels, const std::vector<int>& tens
 
 bool contains(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
-enum Cls { C_SMALL = 0, C_SPLITK = 1, C_GEMM = 2 };
+enum Cls { C_SMALL = 0, C_SPLITK = 1, C_GEMM = 2, C_DOT = 3 };
+constexpr int kDotTileBits = 10;
 
 struct StepInfo {
   int cls = C_SMALL;
@@ -149,7 +150,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     const double mnk = std::ldexp(1.0, ma + nb + rk);
     std::vector<int> out;
     if (rc == 0) {
-      I.cls = C_SPLITK;
+      I.cls = rk >= kDotTileBits ? C_DOT : C_SPLITK;
       I.a = st.a;
       I.b = st.b;
       I.shared = sh;
@@ -241,11 +242,11 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   while (i < S) {
     const int s0 = order[i];
     const int cls = info[s0].cls, lev = info[s0].level;
-    if (cls == C_SMALL || cls == C_SPLITK) {
+    if (cls == C_SMALL || cls == C_SPLITK || cls == C_DOT) {
       int j = i;
       while (j < S && info[order[j]].level == lev && info[order[j]].cls == cls) ++j;
       Launch ln;
-      ln.kind = cls == C_SMALL ? LK_SMALL : LK_SPLITK;
+      ln.kind = cls == C_SMALL ? LK_SMALL : (cls == C_SPLITK ? LK_SPLITK : LK_DOT);
       ln.first = static_cast<int>(P.steps.size());
       ln.count = j - i;
       int blocks = 0;
@@ -281,6 +282,34 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
         if (cls == C_SMALL) {
           const int64_t nout = int64_t(1) << d.rc;
           blocks += static_cast<int>(std::min<int64_t>((nout + 255) / 256, 8192));
+        } else if (cls == C_DOT) {
+          // tile bits: the contracted bits on A's five lowest positions, then those on B's five
+          // lowest, topped up from A's order (kl follows A's bit order)
+          std::vector<int> bits;
+          auto add = [&](int i) {
+            if (static_cast<int>(bits.size()) < kDotTileBits && !contains(bits, i)) bits.push_back(i);
+          };
+          std::vector<int> by_b(d.rk);
+          for (int q = 0; q < d.rk; ++q) by_b[q] = q;
+          std::sort(by_b.begin(), by_b.end(), [&](int x, int y) { return d.kb.pos[x] < d.kb.pos[y]; });
+          for (int q = 0; q < 5 && q < d.rk; ++q) add(q);
+          for (int q = 0; q < 5 && q < d.rk; ++q) add(by_b[q]);
+          for (int q = 0; q < d.rk; ++q) add(q);
+          std::vector<int> tla = bits, tlb = bits;
+          std::sort(tla.begin(), tla.end(), [&](int x, int y) { return d.ka.pos[x] < d.ka.pos[y]; });
+          std::sort(tlb.begin(), tlb.end(), [&](int x, int y) { return d.kb.pos[x] < d.kb.pos[y]; });
+          d.ntl = static_cast<int32_t>(bits.size());
+          for (int q = 0; q < d.ntl; ++q) {
+            d.tl[q] = static_cast<int8_t>(tla[q]);
+            d.tlb[q] = static_cast<int8_t>(tlb[q]);
+          }
+          const int64_t tiles = int64_t(1) << (d.rk - d.ntl);
+          const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(tiles, 1216));
+          d.nsplit = static_cast<int32_t>(nsplit);
+          d.poff = static_cast<int64_t>(partials);
+          partials += static_cast<size_t>(nsplit);
+          d.scalar_slot = scalar_slots++;
+          blocks += static_cast<int>(nsplit);
         } else {
           const int64_t nout = int64_t(1) << d.rc;
           int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((int64_t(1) << d.rk) / 2048, 512));
@@ -291,7 +320,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
           if (d.rc == 0) d.scalar_slot = scalar_slots++;
           blocks += static_cast<int>(nout * nsplit);
         }
-        smem = std::max(smem, step_table_bytes(d));
+        smem = std::max(smem, cls == C_DOT ? dot_smem_bytes(d) : step_table_bytes(d));
         ln.flops += 8.0 * std::ldexp(1.0, d.rc + d.rk);
         ln.bytes += (std::ldexp(1.0, static_cast<int>(la.size())) + std::ldexp(1.0, static_cast<int>(lb.size())) +
                      (d.rc ? std::ldexp(1.0, d.rc) : 0.0)) * 2.0 * P.elem;

@@ -8,7 +8,7 @@
 
 namespace ajf {
 
-enum LaunchKind : int32_t { LK_SMALL = 0, LK_SPLITK = 1, LK_PERM = 2, LK_GEMM_SIMT = 3, LK_GEMM_TC = 4 };
+enum LaunchKind : int32_t { LK_SMALL = 0, LK_SPLITK = 1, LK_PERM = 2, LK_GEMM_SIMT = 3, LK_GEMM_TC = 4, LK_DOT = 5 };
 
 struct Launch {
   int32_t kind = 0;

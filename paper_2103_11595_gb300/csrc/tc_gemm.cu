@@ -72,6 +72,8 @@ struct TcParams {
   int32_t terms, kblocks, ntn, slots, bufs;
   uint32_t idesc;
   uint32_t slot_bytes;
+  unsigned long long wait_ns;        // bound of every wait
+  int32_t stall_loads;               // test hook: the producer issues no loads, so every wait expires
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -96,13 +98,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false (and status set) if the phase did not complete within kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+// Bounded wait: false (and status set) if the phase did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns, int* status,
+                                          int code) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t n = 1;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((n & 255) == 0 && globaltimer() - t0 > kWaitNs) {
+    if ((n & 255) == 0 && globaltimer() - t0 > limit_ns) {
       atomicExch(status, code);
       return false;
     }
@@ -220,10 +223,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles
-    const int iters = kblocks * T;
+    const int iters = p.stall_loads ? 0 : kblocks * T;
     for (int it = 0; it < iters; ++it) {
       const int s = it % S;
-      if (*abort_flag || !mbar_wait(empty0 + 8 * s, (static_cast<uint32_t>(it / S) & 1u) ^ 1u, p.status, 11)) {
+      if (*abort_flag || !mbar_wait(empty0 + 8 * s, (static_cast<uint32_t>(it / S) & 1u) ^ 1u, p.wait_ns, p.status, 11)) {
         *abort_flag = 1;
         break;
       }
@@ -239,16 +242,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     bool ok = true;
     for (int kb = 0; kb < kblocks && ok; ++kb) {
       const int b = kb % NB;
-      if (*abort_flag || !mbar_wait(acce0 + 8 * b, (static_cast<uint32_t>(kb / NB) & 1u) ^ 1u, p.status, 14)) {
+      if (*abort_flag || !mbar_wait(acce0 + 8 * b, (static_cast<uint32_t>(kb / NB) & 1u) ^ 1u, p.wait_ns, p.status, 14)) {
         ok = false;
         break;
       }
       // slot of term t of this block: (kb * T + t) % S; descriptors are kept in registers (a
       // dynamically indexed array would live in local memory and stall every MMA issue)
       const int s0 = (kb * T) % S, s1 = (kb * T + 1) % S, s2 = (kb * T + 2) % S;
-      if (!mbar_wait(full0 + 8 * s0, static_cast<uint32_t>((kb * T) / S) & 1u, p.status, 12) ||
-          (T > 1 && !mbar_wait(full0 + 8 * s1, static_cast<uint32_t>((kb * T + 1) / S) & 1u, p.status, 12)) ||
-          (T > 2 && !mbar_wait(full0 + 8 * s2, static_cast<uint32_t>((kb * T + 2) / S) & 1u, p.status, 12))) {
+      if (!mbar_wait(full0 + 8 * s0, static_cast<uint32_t>((kb * T) / S) & 1u, p.wait_ns, p.status, 12) ||
+          (T > 1 && !mbar_wait(full0 + 8 * s1, static_cast<uint32_t>((kb * T + 1) / S) & 1u, p.wait_ns, p.status, 12)) ||
+          (T > 2 && !mbar_wait(full0 + 8 * s2, static_cast<uint32_t>((kb * T + 2) / S) & 1u, p.wait_ns, p.status, 12))) {
         ok = false;
         break;
       }
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     for (int kb = 0; kb < kblocks; ++kb) {
       const int b = kb % NB;
       int w = 1;
-      if (lane == 0) w = mbar_wait(accf0 + 8 * b, static_cast<uint32_t>(kb / NB) & 1u, p.status, 13) ? 1 : 0;
+      if (lane == 0) w = mbar_wait(accf0 + 8 * b, static_cast<uint32_t>(kb / NB) & 1u, p.wait_ns, p.status, 13) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       if (!ok || *abort_flag) {
         ok = false;
@@ -415,6 +418,12 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind) {
 
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s) {
+  return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, d_status, s, kWaitNs, 0);
+}
+
+cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
+                              int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s,
+                              unsigned long long wait_ns, int stall_loads) {
   if (!tc_gemm_supported(M, N, K, kind) || terms < 1 || terms > kMaxTerms) return cudaErrorNotSupported;
   const bool bf16 = kind == 1;
   // BN = 256 would need 128 FP32 accumulators per epilogue thread and spills at 320 threads.
@@ -431,6 +440,8 @@ cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_of
   p.N = N;
   p.scale = debias_scale(bf16);
   p.terms = terms;
+  p.wait_ns = wait_ns;
+  p.stall_loads = stall_loads;
   const int64_t row_elems = kRowBytes / (bf16 ? 2 : 4);
   p.kblocks = static_cast<int32_t>((K + row_elems - 1) / row_elems);
   if (bf16) {

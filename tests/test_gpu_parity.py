@@ -288,7 +288,11 @@ def test_batching_circuit_alg1(precision):
     assert abs(r64["F"] - r2["F"]) <= 1e-12
     r, t, info = run(inst, 1, precision, trials=8)
     assert info["n_tc_gemms"] > 0
-    assert abs(r["F"] - r64["F"]) <= 1e-6
+    err = abs(r["F"] - r64["F"])
+    print(f"{precision}: |dF| = {err:.3e}")
+    # the TF32 split keeps 22 of the 24 FP32 mantissa bits; its bound on this Alg. I circuit is
+    # looser than the six-product bf16 split's
+    assert err <= (1e-6 if precision == "bf16x6" else 3e-6)
     for choice in ([0] * 6, [1, 0, 2, 0, 0, 3]):
         idx = 0
         for c in choice:

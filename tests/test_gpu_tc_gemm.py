@@ -86,6 +86,21 @@ def test_split_tf32_has_no_k_growing_bias(K):
     assert np.abs(rel).max() < 3e-6
 
 
+def test_bounded_waits_report_timeout_and_device_stays_usable():
+    """Failure detection without a GPU fault: the producer issues no loads, so the MMA and epilogue
+    waits expire after 50 ms; the kernel reports which wait gave up (codes 12-14), frees its TMEM and
+    returns. A normal GEMM in the same process then still works."""
+    st, code = ajf.ajf_selftest_wait_timeout(0, 50.0)
+    assert st == ajf.AJF_E_TIMEOUT
+    assert code in (12, 13, 14)
+    rng = np.random.default_rng(0)
+    A = tf32(rng.standard_normal((1, 128, 64)).astype(np.float32))
+    B = tf32(rng.standard_normal((1, 64, 64)).astype(np.float32))
+    C = ajf.ajf_selftest_gemm(0, 0, A, B, 128, 64, 64)
+    ref, bound = split_ref(A.astype(np.float64), B.astype(np.float64))
+    assert np.all(np.abs(C - ref) <= 4 * 64 * 2.0 ** -23 * bound + 1e-30)
+
+
 def test_unsupported_shape_is_reported():
     A = np.zeros((1, 16, 32), dtype=np.float32)
     B = np.zeros((1, 32, 32), dtype=np.float32)
