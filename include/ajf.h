@@ -285,6 +285,36 @@ ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double e
  * AJF_E_ARG (wait_ms not in (0, 10000], code NULL), AJF_E_NOMEM, AJF_E_CUDA. */
 ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t *code);
 
+/* ---- Learned merge scorer (AJF_PLANNER_LEARNED). The paper orders contractions by a tree
+ * decomposition (Sec. IV-C); this optional planner instead scores candidate pairwise merges with a
+ * small MLP (16 features of the two operands, the result and the planner state; 16-224-192-1,
+ * ReLU; 47,201 float32 parameters), trained to imitate the best paths that the greedy and min-fill
+ * planners find with restarts. The greedy planner remains its fallback (no model loaded) and its
+ * judge (the learned path is kept only if its estimated time is no worse). */
+
+/* Number of float32 parameters of the scorer (47201). */
+int32_t ajf_learned_param_count(void);
+
+/* Give the context a scorer model (n must equal ajf_learned_param_count(); the library copies it;
+ * NULL removes it). Invalidates the plan. Errors: AJF_E_ARG. */
+ajf_status ajf_set_learned_model(ajf_ctx *ctx, const float *weights, int32_t n);
+
+/* Training data from the loaded circuit: the network of `alg` is planned by the greedy and min-fill
+ * planners (`trials` restarts, `seed`), and the best path is replayed; at every step the merge it
+ * takes is paired with up to `negatives` other candidates. Each pair is 2 x 16 floats (the taken
+ * merge's features, then the other's). Up to cap_pairs pairs go to `out` (host); *n_pairs gets the
+ * total. Works on host-only contexts. Errors: AJF_E_ARG, AJF_E_STATE, AJF_E_BUDGET. */
+ajf_status ajf_learned_dataset(ajf_ctx *ctx, int alg, int32_t trials, uint64_t seed, int32_t negatives, float *out,
+                               int64_t cap_pairs, int64_t *n_pairs);
+
+/* Train the scorer on device `device` with the hand-written CUDA training kernels: pairwise ranking
+ * loss softplus(s(other) - s(taken)), minibatches of `batch` pairs, Adam (learning rate lr),
+ * `epochs` passes, Glorot-initialised from `seed`. pairs: n_pairs x 2 x 16 floats (host).
+ * Writes n_weights (= ajf_learned_param_count()) parameters and the last epoch's mean loss.
+ * Errors: AJF_E_ARG, AJF_E_NOMEM, AJF_E_CUDA. */
+ajf_status ajf_learned_train(int device, const float *pairs, int64_t n_pairs, int32_t epochs, int32_t batch, float lr,
+                             uint64_t seed, float *weights, int32_t n_weights, double *final_loss);
+
 /* Library version string, e.g. "ajf 0.1 sm_103a". */
 const char *ajf_version(void);
 

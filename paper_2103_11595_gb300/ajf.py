@@ -102,6 +102,11 @@ def lib() -> ctypes.CDLL:
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_selftest_wait_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
+            "ajf_learned_param_count": (I32, []),
+            "ajf_set_learned_model": (I32, [P, P, I32]),
+            "ajf_learned_dataset": (I32, [P, ctypes.c_int, I32, ctypes.c_uint64, I32, P, I64, ctypes.POINTER(I64)]),
+            "ajf_learned_train": (I32, [ctypes.c_int, P, I64, I32, I32, ctypes.c_float, ctypes.c_uint64, P, I32,
+                                        ctypes.POINTER(D)]),
             "ajf_plan_launches": (I32, [P, ctypes.POINTER(LaunchInfo), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
@@ -264,6 +269,42 @@ def ajf_selftest_wait_timeout(device: int, wait_ms: float) -> tuple:
     code = ctypes.c_int32()
     st = lib().ajf_selftest_wait_timeout(device, float(wait_ms), ctypes.byref(code))
     return st, code.value
+
+
+def ajf_learned_param_count() -> int:
+    return int(lib().ajf_learned_param_count())
+
+
+def ajf_set_learned_model(ctx, weights: Optional[np.ndarray]) -> None:
+    if weights is None:
+        _check(ctx, lib().ajf_set_learned_model(ctx, None, 0))
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(ctx, lib().ajf_set_learned_model(ctx, _ptr(w), int(w.size)))
+
+
+def ajf_learned_dataset(ctx, alg: int, trials: int = 8, seed: int = 0, negatives: int = 8) -> np.ndarray:
+    """(n, 2, 16) float32 ranking pairs from the loaded circuit (taken merge, other candidate)."""
+    n = ctypes.c_int64()
+    _check(ctx, lib().ajf_learned_dataset(ctx, int(alg), int(trials), int(seed), int(negatives), None, 0,
+                                          ctypes.byref(n)))
+    out = np.empty((max(1, n.value), 2, 16), dtype=np.float32)
+    _check(ctx, lib().ajf_learned_dataset(ctx, int(alg), int(trials), int(seed), int(negatives), _ptr(out), n.value,
+                                          ctypes.byref(n)))
+    return out[:n.value]
+
+
+def ajf_learned_train(device: int, pairs: np.ndarray, epochs: int = 10, batch: int = 512, lr: float = 1e-3,
+                      seed: int = 0) -> tuple:
+    """Train the merge scorer on the GPU; returns (weights float32[47201], final mean loss)."""
+    p = np.ascontiguousarray(pairs, dtype=np.float32)
+    w = np.empty(ajf_learned_param_count(), dtype=np.float32)
+    loss = ctypes.c_double()
+    st = lib().ajf_learned_train(int(device), _ptr(p), int(p.shape[0]), int(epochs), int(batch), float(lr), int(seed),
+                                 _ptr(w), int(w.size), ctypes.byref(loss))
+    if st != AJF_OK:
+        raise AjfError(st, "ajf_learned_train failed")
+    return w, float(loss.value)
 
 
 def ajf_profile_enable(ctx, on: bool = True) -> None:

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -91,6 +92,10 @@ struct PlanParams {
   double peak_flops = 1e12;   // contraction throughput of the chosen precision (time model)
   double peak_bw = 6.5e12;    // bytes/s
   double elem_bytes = 16;
+  // learned merge scorer: weights and a batched scoring function (device kernels or host)
+  const float* mlp = nullptr;
+  std::function<void(const float* w, const float* x, int n, float* out)> scorer;
+  double learned_noise = 0.0;  // Gumbel noise on scores for randomised restarts
 };
 
 Path plan_path(const Network& net, const PlanParams& p);
@@ -98,6 +103,8 @@ void evaluate_path(const Network& net, Path& path, const PlanParams& p);
 Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature);
 Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed);
 Path plan_learned(const Network& net, const PlanParams& p, uint64_t seed, bool* used);
+// Replay `ref` and append (chosen merge, other candidate) feature pairs; returns the pair count.
+int learned_dataset(const Network& net, const Path& ref, uint64_t seed, int negatives, std::vector<float>& out);
 
 // ------------------------------------------------------------------ network builders
 

@@ -14,6 +14,7 @@
 
 #include "ajf_internal.h"
 #include "kernels.h"
+#include "mlp.h"
 #include "program.h"
 
 using namespace ajf;
@@ -78,6 +79,10 @@ struct ajf_ctx {
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> event_pool;
   ajf_kernel_stats stats[7] = {};
+  // learned merge scorer
+  std::vector<float> mlp_weights;
+  int64_t mlp_version = 0;
+  ajf::MlpScorer mlp_scorer;
 };
 
 namespace {
@@ -594,7 +599,25 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     case AJF_PREC_BF16X3: pp.peak_flops = 400e12; break;
     default: pp.peak_flops = 200e12; break;
   }
-  std::vector<int64_t> key = {alg, c->n, c->has_impl, o.planner, o.precision, o.trials, static_cast<int64_t>(o.seed)};
+  cudaError_t score_err = cudaSuccess;
+  if (o.planner == AJF_PLANNER_LEARNED && static_cast<int>(c->mlp_weights.size()) == kMlpParams) {
+    pp.mlp = c->mlp_weights.data();
+    if (c->device >= 0) {
+      pp.scorer = [c, &score_err](const float* w, const float* x, int n, float* out) {
+        const cudaError_t e = c->mlp_scorer.score(w, x, n, out);
+        if (e != cudaSuccess) {
+          score_err = e;
+          for (int i = 0; i < n; ++i) out[i] = 0.0f;
+        }
+      };
+    } else {
+      pp.scorer = [](const float* w, const float* x, int n, float* out) {
+        for (int i = 0; i < n; ++i) out[i] = mlp_score_host(w, x + static_cast<size_t>(i) * kMlpFeatures);
+      };
+    }
+  }
+  std::vector<int64_t> key = {alg, c->n, c->has_impl, o.planner, o.precision, o.trials, static_cast<int64_t>(o.seed),
+                              c->mlp_version};
   auto key_gates = [&](const std::vector<GateData>& gs) {
     key.push_back(static_cast<int64_t>(gs.size()));
     for (auto& g : gs) key.insert(key.end(), {g.arity, g.q[0], g.q[1], g.q[2]});
@@ -610,9 +633,30 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
       c->plan_key = key;
       c->path_valid = true;
     }
-    c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device);
+    if (score_err == cudaSuccess && c->path.width > kMaxBits - 2) {
+      // too wide to address: report the path's cost and width with the budget error
+      ajf_plan_info pi{};
+      pi.cmacs = c->path.cmacs;
+      pi.flops = 8.0 * c->path.cmacs;
+      pi.width = c->path.width;
+      pi.n_steps = static_cast<int32_t>(c->path.steps.size());
+      pi.n_leaves = static_cast<int32_t>(c->net.leaf_labels.size());
+      pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
+      pi.planner_used = c->path.planner;
+      pi.arena_bytes = std::ldexp(1.0, c->path.width) * 16.0;
+      pi.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      c->info = pi;
+      if (info) *info = pi;
+      return fail(c, AJF_E_BUDGET, "planned width 2^" + std::to_string(c->path.width) +
+                                       " elements is beyond what one device can hold");
+    }
+    if (score_err == cudaSuccess) c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device);
   } catch (const std::exception& ex) {
     return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
+  }
+  if (score_err != cudaSuccess) {
+    c->path_valid = false;
+    return cuda_fail(c, score_err, "learned merge scorer");
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // descriptor image
@@ -888,6 +932,65 @@ ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t* code) 
   if (st != AJF_OK) return st;
   *code = status;
   return status != 0 ? AJF_E_TIMEOUT : AJF_OK;
+}
+
+int32_t ajf_learned_param_count(void) { return kMlpParams; }
+
+ajf_status ajf_set_learned_model(ajf_ctx* c, const float* weights, int32_t n) {
+  if (!c) return AJF_E_ARG;
+  if (!weights) {
+    c->mlp_weights.clear();
+  } else {
+    if (n != kMlpParams) return fail(c, AJF_E_ARG, "the merge scorer has " + std::to_string(kMlpParams) + " parameters");
+    c->mlp_weights.assign(weights, weights + n);
+  }
+  c->mlp_version++;
+  invalidate(c);
+  return AJF_OK;
+}
+
+ajf_status ajf_learned_dataset(ajf_ctx* c, int alg, int32_t trials, uint64_t seed, int32_t negatives, float* out,
+                               int64_t cap_pairs, int64_t* n_pairs) {
+  if (!c || !n_pairs || cap_pairs < 0 || (cap_pairs > 0 && !out) || negatives < 1) return AJF_E_ARG;
+  if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 1 or 2");
+  if (!c->has_ideal) return fail(c, AJF_E_STATE, "no circuit loaded");
+  pack_inputs(c);
+  if (alg == 1) {
+    int open_bits = 0;
+    for (auto& nz : c->in.noises) open_bits += nz.kbits;
+    if (open_bits > 40) return fail(c, AJF_E_BUDGET, "Alg. I result tensor too large");
+  }
+  const Network net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
+  PlanParams pp;
+  pp.planner = AJF_PLANNER_AUTO;
+  pp.trials = std::max(1, trials);
+  pp.seed = seed;
+  pp.peak_flops = 200e12;
+  pp.elem_bytes = 16;
+  Path ref;
+  std::vector<float> pairs;
+  try {
+    ref = plan_path(net, pp);
+    learned_dataset(net, ref, seed + 7, negatives, pairs);
+  } catch (const std::exception& ex) {
+    return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
+  }
+  const int64_t n = static_cast<int64_t>(pairs.size() / (2 * kMlpFeatures));
+  *n_pairs = n;
+  const int64_t m = std::min(n, cap_pairs);
+  if (m > 0) std::memcpy(out, pairs.data(), static_cast<size_t>(m) * 2 * kMlpFeatures * sizeof(float));
+  return AJF_OK;
+}
+
+ajf_status ajf_learned_train(int device, const float* pairs, int64_t n_pairs, int32_t epochs, int32_t batch, float lr,
+                             uint64_t seed, float* weights, int32_t n_weights, double* final_loss) {
+  if (!pairs || !weights || n_pairs < 1 || epochs < 1 || batch < 1 || n_weights != kMlpParams || n_pairs > (1 << 30))
+    return AJF_E_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
+  const cudaError_t e = mlp_train(pairs, static_cast<int>(n_pairs), epochs,
+                                  static_cast<int>(std::min<int64_t>(batch, n_pairs)), lr, seed, weights, final_loss);
+  if (e == cudaErrorMemoryAllocation) return AJF_E_NOMEM;
+  return e == cudaSuccess ? AJF_OK : AJF_E_CUDA;
 }
 
 ajf_status ajf_profile_enable(ajf_ctx* c, int on) {

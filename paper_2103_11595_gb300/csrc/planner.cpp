@@ -352,11 +352,14 @@ Path plan_path(const Network& net, const PlanParams& p) {
   }
   if (p.planner == AJF_PLANNER_LEARNED) {
     bool used = false;
-    Path lp = plan_learned(net, p, p.seed, &used);
-    consider(std::move(lp));
+    PlanParams q = p;
+    for (int t = 0; t < trials; ++t) {
+      q.learned_noise = t == 0 ? 0.0 : 0.25;
+      consider(plan_learned(net, q, p.seed * 1000003ull + static_cast<uint64_t>(t), &used));
+      if (!used) break;  // no model: plan_learned returned the greedy path
+    }
     // the greedy planner judges: keep the learned path only if it is no worse
     consider(plan_greedy(net, p, p.seed, 0.0));
-    if (best.planner != AJF_PLANNER_LEARNED && used) best.planner = AJF_PLANNER_GREEDY;
     return best;
   }
   const bool do_greedy = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_GREEDY;
