@@ -182,11 +182,19 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--instances", type=int, default=N_INSTANCES,
                     help="mid-config seeds per step (small values for profiler captures)")
+    ap.add_argument("--persistent-flops", type=float, default=2e6,
+                    help="batching workload: networks up to this many flops run in the persistent kernel")
+    ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "batching"],
+                    help="mid: the headline workload; tiny / batching: the small-network workloads "
+                         "run through the persistent kernel")
     args = ap.parse_args()
     n_inst = args.instances
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "mid":
+        run_small_networks(args, world, rank, local)
         return
 
     import numpy as np
@@ -371,6 +379,260 @@ def main():
             "F_J": [float(x) for x in F_fast],
             "roofline": roof, "kernel_classes": classes, "plain": plain, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+TINY = ("tiny: n=3, 20 gates over {H, T, S, CX, Rz}, 2 depolarising noises p=0.01; 100 seeds, "
+        "Alg. I and Alg. II each (200 evaluations per step)")
+BATCHING = ("batching: 64 circuits, n~U{8..20}, 50-300 gates (U3 + NN-CX bricks), 6 depolarising noises "
+            "(4096 Kraus combinations each); Alg. I")
+
+
+def run_small_networks(args, world, rank, local):
+    """Small-network workloads: all networks of a step in one persistent-kernel launch (tiny), or
+    the small ones in one persistent launch and the large ones on their own streams (batching)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    __graft_entry__.build()
+    from paper_2103_11595_gb300 import ajf
+    from paper_2103_11595_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    if args.workload == "tiny":
+        n_seeds = 100
+        insts = [W.tiny(rank * n_seeds + i) for i in range(n_seeds)]
+        jobs = [(inst, alg) for alg in (1, 2) for inst in insts]
+        pers_flops_max = float("inf")
+        workload = TINY
+    else:
+        n_seeds = 64
+        insts = [W.batching_circuit(rank * n_seeds + i) for i in range(n_seeds)]
+        jobs = [(inst, 1) for inst in insts]
+        pers_flops_max = args.persistent_flops
+        workload = BATCHING
+    n_jobs = len(jobs)
+
+    # small networks: persistent lowering (FP64) on the timing stream; large ones: default lowering
+    # in the requested precision, each on a stream of its own with its CUDA graph
+    pers, big, big_streams, order = [], [], [], []
+    infos = []
+    for inst, alg in jobs:
+        probe = ajf.Context(-1)
+        ajf.load_instance(probe.handle, inst)
+        pinfo = ajf.ajf_plan(probe.handle, alg, trials=args.trials, lowering="persistent")
+        probe.close()
+        if pinfo["flops"] <= pers_flops_max:
+            c = ajf.Context(dev, stream.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            infos.append(ajf.ajf_plan(c.handle, alg, trials=args.trials, lowering="persistent"))
+            ajf.ajf_upload(c.handle)
+            order.append(("p", len(pers)))
+            pers.append(c)
+        else:
+            s = torch.cuda.Stream()
+            c = ajf.Context(dev, s.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            infos.append(ajf.ajf_plan(c.handle, alg, precision=args.precision, trials=args.trials, use_graph=True))
+            ajf.ajf_upload(c.handle)
+            order.append(("b", len(big)))
+            big.append(c)
+            big_streams.append(s)
+    # one persistent launch per algorithm (the kernel runs one program kind per context anyway)
+    groups = {}
+    for (inst, alg), (kind, idx) in zip(jobs, order):
+        if kind == "p":
+            groups.setdefault(alg, []).append(idx)
+    out = torch.zeros(n_jobs, 3, dtype=torch.float64, device=dev)
+    pers_rows = {}
+    row = 0
+    for alg in sorted(groups):
+        pers_rows[alg] = row
+        row += len(groups[alg])
+    big_rows = list(range(row, row + len(big)))
+
+    def step():
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for k, c in enumerate(big):
+            big_streams[k].wait_event(fork)
+            ajf.ajf_launch(c.handle, out[big_rows[k]].data_ptr())
+        for alg in sorted(groups):
+            hs = [pers[i].handle for i in groups[alg]]
+            ajf.ajf_launch_persistent(hs, out[pers_rows[alg]].data_ptr())
+        for k in range(len(big)):
+            done = torch.cuda.Event()
+            done.record(big_streams[k])
+            stream.wait_event(done)
+
+    def timed(steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            barrier(world)
+            total = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+            torch.cuda.synchronize()
+        return total
+
+    with ClockSampler(dev) as clk:
+        total_ms = timed(args.steps, args.warmup)
+    clocks = clk.summary()
+    total_s = max_over_ranks(total_ms / 1e3, world)
+    value = n_jobs * args.steps * world / total_s
+    F_dev = out[:, 1].cpu().numpy().copy()
+
+    # per-kernel timing of the persistent launches (CUDA events inside the library)
+    for alg in sorted(groups):
+        lead = pers[groups[alg][0]]
+        ajf.ajf_profile_enable(lead.handle, True)
+        with torch.cuda.stream(stream):
+            ajf.ajf_launch_persistent([pers[i].handle for i in groups[alg]], out[pers_rows[alg]].data_ptr())
+        stream.synchronize()
+    pst = {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0}
+    for alg in sorted(groups):
+        lead = pers[groups[alg][0]]
+        v = ajf.ajf_profile_read(lead.handle)["persistent"]
+        for f in pst:
+            pst[f] += v[f]
+        ajf.ajf_profile_enable(lead.handle, False)
+    fp64_peak = 1.25
+    achieved = pst["flops"] / (pst["ms"] / 1e3) / 1e12 if pst["ms"] else 0.0
+    roof = {"bound": "alu", "kernel_class": "persistent", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None,
+            "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s); the kernel is latency-bound at these sizes",
+            "launches_per_step": pst["launches"], "avg_launch_ms": pst["ms"] / max(1, pst["launches"]),
+            "hbm_bytes_per_launch_alg": pst["bytes"] / max(1, pst["launches"])}
+
+    # the default path on the same jobs (per-context CUDA graphs, one stream per context)
+    default = None
+    if not args.no_plain:
+        dctx, dstreams = [], []
+        for inst, alg in jobs:
+            s = torch.cuda.Stream()
+            c = ajf.Context(dev, s.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            ajf.ajf_plan(c.handle, alg, precision="f64", trials=args.trials, use_graph=True)
+            ajf.ajf_upload(c.handle)
+            dctx.append(c)
+            dstreams.append(s)
+        dout = torch.zeros(n_jobs, 3, dtype=torch.float64, device=dev)
+
+        def dstep():
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            for k, c in enumerate(dctx):
+                dstreams[k].wait_event(fork)
+                ajf.ajf_launch(c.handle, dout[k].data_ptr())
+            for k in range(len(dctx)):
+                done = torch.cuda.Event()
+                done.record(dstreams[k])
+                stream.wait_event(done)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                dstep()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dstep()
+            e1.record(stream)
+            e1.synchronize()
+        d_ms = e0.elapsed_time(e1)
+        F_def = dout[:, 1].cpu().numpy()
+        # rows of `out` follow (persistent groups by alg, then big); map them back to job order
+        F_ord = np.empty(n_jobs)
+        for j, ((inst, alg), (kind, idx)) in enumerate(zip(jobs, order)):
+            if kind == "p":
+                F_ord[j] = F_dev[pers_rows[alg] + groups[alg].index(idx)]
+            else:
+                F_ord[j] = F_dev[big_rows[idx]]
+        default = {"value": n_jobs / (d_ms / 1e3), "unit": "evals/s", "dtype": "f64",
+                   "path": "default lowering, one CUDA graph per network, one stream per network",
+                   "max_abs_dF_vs_persistent_run": float(np.max(np.abs(F_ord - F_def)))}
+        for c in dctx:
+            c.close()
+
+    # end to end: load + plan (structural cache) per network, one batch call from host arrays
+    e2e_ctx = pers + big
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(args.e2e_steps):
+        h2d = d2h = 0
+        for (inst, alg), (kind, idx) in zip(jobs, order):
+            c = pers[idx] if kind == "p" else big[idx]
+            ajf.load_instance(c.handle, inst)
+            if kind == "p":
+                info = ajf.ajf_plan(c.handle, alg, trials=args.trials, lowering="persistent")
+            else:
+                info = ajf.ajf_plan(c.handle, alg, precision=args.precision, trials=args.trials, use_graph=True)
+            h2d += int(info["upload_bytes"])
+            d2h += 24
+        for alg in sorted(set(a for _, a in jobs)):
+            hs = [c.handle for c, (_, a) in zip([pers[i] if k == "p" else big[i] for k, i in order], jobs) if a == alg]
+            ajf.ajf_fidelity_batch_persistent(hs, alg)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) if args.e2e_steps else float("nan")
+    e2e = {"value": n_jobs * args.e2e_steps * world / e2e_s if args.e2e_steps else None, "unit": "evals/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "note": "host wall clock: load + plan (structural cache hit) per network, then "
+                   "ajf_fidelity_batch_persistent per algorithm (upload, one persistent launch + "
+                   "per-stream launches of the large networks, read back)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import dense, network
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 10.0 and done < n_jobs:
+            inst, alg = jobs[done]
+            if args.workload == "tiny":
+                dense.fidelity(inst)
+            else:
+                network.alg2_fidelity(inst, order="minfill")
+            done += 1
+        dt = time.perf_counter() - t0
+        how = ("oracle dense definition (Alg. I enumeration)" if args.workload == "tiny" else
+               "oracle Alg. II network, min-fill order, numpy complex128 (the oracle's fastest route to F_J)")
+        cpu = {"value": done / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the first {done} evaluations of the step, {how}, in {dt:.1f} s"}
+
+    for c in pers + big:
+        c.close()
+    if rank == 0:
+        n_traces = sum(i.n_combinations() for i, a in jobs if a == 1)
+        line = {
+            "metric": "fidelity evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "us_per_eval": total_s * 1e6 / (n_jobs * args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (persistent kernel); " + args.precision + " GEMM operands elsewhere",
+            "data": "synthetic",
+            "config": {"workload": workload, "persistent_networks": len(pers), "other_networks": len(big),
+                       "persistent_flops_max": None if pers_flops_max == float("inf") else pers_flops_max,
+                       "l2": "flushed (256 MiB write) before every step", "trials": args.trials,
+                       "parallelism": f"{world} independent ranks (weak scaling)"},
+            "traces_per_s": n_traces * args.steps * world / total_s,
+            "roofline": roof, "default_path": default, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": (len(groups) + sum(i["n_launches"] for i, (k, _) in zip(infos, order) if k == "b"))
+                            * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

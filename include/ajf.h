@@ -64,14 +64,24 @@ enum {
 };
 
 enum {
-  AJF_PREC_F64 = 0,    /* complex128 storage, FP64 arithmetic everywhere                       */
-  AJF_PREC_F32 = 1,    /* complex64 storage, FP32 CUDA-core GEMMs                              */
-  AJF_PREC_TF32 = 2,   /* complex64 storage, one-pass TF32 tensor-core GEMMs (tcgen05), FP32 accumulate */
-  AJF_PREC_TF32X3 = 3, /* complex64 storage, split TF32 hi/lo, three tcgen05 passes, FP32 accumulate */
-  AJF_PREC_BF16X3 = 4, /* complex64 storage, bf16 split in two terms, three tcgen05 passes      */
-  AJF_PREC_BF16X6 = 5  /* complex64 storage, bf16 split in three terms, six tcgen05 passes      */
+  AJF_PREC_F64 = 0,    /* FP64 arithmetic everywhere                                           */
+  AJF_PREC_F32 = 1,    /* GEMM-class steps on FP32 CUDA cores (operands rounded to FP32)       */
+  AJF_PREC_TF32 = 2,   /* GEMM-class steps: one-pass TF32 tensor-core GEMMs (tcgen05), FP32 accumulate */
+  AJF_PREC_TF32X3 = 3, /* split TF32 hi/lo operands, three tcgen05 products, FP32 accumulate   */
+  AJF_PREC_BF16X3 = 4, /* bf16 operands split in two terms, three tcgen05 products             */
+  AJF_PREC_BF16X6 = 5  /* bf16 operands split in three terms, six tcgen05 products             */
 };
-/* In every mode the final contraction to a scalar, sum_i |t_i|^2, F_J and 1 - F_J are FP64. */
+/* Tensors are FP64 (planar complex) in device memory in every mode; a mode only sets how the
+ * operands of the GEMM-class steps are rounded or split. Leaves, small steps, the final
+ * contraction to a scalar, sum_i |t_i|^2, F_J and 1 - F_J are FP64 in every mode. */
+
+enum {
+  AJF_LOWER_DEFAULT = 0,   /* GEMM-class steps on tensor cores / CUDA-core GEMMs, one launch per
+                              level of small steps                                              */
+  AJF_LOWER_PERSISTENT = 1 /* every step a CUDA-core gather or reduction step in FP64, so that one
+                              thread block of the persistent kernel runs the whole network
+                              (ajf_launch_persistent); meant for small networks                */
+};
 
 typedef struct ajf_ctx ajf_ctx;
 
@@ -82,7 +92,8 @@ typedef struct ajf_plan_opts {
   int32_t use_graph;       /* 1: capture the device program in a CUDA graph on first run       */
   uint64_t seed;           /* planner random seed                                             */
   double mem_budget_bytes; /* 0 = 60% of the device's free memory at plan time                 */
-  int32_t reserved[8];     /* must be zero                                                     */
+  int32_t lowering;        /* AJF_LOWER_*; AJF_LOWER_PERSISTENT requires AJF_PREC_F64          */
+  int32_t reserved[7];     /* must be zero                                                     */
 } ajf_plan_opts;
 
 typedef struct ajf_plan_info {
@@ -228,8 +239,8 @@ ajf_status ajf_upload(ajf_ctx *ctx);
 
 /* Alg. I over several contexts (independent circuits of uneven sizes; Sec. IV-A remarks that
  * the traces are independent): every context must have an Alg. I plan of the same precision
- * on the same device; all of them are executed together (merged level launches on the first
- * context's stream) and out[i] receives context i's result. eps as in ajf_fidelity_alg1.
+ * on the same device; every context's program is enqueued on that context's own stream (so the
+ * circuits overlap on the GPU) and out[i] receives context i's result. eps as in ajf_fidelity_alg1.
  * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, mixed device or precision), AJF_E_STATE. */
 ajf_status ajf_fidelity_alg1_batch(ajf_ctx *const *ctxs, int n_ctx, double eps, ajf_result *out);
 
@@ -252,7 +263,9 @@ ajf_status ajf_plan_launches(const ajf_ctx *ctx, ajf_launch_info *out, int cap, 
  * CUDA events around each launch (CUDA-graph replay is bypassed). */
 ajf_status ajf_profile_enable(ajf_ctx *ctx, int on);
 
-/* Read the counters: `stats` receives up to `cap` classes (7 are defined). Synchronises the
+/* Read the counters: `stats` receives up to `cap` classes (8 are defined: 0 leaves, 1 small,
+ * 2 split-K and tiled dot, 3 operand gather, 4 CUDA-core GEMM, 5 tensor-core GEMM, 6 final,
+ * 7 persistent kernel -- counted on the context that leads the launch). Synchronises the
  * context's stream. Errors: AJF_E_ARG. */
 ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
 
@@ -275,6 +288,28 @@ ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t
  * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, bad alg, contexts on different devices),
  * AJF_E_STATE (a context without a plan for `alg`), plus those of ajf_fidelity_alg1/alg2. */
 ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out);
+
+/* Persistent execution of many small networks in ONE kernel launch (no paper counterpart; the
+ * independence of circuits and traces is Sec. IV-A's remark): one thread block per context runs
+ * that context's whole program -- leaves, every pairwise step level by level, the FP64 trace,
+ * sum |t_i|^2, F and 1 - F -- with its tensors in shared memory when the plan's work region
+ * fits (96 KiB), otherwise in the context's device arena. Every context must be planned with
+ * opts.lowering = AJF_LOWER_PERSISTENT, on one device; inputs not yet resident are uploaded on
+ * each context's stream first. The launch goes on ctxs[0]'s stream, ordered after every
+ * context's stream and before their later work (events). `dev_results` (device memory, 3 *
+ * n_ctx doubles, may be NULL) receives {S, F, 1-F} per context; each context's own result and
+ * Alg. I traces are written as by ajf_launch. Does not wait for the GPU.
+ * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, contexts on different devices or host-only),
+ * AJF_E_STATE (a context without a persistent-lowered plan), AJF_E_NOMEM, AJF_E_CUDA. */
+ajf_status ajf_launch_persistent(ajf_ctx *const *ctxs, int n_ctx, double *dev_results);
+
+/* Like ajf_fidelity_batch, with the contexts planned with AJF_LOWER_PERSISTENT run together in
+ * one launch of the persistent kernel (ajf_launch_persistent) and the others on their own
+ * streams, concurrently; waits and fills out[i] for every context. *n_persistent (may be NULL)
+ * receives how many contexts ran in the persistent launch.
+ * Errors: those of ajf_fidelity_batch and ajf_launch_persistent. */
+ajf_status ajf_fidelity_batch_persistent(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out,
+                                         int32_t *n_persistent);
 
 /* Self-test of the failure path of the device-side waits (no paper counterpart; used by the test
  * suite): runs the tensor-core GEMM kernel on a 128 x 32 x 32 problem with every wait bounded by

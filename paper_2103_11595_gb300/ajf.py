@@ -29,7 +29,7 @@ PLANNERS = {"auto": AJF_PLANNER_AUTO, "greedy": AJF_PLANNER_GREEDY, "minfill": A
 class PlanOpts(ctypes.Structure):
     _fields_ = [("planner", ctypes.c_int32), ("precision", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("lowering", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -49,7 +49,9 @@ class KernelStats(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-KERNEL_CLASSES = ["leaves", "small", "splitk", "gather", "gemm_simt", "gemm_tc", "final"]
+AJF_LOWER_DEFAULT, AJF_LOWER_PERSISTENT = 0, 1
+LOWERINGS = {"default": AJF_LOWER_DEFAULT, "persistent": AJF_LOWER_PERSISTENT}
+KERNEL_CLASSES = ["leaves", "small", "splitk", "gather", "gemm_simt", "gemm_tc", "final", "persistent"]
 
 
 class LaunchInfo(ctypes.Structure):
@@ -110,6 +112,9 @@ def lib() -> ctypes.CDLL:
             "ajf_plan_launches": (I32, [P, ctypes.POINTER(LaunchInfo), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
+            "ajf_launch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_fidelity_batch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D,
+                                                    ctypes.POINTER(Result), ctypes.POINTER(I32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -170,8 +175,9 @@ def ajf_clear_noise(ctx) -> None:
 
 
 def ajf_plan(ctx, alg: int, planner="auto", precision="f64", trials: int = 0, use_graph: bool = False,
-             seed: int = 0, mem_budget_bytes: float = 0.0) -> dict:
+             seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default") -> dict:
     o = PlanOpts()
+    o.lowering = LOWERINGS[lowering] if isinstance(lowering, str) else int(lowering)
     o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.trials = int(trials)
@@ -275,6 +281,12 @@ def ajf_learned_param_count() -> int:
     return int(lib().ajf_learned_param_count())
 
 
+def default_learned_model() -> np.ndarray:
+    """The merge scorer trained on the 2000 training circuits of the learned-planner workload
+    (paper_2103_11595_gb300/data/merge_scorer.npy, written by learned_planner train)."""
+    return np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "merge_scorer.npy"))
+
+
 def ajf_set_learned_model(ctx, weights: Optional[np.ndarray]) -> None:
     if weights is None:
         _check(ctx, lib().ajf_set_learned_model(ctx, None, 0))
@@ -326,6 +338,26 @@ def ajf_fidelity_batch(ctxs: Sequence, alg: int, eps: float = -1.0) -> list:
         msgs = "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c))
         raise AjfError(st, msgs)
     return [r.as_dict() for r in res]
+
+
+def ajf_launch_persistent(ctxs: Sequence, dev_results: int = 0) -> None:
+    """One persistent-kernel launch over `ctxs` (all planned with lowering="persistent"); results
+    as 3 doubles per context to the device pointer `dev_results` (0: none). Does not wait."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    st = lib().ajf_launch_persistent(arr, len(ctxs), ctypes.c_void_p(dev_results) if dev_results else None)
+    if st != AJF_OK:
+        raise AjfError(st, "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c)))
+
+
+def ajf_fidelity_batch_persistent(ctxs: Sequence, alg: int, eps: float = -1.0) -> tuple:
+    """(results, n_persistent): persistent-lowered contexts in one launch, the others on their streams."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    res = (Result * len(ctxs))()
+    n = ctypes.c_int32()
+    st = lib().ajf_fidelity_batch_persistent(arr, len(ctxs), int(alg), float(eps), res, ctypes.byref(n))
+    if st != AJF_OK:
+        raise AjfError(st, "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c)))
+    return [r.as_dict() for r in res], int(n.value)
 
 
 # ----------------------------------------------------------------------------- marshalling helpers

@@ -78,11 +78,19 @@ struct ajf_ctx {
   bool profiling = false;
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> event_pool;
-  ajf_kernel_stats stats[7] = {};
+  ajf_kernel_stats stats[8] = {};
   // learned merge scorer
   std::vector<float> mlp_weights;
   int64_t mlp_version = 0;
   ajf::MlpScorer mlp_scorer;
+  // persistent launches led by this context: job/op table (device) and what it was built for
+  int64_t plan_gen = 0;
+  char* pers_dev = nullptr;
+  size_t pers_cap = 0;
+  std::vector<char> pers_host;
+  std::vector<uintptr_t> pers_key;
+  size_t pers_smem = 0;
+  cudaEvent_t sync_ev = nullptr;  // cross-stream ordering of persistent launches
 };
 
 namespace {
@@ -461,6 +469,8 @@ void ajf_destroy(ajf_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->own_arena && c->arena && !c->user_ws) cudaFree(c->arena);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->pers_dev) cudaFree(c->pers_dev);
+  if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -567,8 +577,11 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   if (o.trials <= 0) o.trials = 32;
   if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
   if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 7; ++i)
     if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
+  if (o.lowering != AJF_LOWER_DEFAULT && o.lowering != AJF_LOWER_PERSISTENT) return fail(c, AJF_E_ARG, "bad lowering");
+  if (o.lowering == AJF_LOWER_PERSISTENT && o.precision != AJF_PREC_F64)
+    return fail(c, AJF_E_ARG, "the persistent lowering computes in FP64: precision must be AJF_PREC_F64");
   const int nsk = static_cast<int>(c->has_impl ? c->impl.size() : c->ideal.size());
   for (auto& nz : c->noises)
     if (nz.after >= nsk) return fail(c, AJF_E_ARG, "a noise is placed after a gate the skeleton does not have");
@@ -650,7 +663,9 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
       return fail(c, AJF_E_BUDGET, "planned width 2^" + std::to_string(c->path.width) +
                                        " elements is beyond what one device can hold");
     }
-    if (score_err == cudaSuccess) c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device);
+    if (score_err == cudaSuccess)
+      c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device,
+                      o.lowering == AJF_LOWER_PERSISTENT);
   } catch (const std::exception& ex) {
     return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
   }
@@ -704,6 +719,7 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   c->opts = o;
   c->alg = alg;
   c->planned = true;
+  c->plan_gen++;
   c->err.clear();
   return AJF_OK;
 }
@@ -1010,7 +1026,7 @@ ajf_status ajf_profile_read(ajf_ctx* c, ajf_kernel_stats* stats, int cap) {
     CUDA_TRY(c, cudaSetDevice(c->device));
     drain_profile(c);
   }
-  for (int i = 0; i < cap && i < 7; ++i) stats[i] = c->stats[i];
+  for (int i = 0; i < cap && i < 8; ++i) stats[i] = c->stats[i];
   return AJF_OK;
 }
 
@@ -1087,6 +1103,195 @@ ajf_status ajf_fidelity_alg1_batch(ajf_ctx* const* ctxs, int n_ctx, double eps, 
     out[i].reserved = 0;
     c->have_alg1 = true;
   }
+  return AJF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+ajf_status sync_event(ajf_ctx* c, cudaEvent_t* ev) {
+  if (!c->sync_ev) CUDA_TRY(c, cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming));
+  *ev = c->sync_ev;
+  return AJF_OK;
+}
+
+// Job and op table of a persistent launch over `ctxs`, kept in ctxs[0]'s device buffer and
+// rebuilt only when a context, its arena, its plan or the result pointer changed.
+ajf_status persistent_table(ajf_ctx* const* ctxs, int n, double* dev_results) {
+  ajf_ctx* lead = ctxs[0];
+  std::vector<uintptr_t> key;
+  key.reserve(3 * static_cast<size_t>(n) + 1);
+  key.push_back(reinterpret_cast<uintptr_t>(dev_results));
+  for (int i = 0; i < n; ++i) {
+    key.push_back(reinterpret_cast<uintptr_t>(ctxs[i]));
+    key.push_back(reinterpret_cast<uintptr_t>(ctxs[i]->arena));
+    key.push_back(static_cast<uintptr_t>(ctxs[i]->plan_gen));
+  }
+  if (lead->pers_dev && key == lead->pers_key) return AJF_OK;
+  std::vector<InterpJob> jobs(n);
+  std::vector<InterpOp> ops;
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const ajf_ctx* c = ctxs[i];
+    const Program& P = c->prog;
+    InterpJob& J = jobs[i];
+    std::memset(&J, 0, sizeof(J));
+    J.base = c->arena;
+    J.out = dev_results ? dev_results + 3 * static_cast<size_t>(i) : nullptr;
+    J.off_leaves = static_cast<int64_t>(P.off_leaves);
+    J.off_steps = static_cast<int64_t>(P.off_steps);
+    J.off_final = static_cast<int64_t>(P.off_final);
+    J.off_inputs = static_cast<int64_t>(P.off_inputs);
+    J.off_scalars = static_cast<int64_t>(P.off_scalars);
+    J.off_traces = static_cast<int64_t>(P.off_traces);
+    J.off_result = static_cast<int64_t>(P.off_result);
+    J.work0 = static_cast<int64_t>(P.off_work / P.elem);
+    J.n_leaves = static_cast<int32_t>(P.leaves.size());
+    J.op0 = static_cast<int32_t>(ops.size());
+    J.n_ops = static_cast<int32_t>(P.launches.size());
+    J.smem = P.work_bytes <= kPersistentSmemMax ? 1 : 0;
+    if (J.smem) smem = std::max(smem, P.work_bytes);
+    for (const Launch& ln : P.launches) {
+      if (ln.kind != LK_SMALL && ln.kind != LK_SPLITK)
+        return fail(ctxs[i], AJF_E_STATE, "internal: a persistent-lowered program holds a GEMM launch");
+      ops.push_back(InterpOp{ln.kind, ln.first, ln.count, 0});
+    }
+  }
+  const size_t jb = (sizeof(InterpJob) * static_cast<size_t>(n) + 255) & ~size_t(255);
+  const size_t bytes = jb + sizeof(InterpOp) * std::max<size_t>(1, ops.size());
+  lead->pers_host.assign(bytes, 0);
+  std::memcpy(lead->pers_host.data(), jobs.data(), sizeof(InterpJob) * static_cast<size_t>(n));
+  if (!ops.empty()) std::memcpy(lead->pers_host.data() + jb, ops.data(), sizeof(InterpOp) * ops.size());
+  if (bytes > lead->pers_cap) {
+    if (lead->pers_dev) {
+      CUDA_TRY(lead, cudaStreamSynchronize(lead->stream));
+      cudaFree(lead->pers_dev);
+      lead->pers_dev = nullptr;
+      lead->pers_cap = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(lead, AJF_E_NOMEM, "persistent job table");
+    }
+    lead->pers_dev = static_cast<char*>(p);
+    lead->pers_cap = bytes;
+  }
+  CUDA_TRY(lead, cudaMemcpyAsync(lead->pers_dev, lead->pers_host.data(), bytes, cudaMemcpyHostToDevice, lead->stream));
+  lead->pers_key = key;
+  lead->pers_smem = smem;
+  return AJF_OK;
+}
+
+size_t persistent_ops_offset(int n) { return (sizeof(InterpJob) * static_cast<size_t>(n) + 255) & ~size_t(255); }
+
+ajf_status check_batch(ajf_ctx* const* ctxs, int n_ctx) {
+  if (!ctxs || n_ctx < 1) return AJF_E_ARG;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return AJF_E_ARG;
+    if (ctxs[i]->device < 0 || ctxs[i]->device != ctxs[0]->device)
+      return fail(ctxs[0], AJF_E_ARG, "contexts must share one device");
+  }
+  return AJF_OK;
+}
+
+// Enqueue one persistent launch over ctxs (all persistent-lowered, planned) on ctxs[0]'s stream.
+ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_results) {
+  ajf_ctx* lead = ctxs[0];
+  CUDA_TRY(lead, cudaSetDevice(lead->device));
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]->uploaded) {
+      ajf_status st = do_upload(ctxs[i]);
+      if (st != AJF_OK) return st;
+    }
+  }
+  ajf_status st = persistent_table(ctxs, n_ctx, dev_results);
+  if (st != AJF_OK) return st;
+  cudaStream_t s0 = lead->stream;
+  for (int i = 1; i < n_ctx; ++i) {
+    if (ctxs[i]->stream == s0) continue;
+    cudaEvent_t ev;
+    if ((st = sync_event(ctxs[i], &ev)) != AJF_OK) return st;
+    CUDA_TRY(ctxs[i], cudaEventRecord(ev, ctxs[i]->stream));
+    CUDA_TRY(lead, cudaStreamWaitEvent(s0, ev, 0));
+  }
+  {
+    double fl = 0, by = 0;
+    for (int i = 0; i < n_ctx; ++i) {
+      fl += ctxs[i]->prog.flops;
+      by += ctxs[i]->prog.bytes;
+    }
+    ProfScope ps(lead, s0, 7, fl, by);
+    const cudaError_t e = launch_persistent(reinterpret_cast<const InterpJob*>(lead->pers_dev), n_ctx,
+                                            reinterpret_cast<const InterpOp*>(lead->pers_dev + persistent_ops_offset(n_ctx)),
+                                            lead->pers_smem, s0);
+    if (e != cudaSuccess) return cuda_fail(lead, e, "persistent kernel");
+  }
+  cudaEvent_t ev0;
+  if ((st = sync_event(lead, &ev0)) != AJF_OK) return st;
+  CUDA_TRY(lead, cudaEventRecord(ev0, s0));
+  for (int i = 1; i < n_ctx; ++i)
+    if (ctxs[i]->stream != s0) CUDA_TRY(ctxs[i], cudaStreamWaitEvent(ctxs[i]->stream, ev0, 0));
+  for (int i = 0; i < n_ctx; ++i)
+    if (ctxs[i]->alg == 1) ctxs[i]->have_alg1 = true;
+  return AJF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ajf_status ajf_launch_persistent(ajf_ctx* const* ctxs, int n_ctx, double* dev_results) {
+  ajf_status st = check_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  for (int i = 0; i < n_ctx; ++i)
+    if (!ctxs[i]->planned || !ctxs[i]->prog.persistent)
+      return fail(ctxs[i], AJF_E_STATE, "context without a plan made with AJF_LOWER_PERSISTENT");
+  return launch_persistent_ctxs(ctxs, n_ctx, dev_results);
+}
+
+ajf_status ajf_fidelity_batch_persistent(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out,
+                                         int32_t* n_persistent) {
+  ajf_status st = check_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  if (!out || (alg != 1 && alg != 2)) return fail(ctxs[0], AJF_E_ARG, "bad alg or out");
+  if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
+  std::vector<ajf_ctx*> pers, rest;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]->planned || ctxs[i]->alg != alg)
+      return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
+    (ctxs[i]->prog.persistent ? pers : rest).push_back(ctxs[i]);
+  }
+  CUDA_TRY(ctxs[0], cudaSetDevice(ctxs[0]->device));
+  if (!pers.empty()) {
+    st = launch_persistent_ctxs(pers.data(), static_cast<int>(pers.size()), nullptr);
+    if (st != AJF_OK) return st;
+  }
+  for (ajf_ctx* c : rest) {
+    if (!c->uploaded) {
+      st = do_upload(c);
+      if (st != AJF_OK) return st;
+    }
+    st = run_program(c);
+    if (st != AJF_OK) return st;
+  }
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    out[i].S = res[0];
+    out[i].F = res[1];
+    out[i].one_minus_F = res[2];
+    out[i].traces_done = alg == 1 ? real_combinations(c) : 0;
+    out[i].equivalent = eps < 0 ? -1 : (res[1] > 1.0 - eps ? 1 : 0);
+    out[i].reserved = 0;
+    if (alg == 1) c->have_alg1 = true;
+  }
+  if (n_persistent) *n_persistent = static_cast<int32_t>(pers.size());
   return AJF_OK;
 }
 

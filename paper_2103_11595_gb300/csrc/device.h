@@ -81,4 +81,21 @@ struct FinalDev {
   int32_t nblocks;               // blocks of the open-tensor pass
 };
 
+// One network of a persistent-kernel launch (one thread block each). Byte offsets are into the
+// network's own arena; the program is a sequence of ops, each a range of independent steps.
+struct InterpJob {
+  char* base;                    // the network's arena (device)
+  double* out;                   // optional copy of (S, F, 1 - F); nullptr: none
+  int64_t off_leaves, off_steps, off_final, off_inputs, off_scalars, off_traces, off_result;
+  int64_t work0;                 // element offset of the work region in the arena
+  int32_t n_leaves, op0, n_ops;  // leaves; first op and op count in the op table
+  int32_t smem;                  // 1: the work region lives in shared memory for the whole program
+};
+
+struct InterpOp {
+  int32_t kind;                  // LK_SMALL (0) or LK_SPLITK (1)
+  int32_t first, count;          // range of steps (all at one level: independent)
+  int32_t pad;
+};
+
 }  // namespace ajf

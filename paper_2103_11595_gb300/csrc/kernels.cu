@@ -48,51 +48,59 @@ __device__ __forceinline__ int64_t lookup(const int64_t* tab, int nc, int64_t id
 
 // ------------------------------------------------------------------ leaves
 
+// Element e of leaf L (complex, FP64) from the uploaded complex128 matrices.
+__device__ __forceinline__ void leaf_value(const LeafDev& L, const double* __restrict__ in, int64_t e, double& re,
+                                           double& im) {
+  re = 0;
+  im = 0;
+  const int a = L.a;
+  const int64_t dim = int64_t(1) << a;
+  switch (L.kind) {
+    case 0: case 1: case 2: case 3: {  // gate, conj, adjoint, transpose
+      const int64_t r = e >> a, c = e & (dim - 1);
+      const bool swap = (L.kind == 2 || L.kind == 3);
+      const int64_t idx = swap ? (c * dim + r) : (r * dim + c);
+      re = in[2 * (L.src + idx)];
+      im = in[2 * (L.src + idx) + 1];
+      if (L.kind == 1 || L.kind == 2) im = -im;
+      break;
+    }
+    case 4: {  // Kraus stack with open index kappa above the 2a operator bits
+      const int64_t kappa = e >> (2 * a);
+      const int64_t rc = e & (dim * dim - 1);
+      if (kappa < L.nk) {
+        re = in[2 * (L.src + kappa * dim * dim + rc)];
+        im = in[2 * (L.src + kappa * dim * dim + rc) + 1];
+      }
+      break;
+    }
+    case 5: {  // M_N over wires (q..., q'...): a = 2 * noise arity
+      const int an = a / 2;
+      const int64_t nd = int64_t(1) << an;
+      const int64_t R = e >> a, C = e & (dim - 1);
+      const int64_t o = R >> an, op = R & (nd - 1), i = C >> an, ip = C & (nd - 1);
+      for (int k = 0; k < L.nk; ++k) {
+        const int64_t base = L.src + int64_t(k) * nd * nd;
+        const double xr = in[2 * (base + o * nd + i)], xi = in[2 * (base + o * nd + i) + 1];
+        const double yr = in[2 * (base + op * nd + ip)], yi = -in[2 * (base + op * nd + ip) + 1];
+        re += xr * yr - xi * yi;
+        im += xr * yi + xi * yr;
+      }
+      break;
+    }
+    default:  // identity delta[out][in]
+      re = (e == 0 || e == 3) ? 1.0 : 0.0;
+      break;
+  }
+}
+
 template <typename T>
 __global__ void k_leaf(const LeafDev* leaves, const double* __restrict__ in, T* __restrict__ arena) {
   const LeafDev L = leaves[blockIdx.x];
   const int64_t n = int64_t(1) << L.bits;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-    double re = 0, im = 0;
-    const int a = L.a;
-    const int64_t dim = int64_t(1) << a;
-    switch (L.kind) {
-      case 0: case 1: case 2: case 3: {  // gate, conj, adjoint, transpose
-        const int64_t r = e >> a, c = e & (dim - 1);
-        const bool swap = (L.kind == 2 || L.kind == 3);
-        const int64_t idx = swap ? (c * dim + r) : (r * dim + c);
-        re = in[2 * (L.src + idx)];
-        im = in[2 * (L.src + idx) + 1];
-        if (L.kind == 1 || L.kind == 2) im = -im;
-        break;
-      }
-      case 4: {  // Kraus stack with open index kappa above the 2a operator bits
-        const int64_t kappa = e >> (2 * a);
-        const int64_t rc = e & (dim * dim - 1);
-        if (kappa < L.nk) {
-          re = in[2 * (L.src + kappa * dim * dim + rc)];
-          im = in[2 * (L.src + kappa * dim * dim + rc) + 1];
-        }
-        break;
-      }
-      case 5: {  // M_N over wires (q..., q'...): a = 2 * noise arity
-        const int an = a / 2;
-        const int64_t nd = int64_t(1) << an;
-        const int64_t R = e >> a, C = e & (dim - 1);
-        const int64_t o = R >> an, op = R & (nd - 1), i = C >> an, ip = C & (nd - 1);
-        for (int k = 0; k < L.nk; ++k) {
-          const int64_t base = L.src + int64_t(k) * nd * nd;
-          const double xr = in[2 * (base + o * nd + i)], xi = in[2 * (base + o * nd + i) + 1];
-          const double yr = in[2 * (base + op * nd + ip)], yi = -in[2 * (base + op * nd + ip) + 1];
-          re += xr * yr - xi * yi;
-          im += xr * yi + xi * yr;
-        }
-        break;
-      }
-      default:  // identity delta[out][in]
-        re = (e == 0 || e == 3) ? 1.0 : 0.0;
-        break;
-    }
+    double re, im;
+    leaf_value(L, in, e, re, im);
     arena[L.off + e] = static_cast<T>(re);
     arena[L.off + L.plane + e] = static_cast<T>(im);
   }
@@ -614,6 +622,156 @@ __global__ void k_final(const FinalDev* __restrict__ fd, const double2* __restri
   result[2] = (d2 - S) / d2;
 }
 
+// ------------------------------------------------------------------ persistent kernel
+
+// offset(idx) = sum over the map's bits set in idx of 2^pos (bits with pos < 0 address nothing)
+__device__ __forceinline__ int64_t map_offset(const BitMap& m, int64_t idx) {
+  int64_t off = 0;
+  for (int i = 0; i < m.nbits; ++i)
+    if (((idx >> i) & 1) && m.pos[i] >= 0) off += int64_t(1) << m.pos[i];
+  return off;
+}
+
+// First local index handled by this thread when the flat index space continues from `base`
+// (thread t takes the flat indices congruent to t modulo the block size).
+__device__ __forceinline__ int64_t first_local(int64_t base, int unit, int nunits) {
+  return ((unit - base % nunits) % nunits + nunits) % nunits;
+}
+
+// One thread block per network runs the network's whole program: leaves, every step in level
+// order (one block barrier per level), the FP64 trace and F. The work region (all tensors) is
+// kept in shared memory when it fits (job.smem), otherwise it stays in the arena. Steps of one
+// level are independent; a level's outputs are spread over the threads (LK_SMALL: a thread per
+// output element; LK_SPLITK: a warp per output element, lanes along the contracted index,
+// summed in a fixed shuffle order).
+__global__ void __launch_bounds__(256) k_persistent(const InterpJob* __restrict__ jobs,
+                                                    const InterpOp* __restrict__ ops) {
+  extern __shared__ double swork[];
+  __shared__ double red[256];
+  const InterpJob J = jobs[blockIdx.x];
+  double* arena = reinterpret_cast<double*>(J.base);
+  double* W = J.smem ? swork : arena;
+  const int64_t w0 = J.smem ? J.work0 : 0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // leaves
+  {
+    const LeafDev* leaves = reinterpret_cast<const LeafDev*>(J.base + J.off_leaves);
+    const double* in = reinterpret_cast<const double*>(J.base + J.off_inputs);
+    int64_t base = 0;
+    for (int l = 0; l < J.n_leaves; ++l) {
+      const LeafDev L = leaves[l];
+      const int64_t n = int64_t(1) << L.bits;
+      for (int64_t e = first_local(base, tid, nt); e < n; e += nt) {
+        double re, im;
+        leaf_value(L, in, e, re, im);
+        W[L.off - w0 + e] = re;
+        W[L.off - w0 + L.plane + e] = im;
+      }
+      base += n;
+    }
+  }
+  __syncthreads();
+
+  const StepDev* steps = reinterpret_cast<const StepDev*>(J.base + J.off_steps);
+  double2* scalars = reinterpret_cast<double2*>(J.base + J.off_scalars);
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int q = 0; q < J.n_ops; ++q) {
+    const InterpOp op = ops[J.op0 + q];
+    int64_t base = 0;
+    for (int s = op.first; s < op.first + op.count; ++s) {
+      const StepDev& st = steps[s];
+      const int64_t nout = int64_t(1) << st.rc, nk = int64_t(1) << st.rk;
+      const double* A = W + (st.a - w0);
+      const double* B = W + (st.b - w0);
+      if (op.kind == 0) {
+        double* C = W + (st.c - w0);
+        for (int64_t o = first_local(base, tid, nt); o < nout; o += nt) {
+          const int64_t oa = map_offset(st.oa, o), ob = map_offset(st.ob, o);
+          double re = 0, im = 0;
+          for (int64_t kk = 0; kk < nk; ++kk) {
+            const int64_t ia = oa + map_offset(st.ka, kk), ib = ob + map_offset(st.kb, kk);
+            const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+            re += ar * br - ai * bi;
+            im += ar * bi + ai * br;
+          }
+          C[o] = re;
+          C[st.pc + o] = im;
+        }
+      } else {
+        for (int64_t o = first_local(base, warp, nw); o < nout; o += nw) {
+          const int64_t oa = map_offset(st.oa, o), ob = map_offset(st.ob, o);
+          double re = 0, im = 0;
+          for (int64_t kk = lane; kk < nk; kk += 32) {
+            const int64_t ia = oa + map_offset(st.ka, kk), ib = ob + map_offset(st.kb, kk);
+            const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+            re += ar * br - ai * bi;
+            im += ar * bi + ai * br;
+          }
+          for (int w = 16; w > 0; w >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, w);
+            im += __shfl_xor_sync(0xffffffffu, im, w);
+          }
+          if (lane == 0) {
+            if (st.scalar_slot >= 0) {
+              scalars[st.scalar_slot] = make_double2(re, im);
+            } else {
+              W[st.c - w0 + o] = re;
+              W[st.c - w0 + st.pc + o] = im;
+            }
+          }
+        }
+      }
+      base += nout;
+    }
+    __syncthreads();
+  }
+
+  // FP64 end: common factor, traces (Alg. I), sum |t|^2, F and 1 - F
+  const FinalDev& f = *reinterpret_cast<const FinalDev*>(J.base + J.off_final);
+  double sr = ldexp(1.0, f.loops), si = 0;
+  for (int i = 0; i < f.n_scalars; ++i) {
+    const double2 v = scalars[i];
+    const double nr = sr * v.x - si * v.y, ni = sr * v.y + si * v.x;
+    sr = nr;
+    si = ni;
+  }
+  double* traces = reinterpret_cast<double*>(J.base + J.off_traces);
+  const int64_t n = int64_t(1) << f.open_bits;
+  double acc = 0;
+  for (int64_t j = tid; j < n; j += nt) {
+    double tr = 1, ti = 0;
+    if (f.open_off >= 0) {
+      const int64_t off = map_offset(f.open_map, j);
+      tr = W[f.open_off - w0 + off];
+      ti = W[f.open_off - w0 + f.open_plane + off];
+    }
+    const double vr = tr * sr - ti * si, vi = tr * si + ti * sr;
+    traces[2 * j] = vr;
+    traces[2 * j + 1] = vi;
+    acc += vr * vr + vi * vi;
+  }
+  red[tid] = acc;
+  __syncthreads();
+  for (int w = nt / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double S = f.alg == 2 ? sr : red[0];
+    const double d2 = ldexp(1.0, 2 * f.n_qubits);
+    double* result = reinterpret_cast<double*>(J.base + J.off_result);
+    result[0] = S;
+    result[1] = S / d2;
+    result[2] = (d2 - S) / d2;
+    if (J.out) {
+      J.out[0] = S;
+      J.out[1] = S / d2;
+      J.out[2] = (d2 - S) / d2;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launch wrappers
 
 static size_t table_bytes(const BitMap* const* maps, int n) {
@@ -720,6 +878,22 @@ cudaError_t set_kernel_smem_limits() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;
+}
+
+}  // namespace ajf
+
+namespace ajf {
+
+cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem,
+                              cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_persistent<<<n_jobs, 256, smem, s>>>(d_jobs, d_ops);
+  return cudaGetLastError();
 }
 
 }  // namespace ajf

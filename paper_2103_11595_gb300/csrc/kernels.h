@@ -31,6 +31,12 @@ cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, i
 cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
                          const double2* scalars, double* traces, double* partial, double* result, bool f64,
                          cudaStream_t s);
+// Persistent kernel: one thread block per network runs that network's whole program (leaves,
+// all steps level by level, the FP64 trace and F) -- n_jobs networks in one launch. `smem`:
+// dynamic shared memory per block (the largest work region among the jobs with job.smem = 1).
+cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem,
+                              cudaStream_t s);
+constexpr size_t kPersistentSmemMax = 96 * 1024;
 
 // Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (FP64, row-major) =
 // sum_{i + j < terms} A_i[M][K] . B_j[N][K]^T for the split terms A_t, B_t (byte offsets from

@@ -219,7 +219,7 @@ cudaError_t MlpScorer::score(const float* weights_host, const float* x, int n, f
 cudaError_t mlp_train(const float* pairs, int n_pairs, int epochs, int batch, float lr, uint64_t seed, float* weights,
                       double* final_loss) {
   if (n_pairs <= 0 || batch <= 0) return cudaErrorInvalidValue;
-  const int P = batch, B = 2 * P;
+  const int P = batch < n_pairs ? batch : n_pairs, B = 2 * P;
   std::vector<float> w(kMlpParams);
   mlp_init(w.data(), seed);
   float *d_w, *d_g, *d_m, *d_v, *d_data, *d_x, *d_h1, *d_h2, *d_s, *d_ds, *d_dh1, *d_dh2, *d_loss;

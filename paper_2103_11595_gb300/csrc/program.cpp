@@ -119,8 +119,10 @@ size_t mode_bytes(int mode) { return mode == OPM_F64 ? 8 : (mode >= OPM_BF16X2 ?
 
 }  // namespace
 
-Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok) {
+Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok,
+              bool persistent) {
   Program P;
+  P.persistent = persistent;
   P.alg = net.alg;
   P.precision = precision;
   P.f64 = true;  // tensors are FP64 in HBM in every mode; the precision mode sets the GEMM operands
@@ -149,7 +151,19 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     const int ma = static_cast<int>(fa.size()), nb = static_cast<int>(fb.size());
     const double mnk = std::ldexp(1.0, ma + nb + rk);
     std::vector<int> out;
-    if (rc == 0) {
+    if (persistent) {
+      // one thread block runs the step: a warp per output where the contraction is long and
+      // the output short, a thread per output otherwise
+      const bool a_big = la.size() >= lb.size();
+      I.cls = (rc == 0 || (rc <= 6 && rk >= 8)) ? C_SPLITK : C_SMALL;
+      I.a = st.a;
+      I.b = st.b;
+      I.shared = sh;
+      const auto& big = a_big ? fa : fb;
+      const auto& small = a_big ? fb : fa;
+      out = big;
+      out.insert(out.end(), small.begin(), small.end());
+    } else if (rc == 0) {
       I.cls = rk >= kDotTileBits ? C_DOT : C_SPLITK;
       I.a = st.a;
       I.b = st.b;
@@ -483,6 +497,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   P.off_traces = off;
   off += align_up(sizeof(double) * 2 * static_cast<size_t>(P.n_traces));
   P.off_work = off;
+  P.work_bytes = ff.peak();
   P.arena_bytes = off + ff.peak();
 
   // ---- rebase work-region offsets to the arena

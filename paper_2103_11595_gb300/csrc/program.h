@@ -50,7 +50,9 @@ struct Program {
   size_t off_traces = 0;                      // double2 per trace (Alg. I)
   size_t off_status = 0;                      // int32 device status words
   size_t off_work = 0;                        // tensors and GEMM scratch
+  size_t work_bytes = 0;                      // size of the work region
   size_t arena_bytes = 0;
+  bool persistent = false;                    // lowered for the persistent kernel (CUDA-core steps only)
   // statistics
   double flops = 0, bytes = 0, gemm_flops = 0, gemm_bytes = 0;
   int n_gemm = 0;
@@ -59,6 +61,9 @@ struct Program {
 
 // Lower `path` over `net` to a device program for `precision`. `inputs_complex` is the number
 // of complex128 values in the packed input buffer. `tc_ok`: tensor-core GEMMs may be used.
-Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok);
+// `persistent`: every step becomes a CUDA-core gather step (LK_SMALL) or a reduction step
+// (LK_SPLITK), so that one thread block of the persistent kernel can run the whole program.
+Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok,
+              bool persistent = false);
 
 }  // namespace ajf

@@ -93,7 +93,7 @@ def cmd_eval(a):
         row = {"seed": 10000 + i, "n": inst.n, "gates": len(inst.ideal), "noises": len(inst.noises)}
         runs = [("greedy1", "greedy", 1), ("learned1", "learned", 1)]
         if i < a.restart_subset:
-            runs += [("auto8", "auto", 8), ("learned8", "learned", 8)]
+            runs += [("greedy8", "greedy", 8), ("auto8", "auto", 8), ("learned8", "learned", 8)]
         for name, planner, trials in runs:
             t0 = time.time()
             try:
@@ -142,12 +142,13 @@ def cmd_eval(a):
     summary = {
         "held_out": len(rows),
         "geomean_cmacs_learned1_over_greedy1": geo("learned1", "greedy1"),
+        "geomean_cmacs_learned8_over_greedy8": geo("learned8", "greedy8"),
         "geomean_cmacs_learned8_over_auto8": geo("learned8", "auto8"),
         "learned_path_kept_1": sum(1 for r in rows if r["learned1"]["used"] == 3),
         "learned_path_kept_8": sum(1 for r in rows if "learned8" in r and r["learned8"]["used"] == 3),
         "restart_subset": min(a.restart_subset, len(rows)),
         "mean_plan_s": {k: float(np.mean([r[k]["s"] for r in rows if k in r]))
-                        for k in ("greedy1", "learned1", "auto8", "learned8")},
+                        for k in ("greedy1", "learned1", "greedy8", "auto8", "learned8")},
         "fj_checked": len(fj), "max_abs_dF_learned_vs_greedy": max(fj) if fj else None,
         "executable_held_out": sum(1 for r in rows if r["learned1"]["arena"] <= a.fj_budget),
         "mid_fj_checked": len(mid), "mid_max_abs_dF_learned_vs_greedy": max((m["dF"] for m in mid), default=None),
