@@ -494,6 +494,9 @@ def run_small_networks(args, world, rank, local):
             torch.cuda.synchronize()
         return total
 
+    # a tiny step takes well under a millisecond: time enough steps for the clock sampler (200 ms)
+    if args.workload == "tiny":
+        args.steps = max(args.steps, 2000)
     with ClockSampler(dev) as clk:
         total_ms = timed(args.steps, args.warmup)
     clocks = clk.summary()
