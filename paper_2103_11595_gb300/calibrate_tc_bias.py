@@ -2,13 +2,15 @@
 
 The tcgen05 accumulation truncates toward zero, shrinking every promoted K-block partial by a
 small relative amount e; the GEMM epilogue multiplies its result by (1 + e). This script measures
-e for the TF32 and bf16 kernels on held-out circuits (n = 16 line, U3/CX layers, 10 noises;
-generator seeds 100..105 -- the tests use seeds 0..9): for each circuit it evaluates F_J with the
-FP64 path and with a split tensor-core mode run with AJF_TC_BIAS = 0 and = 1e-7 (the override is
-read once per process, so each setting runs in its own process), and solves the linear relation
-dF(e) = 0 per circuit.
+e for the TF32 and bf16 kernels on held-out circuits of two families -- Alg. II of the mid
+workload (n = 16 line, U3/CX layers, 10 noises; generator seeds 100..105, the tests use 0..9)
+and Alg. I of the batching workload (n = 8..20, 6 depolarising noises, 4096 traces; seeds
+1000..1007, the tests and bench use 0..63). For each circuit it evaluates F_J with the FP64 path
+and with a split tensor-core mode run with AJF_TC_BIAS = 0 and = 1e-7 (the override is read once
+per process, so each setting runs in its own process), and solves the linear relation dF(e) = 0
+per circuit. The constant is the mean over all circuits of both families.
 
-    python -m paper_2103_11595_gb300.calibrate_tc_bias [--seeds 100,101,102,103,104,105]
+    python -m paper_2103_11595_gb300.calibrate_tc_bias [--mid 100,...] [--batching 1000,...] [--json out]
 """
 from __future__ import annotations
 
@@ -23,26 +25,37 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MODES = {"tf32": "tf32x3", "bf16": "bf16x6"}
 
 
-def _evaluate(out_path: str, seeds: str) -> None:
+def _circuits(mid: str, batching: str):
+    from paper_2103_11595_gb300 import workloads as W
+    out = []
+    for seed in [int(x) for x in mid.split(",") if x]:
+        out.append((f"mid{seed}", W.mid(seed), 2))
+    for seed in [int(x) for x in batching.split(",") if x]:
+        out.append((f"batch{seed}", W.batching_circuit(seed), 1))
+    return out
+
+
+def _evaluate(out_path: str, mid: str, batching: str) -> None:
     sys.path.insert(0, ROOT)
     from paper_2103_11595_gb300 import ajf
-    from paper_2103_11595_gb300 import workloads as W
     res = {}
-    for seed in [int(s) for s in seeds.split(",")]:
-        inst = W.mid(seed)
+    for name, inst, alg in _circuits(mid, batching):
         for prec in ["f64"] + list(MODES.values()):
             with ajf.Context(0) as c:
                 ajf.load_instance(c.handle, inst)
-                ajf.ajf_plan(c.handle, 2, precision=prec, trials=16)
-                res[f"{seed}/{prec}"] = ajf.ajf_fidelity_alg2(c.handle)["F"]
+                ajf.ajf_plan(c.handle, alg, precision=prec, trials=16)
+                r = ajf.ajf_fidelity_alg1(c.handle) if alg == 1 else ajf.ajf_fidelity_alg2(c.handle)
+                res[f"{name}/{prec}"] = r["F"]
     with open(out_path, "w") as f:
         json.dump(res, f)
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--seeds", default="100,101,102,103,104,105")
-    ap.add_argument("--_evaluate", nargs=2, help=argparse.SUPPRESS)
+    ap.add_argument("--mid", default="100,101,102,103,104,105")
+    ap.add_argument("--batching", default="1000,1001,1002,1003,1004,1005,1006,1007")
+    ap.add_argument("--json", default="")
+    ap.add_argument("--_evaluate", nargs=3, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args._evaluate:
         _evaluate(*args._evaluate)
@@ -56,20 +69,28 @@ def main():
             path = os.path.join(tmp, f"b{bias}.json")
             env = dict(os.environ, AJF_TC_BIAS=bias)
             subprocess.run([sys.executable, "-m", "paper_2103_11595_gb300.calibrate_tc_bias", "--_evaluate", path,
-                            args.seeds], check=True, env=env, cwd=ROOT)
+                            args.mid, args.batching], check=True, env=env, cwd=ROOT)
             with open(path) as f:
                 runs[bias] = json.load(f)
-    seeds = args.seeds.split(",")
+    names = [n for n, _, _ in _circuits(args.mid, args.batching)]
+    out = {}
     for kind, prec in MODES.items():
-        eps = []
-        for s in seeds:
-            f64 = runs["0"][f"{s}/f64"]
-            d0 = runs["0"][f"{s}/{prec}"] - f64
-            d1 = runs["1e-7"][f"{s}/{prec}"] - f64
-            eps.append(-d0 * 1e-7 / (d1 - d0))
-        m = sum(eps) / len(eps)
-        sd = (sum((e - m) ** 2 for e in eps) / len(eps)) ** 0.5
-        print(f"{kind}: e = {m:.3e} +- {sd:.1e} ({prec}, seeds {args.seeds})")
+        eps = {}
+        for n in names:
+            f64 = runs["0"][f"{n}/f64"]
+            d0 = runs["0"][f"{n}/{prec}"] - f64
+            d1 = runs["1e-7"][f"{n}/{prec}"] - f64
+            eps[n] = -d0 * 1e-7 / (d1 - d0)
+        vals = list(eps.values())
+        m = sum(vals) / len(vals)
+        sd = (sum((e - m) ** 2 for e in vals) / len(vals)) ** 0.5
+        fam = {f: [v for k, v in eps.items() if k.startswith(f)] for f in ("mid", "batch")}
+        fm = {f: (sum(v) / len(v) if v else None) for f, v in fam.items()}
+        print(f"{kind}: e = {m:.3e} +- {sd:.1e} ({prec}; mid {fm['mid']}, batching {fm['batch']})")
+        out[kind] = {"e": m, "sd": sd, "per_family": fm, "per_circuit": eps}
+    if args.json:
+        with open(args.json, "w") as f:
+            json.dump(out, f)
 
 
 if __name__ == "__main__":

@@ -315,7 +315,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
         break;
       case LK_GEMM_TC:
         e = launch_gemm_tc(base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<double*>(base + ln.c_off), ln.M, ln.N,
-                           ln.K, ln.tc_kind, status, s);
+                           ln.K, ln.tc_kind, reinterpret_cast<double*>(base + ln.ws_off), ln.ksplit, status, s);
         break;
       default:
         e = cudaErrorInvalidValue;
@@ -699,7 +699,8 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
   pi.planner_used = c->path.planner;
   pi.n_launches = 3;  // leaves + final pass + final sum
-  for (auto& ln : P.launches) pi.n_launches += (ln.kind == LK_SPLITK || ln.kind == LK_DOT) ? 2 : 1;
+  for (auto& ln : P.launches)
+    pi.n_launches += (ln.kind == LK_SPLITK || ln.kind == LK_DOT || (ln.kind == LK_GEMM_TC && ln.ksplit > 1)) ? 2 : 1;
   pi.n_tc_gemms = P.tensor_cores;
   pi.plan_cached = cached ? 1 : 0;
   pi.upload_bytes = static_cast<double>(P.desc_bytes + P.input_bytes);
@@ -869,9 +870,12 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
   if (!tc_gemm_supported(M, N, K, kind)) return AJF_E_UNSUPPORTED;
   const size_t es = kind == 1 ? 2 : 4;
   const size_t abytes = size_t(npass) * M * K * es, bbytes = size_t(npass) * N * K * es, cbytes = size_t(M) * N * 8;
+  const int ksplit = tc_gemm_splits(M, N, K, kind);
+  const size_t wbytes = ksplit > 1 ? size_t(ksplit) * cbytes : 0;
   char* d = nullptr;
   const size_t off_b = (abytes + 255) / 256 * 256, off_c = off_b + (bbytes + 255) / 256 * 256;
-  const size_t off_s = off_c + (cbytes + 255) / 256 * 256;
+  const size_t off_w = off_c + (cbytes + 255) / 256 * 256;
+  const size_t off_s = off_w + (wbytes + 255) / 256 * 256;
   if (cudaMalloc(&d, off_s + 256) != cudaSuccess) return AJF_E_NOMEM;
   ajf_status st = AJF_OK;
   int status = 0;
@@ -885,7 +889,8 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
       cudaMemset(d + off_s, 0, 256) != cudaSuccess)
     st = AJF_E_CUDA;
   if (st == AJF_OK && launch_gemm_tc(d, ao, bo, npass, reinterpret_cast<double*>(d + off_c), M, N, K, kind,
-                                     reinterpret_cast<int*>(d + off_s), 0) != cudaSuccess)
+                                     reinterpret_cast<double*>(d + off_w), ksplit, reinterpret_cast<int*>(d + off_s),
+                                     0) != cudaSuccess)
     st = AJF_E_CUDA;
   if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
   if (st == AJF_OK && (cudaMemcpy(C, d + off_c, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -937,8 +942,9 @@ ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t* code) 
   const int64_t ao[1] = {0}, bo[1] = {static_cast<int64_t>(off_b)};
   if (cudaMemset(d, 0, off_s + 256) != cudaSuccess) st = AJF_E_CUDA;
   if (st == AJF_OK &&
-      launch_gemm_tc_ex(d, ao, bo, 1, reinterpret_cast<double*>(d + off_c), M, N, K, 0, reinterpret_cast<int*>(d + off_s),
-                        0, static_cast<unsigned long long>(wait_ms * 1e6), 1) != cudaSuccess)
+      launch_gemm_tc_ex(d, ao, bo, 1, reinterpret_cast<double*>(d + off_c), M, N, K, 0, nullptr, 1,
+                        reinterpret_cast<int*>(d + off_s), 0, static_cast<unsigned long long>(wait_ms * 1e6),
+                        1) != cudaSuccess)
     st = AJF_E_CUDA;
   if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
   int status = 0;

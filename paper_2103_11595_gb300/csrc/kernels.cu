@@ -513,11 +513,15 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __
   const int tr = tid / (BN / TN), tc = tid % (BN / TN);
   const int64_t nbn = (N + BN - 1) / BN;
   const int64_t m0 = (int64_t(blockIdx.x) / nbn) * BM, n0 = (int64_t(blockIdx.x) % nbn) * BN;
-  T acc[TM][TN];
+  // FP64: one accumulator per output. FP32: the products of each BK-long K tile are summed in
+  // FP32, and the tile sums are added into a compensated (Kahan) FP32 accumulator, so that long
+  // contractions do not lose the small late addends of a plain FP32 running sum.
+  constexpr bool kComp = sizeof(T) == 4;
+  T acc[TM][TN], comp[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = comp[i][j] = 0;
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
     for (int e = tid; e < BM * BK; e += NT) {
       const int r = e / BK, k = e % BK;
@@ -530,6 +534,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __
       Bs[k][r] = (gn < N && gk < K) ? B[gn * K + gk] : T(0);
     }
     __syncthreads();
+    T part[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) part[i][j] = 0;
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T a[TM], b[TN];
@@ -540,8 +549,21 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < TN; ++j) part[i][j] += a[i] * b[j];
     }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        if (kComp) {
+          const T y = part[i][j] - comp[i][j];
+          const T t = acc[i][j] + y;
+          comp[i][j] = (t - acc[i][j]) - y;
+          acc[i][j] = t;
+        } else {
+          acc[i][j] += part[i][j];
+        }
+      }
     __syncthreads();
   }
 #pragma unroll
@@ -839,9 +861,9 @@ cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, i
     k_gemm_simt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, s>>>(static_cast<const double*>(A), static_cast<const double*>(B),
                                                              static_cast<double*>(C), M, N, K);
   } else {
-    const unsigned grid = unsigned(((N + 127) / 128) * ((M + 127) / 128));
-    k_gemm_simt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, s>>>(static_cast<const float*>(A), static_cast<const float*>(B),
-                                                              static_cast<double*>(C), M, N, K);
+    const unsigned grid = unsigned(((N + 63) / 64) * ((M + 127) / 128));
+    k_gemm_simt<float, 128, 64, 8, 8, 4><<<grid, 256, 0, s>>>(static_cast<const float*>(A), static_cast<const float*>(B),
+                                                             static_cast<double*>(C), M, N, K);
   }
   return cudaGetLastError();
 }

@@ -43,13 +43,17 @@ constexpr size_t kPersistentSmemMax = 96 * 1024;
 // `base`), FP32 accumulation promoted per K block. kind 0: tf32, 1: bf16.
 // Returns cudaErrorNotSupported when the shape is not tile-aligned.
 bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
+// K splits for an M x N x K GEMM: GEMMs with fewer 128 x BN tiles than SMs divide K over several
+// CTAs, each writing an FP64 partial tile to a workspace of ksplit * M * N doubles that a
+// deterministic pass then sums into C. 1 = no split (no workspace).
+int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind);
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                           int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s);
+                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s);
 // Same with an explicit bound on every device-side wait and a test hook: stall_loads = 1 makes the
 // producer issue no loads, so the MMA and epilogue waits expire and the kernel reports a status
 // code and returns.
 cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                              int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s,
+                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
                               unsigned long long wait_ns, int stall_loads);
 
 }  // namespace ajf

@@ -410,7 +410,12 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       P.launches.push_back(lp);
       release_dead(exec_pos[s], {I.a, I.b});
       toff[c] = ff.alloc(tensor_bytes(c));
+      const int ksplit = use_tc ? tc_gemm_splits(Mt, Nt, Kt, tc_kind) : 1;
+      const size_t ws_bytes = ksplit > 1 ? size_t(ksplit) * size_t(Mt) * size_t(Nt) * 8 : 0;
+      const size_t ws = ws_bytes ? ff.alloc(ws_bytes) : 0;
       Launch lg;
+      lg.ksplit = ksplit;
+      lg.ws_off = static_cast<int64_t>(ws);
       lg.kind = use_tc ? LK_GEMM_TC : LK_GEMM_SIMT;
       lg.op_f64 = op_f64 ? 1 : 0;
       lg.M = Mt;
@@ -438,6 +443,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       P.launches.push_back(lg);
       for (int t = 0; t < gterms; ++t) ff.release(xo[t], xbytes);
       for (int t = 0; t < gterms; ++t) ff.release(yo[t], ybytes);
+      if (ws_bytes) ff.release(ws, ws_bytes);
       ++i;
     }
   }
@@ -532,6 +538,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       g.b_off[t] += static_cast<int64_t>(P.off_work);
     }
     g.c_off += static_cast<int64_t>(P.off_work);
+    g.ws_off += static_cast<int64_t>(P.off_work);
   }
   if (f.open_off >= 0) f.open_off += wel;
   return P;

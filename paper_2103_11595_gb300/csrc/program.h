@@ -21,6 +21,8 @@ struct Launch {
   int32_t tc_kind = 0;           // 0 tf32, 1 bf16
   int32_t op_f64 = 1;            // CUDA-core GEMM: FP64 (1) or FP32 (0) operands
   int64_t c_off = 0;             // byte offset of C
+  int32_t ksplit = 1;            // tensor-core GEMM: K splits (> 1: FP64 partials in the workspace)
+  int64_t ws_off = 0;            // byte offset of the split workspace (ksplit * M * N doubles)
   int64_t M = 0, N = 0, K = 0;
   double flops = 0, bytes = 0;   // algorithmic work of the complex step this launch belongs to
 };

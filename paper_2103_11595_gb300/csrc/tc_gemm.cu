@@ -20,7 +20,9 @@
 //    with a mean e per promoted block that was calibrated on GB300 (kBlockBias below), so the
 //    epilogue multiplies the result by (1 + e) once when it stores it.
 //
-// Kernel structure (one CTA per 128 x BN output tile, 320 threads):
+// Kernel structure (persistent: one CTA per SM walks the 128 x BN output tiles in a grouped
+// raster order; 320 threads; the slot and TMEM-buffer rings continue from tile to tile so the
+// loads and MMAs of the next tile overlap the FP64 store of the current one):
 //   warp 0, lane 0 : TMA producer -- for every K block and term, the A tile (128 rows x 128 B) and
 //                    the B tile (BN rows x 128 B), 128-byte swizzle, into a ring of slots
 //                    (mbarrier expect-tx / complete-tx);
@@ -28,8 +30,11 @@
 //                    a ring of TMEM partial buffers and tcgen05.commit to release slots and hand
 //                    partials to the epilogue;
 //   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
-//                    the BN columns: tcgen05.ld, FP32 round-to-nearest accumulation in registers,
-//                    de-biased FP64 store of C (rows < M, columns < N).
+//                    the BN columns of its rows: tcgen05.ld, FP32 round-to-nearest accumulation in
+//                    registers, de-biased FP64 store of the tile (rows < M, columns < N).
+// Work items are (tile, K split) pairs. GEMMs with fewer tiles than SMs, or with more than
+// kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP64 partial
+// tile to a workspace and k_split_sum adds the splits in a fixed order (deterministic).
 // Every wait is bounded by the global timer (2 s); on expiry the kernel records a status code,
 // stops issuing work, releases TMEM and returns, so the host sees AJF_E_TIMEOUT instead of a hang.
 #include <cuda.h>
@@ -50,6 +55,14 @@ constexpr int kMaxSlots = 8;
 constexpr int kMaxBufs = 4;
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
+constexpr int kEpiWarp0 = 2;       // epilogue warps 2..9: warp w reads TMEM lanes 32 * (w % 4) .. + 31
+// The FP32 register accumulation of promoted partials spans at most this many K blocks: longer
+// contractions are split over K (FP64 partial tiles summed afterwards), so the small late
+// partials of a long FP32 running sum are not lost.
+constexpr int kMaxBlocksPerSplit = 64;
+// SM count the K-split heuristic plans for (GB300); the split count only changes how work is
+// divided, never the result beyond rounding.
+constexpr int64_t kPlanSMs = 152;
 constexpr int kMaxTerms = 3;
 constexpr uint32_t kSmemBudget = 192 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -70,6 +83,11 @@ struct TcParams {
   int64_t M, N;
   double scale;                      // de-biasing factor applied at the store
   int32_t terms, kblocks, ntn, slots, bufs;
+  int32_t mtn;                       // tiles along M
+  int32_t group;                     // M tiles per raster group (L2 reuse of B tiles)
+  int32_t ksplit, kb_split;          // K splits and K blocks per split
+  int64_t tiles;
+  double* ws;                        // split partials [ksplit][M][N] (ksplit > 1)
   uint32_t idesc;
   uint32_t slot_bytes;
   unsigned long long wait_ns;        // bound of every wait
@@ -174,13 +192,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int BN, bool kBF16>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
   static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "tile width");
-  constexpr int HALF = BN / 2;                       // columns per epilogue warp
-  constexpr int CH = HALF < 32 ? HALF : 32;          // columns per drain chunk
+  constexpr int COLS = BN / 2;                       // columns per epilogue thread (one TMEM lane = one row)
+  constexpr int CH = COLS < 16 ? COLS : 16;          // columns per drain chunk
   constexpr uint32_t a_bytes = kBM * kRowBytes, b_bytes = BN * kRowBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -194,8 +218,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   const uint32_t acce0 = accf0 + 8 * kMaxBufs;    // partial buffer b drained (epilogue -> MMA)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 16 * kMaxBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 4);
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x / p.ntn) * kBM;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.x % p.ntn) * BN;
+  // persistent tile loop: tile = blockIdx.x, blockIdx.x + gridDim.x, ...; every role walks the
+  // same tiles, and its ring positions (slots, TMEM buffers) continue across tiles
+  // grouped raster: `group` M tiles sweep the N tiles together, so concurrently running CTAs
+  // share each B tile through L2 instead of streaming all of B once per M tile. Work item wi is
+  // tile wi % tiles of K split wi / tiles (tile and work counts fit 32 bits).
+  const uint32_t tiles = static_cast<uint32_t>(p.tiles);
+  const uint32_t nwork = tiles * static_cast<uint32_t>(p.ksplit);
+  auto work_item = [&](uint32_t wi, int32_t& m0, int32_t& n0, int& kb0, int& kb1) {
+    const uint32_t tile = wi % tiles, ks = wi / tiles;
+    const uint32_t per_group = static_cast<uint32_t>(p.group) * static_cast<uint32_t>(p.ntn);
+    const uint32_t g = tile / per_group, r = tile % per_group;
+    const uint32_t first_m = g * static_cast<uint32_t>(p.group);
+    const uint32_t left = static_cast<uint32_t>(p.mtn) - first_m;
+    const uint32_t gm = left < static_cast<uint32_t>(p.group) ? left : static_cast<uint32_t>(p.group);
+    m0 = static_cast<int32_t>((first_m + r % gm) * kBM);
+    n0 = static_cast<int32_t>((r / gm) * BN);
+    kb0 = static_cast<int>(ks) * p.kb_split;
+    kb1 = kb0 + p.kb_split < p.kblocks ? kb0 + p.kb_split : p.kblocks;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -223,116 +264,161 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles
-    const int iters = p.stall_loads ? 0 : kblocks * T;
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % S;
-      if (*abort_flag || !mbar_wait(empty0 + 8 * s, (static_cast<uint32_t>(it / S) & 1u) ^ 1u, p.wait_ns, p.status, 11)) {
-        *abort_flag = 1;
-        break;
+    int slot = 0;
+    uint32_t phase = 0;  // position in the slot ring, continued across tiles
+    bool ok = !p.stall_loads;
+    for (uint32_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+      int32_t m0, n0;
+      int kb0, kb1;
+      work_item(wi, m0, n0, kb0, kb1);
+      for (int kb = kb0; kb < kb1 && ok; ++kb) {
+        for (int t = 0; t < T; ++t) {
+          if (*abort_flag || !mbar_wait(empty0 + 8 * slot, phase ^ 1u, p.wait_ns, p.status, 11)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const uint32_t sa = smem_u32(smem + slot * p.slot_bytes);
+          const int32_t kx = kb * (kRowBytes / (kBF16 ? 2 : 4));
+          mbar_expect_tx(full0 + 8 * slot, a_bytes + b_bytes);
+          tma_load_2d(sa, &p.amap[t], kx, m0, full0 + 8 * slot);
+          tma_load_2d(sa + a_bytes, &p.bmap[t], kx, n0, full0 + 8 * slot);
+          if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
+          }
+        }
       }
-      const int kb = it / T, t = it % T;
-      const uint32_t sa = smem_u32(smem + s * p.slot_bytes);
-      const int32_t kx = kb * (kRowBytes / (kBF16 ? 2 : 4));
-      mbar_expect_tx(full0 + 8 * s, a_bytes + b_bytes);
-      tma_load_2d(sa, &p.amap[t], kx, static_cast<int32_t>(m0), full0 + 8 * s);
-      tma_load_2d(sa + a_bytes, &p.bmap[t], kx, static_cast<int32_t>(n0), full0 + 8 * s);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     bool ok = true;
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
-      const int b = kb % NB;
-      if (*abort_flag || !mbar_wait(acce0 + 8 * b, (static_cast<uint32_t>(kb / NB) & 1u) ^ 1u, p.wait_ns, p.status, 14)) {
-        ok = false;
-        break;
-      }
-      // slot of term t of this block: (kb * T + t) % S; descriptors are kept in registers (a
-      // dynamically indexed array would live in local memory and stall every MMA issue)
-      const int s0 = (kb * T) % S, s1 = (kb * T + 1) % S, s2 = (kb * T + 2) % S;
-      if (!mbar_wait(full0 + 8 * s0, static_cast<uint32_t>((kb * T) / S) & 1u, p.wait_ns, p.status, 12) ||
-          (T > 1 && !mbar_wait(full0 + 8 * s1, static_cast<uint32_t>((kb * T + 1) / S) & 1u, p.wait_ns, p.status, 12)) ||
-          (T > 2 && !mbar_wait(full0 + 8 * s2, static_cast<uint32_t>((kb * T + 2) / S) & 1u, p.wait_ns, p.status, 12))) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem);
-      const uint64_t ad0 = smem_desc(base + s0 * p.slot_bytes), bd0 = smem_desc(base + s0 * p.slot_bytes + a_bytes);
-      const uint64_t ad1 = smem_desc(base + s1 * p.slot_bytes), bd1 = smem_desc(base + s1 * p.slot_bytes + a_bytes);
-      const uint64_t ad2 = smem_desc(base + s2 * p.slot_bytes), bd2 = smem_desc(base + s2 * p.slot_bytes + a_bytes);
-      const uint32_t dst = tmem + static_cast<uint32_t>(b * BN);
-      uint32_t acc = 0;
-      // one product A_i . B_j over the block: 4 instructions, 32 bytes of K each (+2 in the
-      // descriptor's 16-byte address field)
-      auto product = [&](uint64_t ad, uint64_t bd) {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          mma<kBF16>(dst, ad + 2 * kk, bd + 2 * kk, p.idesc, acc);
-          acc = 1;
+    int buf = 0, slot = 0;
+    uint32_t bphase = 0, phase = 0;  // ring positions, continued across tiles
+    for (uint32_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+      int32_t m0, n0;
+      int kb0, kb1;
+      work_item(wi, m0, n0, kb0, kb1);
+      for (int kb = kb0; kb < kb1; ++kb) {
+        const int b = buf;
+        if (*abort_flag || !mbar_wait(acce0 + 8 * b, bphase ^ 1u, p.wait_ns, p.status, 14)) {
+          ok = false;
+          break;
         }
-      };
-      // correction products (i + j >= 1), smallest first, then the leading product
-      if (T == 3) {
-        product(ad0, bd2);
-        product(ad1, bd1);
-        product(ad2, bd0);
+        if (++buf == NB) {
+          buf = 0;
+          bphase ^= 1u;
+        }
+        // slots of the block's terms, in ring order; descriptors are kept in registers (a
+        // dynamically indexed array would live in local memory and stall every MMA issue)
+        int st[3] = {0, 0, 0};
+        bool got = true;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          if (t < T) {
+            st[t] = slot;
+            got = got && mbar_wait(full0 + 8 * slot, phase, p.wait_ns, p.status, 12);
+            if (++slot == S) {
+              slot = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+        if (!got) {
+          ok = false;
+          break;
+        }
+        const int s0 = st[0], s1 = st[1], s2 = st[2];
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem);
+        const uint64_t ad0 = smem_desc(base + s0 * p.slot_bytes), bd0 = smem_desc(base + s0 * p.slot_bytes + a_bytes);
+        const uint64_t ad1 = smem_desc(base + s1 * p.slot_bytes), bd1 = smem_desc(base + s1 * p.slot_bytes + a_bytes);
+        const uint64_t ad2 = smem_desc(base + s2 * p.slot_bytes), bd2 = smem_desc(base + s2 * p.slot_bytes + a_bytes);
+        const uint32_t dst = tmem + static_cast<uint32_t>(b * BN);
+        uint32_t acc = 0;
+        // one product A_i . B_j over the block: 4 instructions, 32 bytes of K each (+2 in the
+        // descriptor's 16-byte address field)
+        auto product = [&](uint64_t ad, uint64_t bd) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            mma<kBF16>(dst, ad + 2 * kk, bd + 2 * kk, p.idesc, acc);
+            acc = 1;
+          }
+        };
+        // correction products (i + j >= 1), smallest first, then the leading product
+        if (T == 3) {
+          product(ad0, bd2);
+          product(ad1, bd1);
+          product(ad2, bd0);
+        }
+        if (T >= 2) {
+          product(ad0, bd1);
+          product(ad1, bd0);
+        }
+        product(ad0, bd0);
+        mma_commit(empty0 + 8 * s0);
+        if (T > 1) mma_commit(empty0 + 8 * s1);
+        if (T > 2) mma_commit(empty0 + 8 * s2);
+        mma_commit(accf0 + 8 * b);
       }
-      if (T >= 2) {
-        product(ad0, bd1);
-        product(ad1, bd0);
-      }
-      product(ad0, bd0);
-      mma_commit(empty0 + 8 * s0);
-      if (T > 1) mma_commit(empty0 + 8 * s1);
-      if (T > 2) mma_commit(empty0 + 8 * s2);
-      mma_commit(accf0 + 8 * b);
     }
     if (!ok) *abort_flag = 1;
-  } else if (warp >= 2) {
-    // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP64
-    const int q = warp & 3, h = (warp - 2) >> 2;
+  } else if (warp >= kEpiWarp0) {
+    // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP64 per tile
+    const int q = warp & 3, h = (warp - kEpiWarp0) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
-    float acc[HALF];
-#pragma unroll
-    for (int j = 0; j < HALF; ++j) acc[j] = 0.0f;
+    float acc[COLS];
     bool ok = true;
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int b = kb % NB;
-      int w = 1;
-      if (lane == 0) w = mbar_wait(accf0 + 8 * b, static_cast<uint32_t>(kb / NB) & 1u, p.wait_ns, p.status, 13) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, w, 0) != 0;
-      if (!ok || *abort_flag) {
-        ok = false;
-        break;
+    int buf = 0;
+    uint32_t bphase = 0;
+    for (uint32_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+      int32_t m0, n0;
+      int kb0, kb1;
+      work_item(wi, m0, n0, kb0, kb1);
+      const int64_t row = static_cast<int64_t>(m0) + 32 * q + lane;
+      const int64_t col0 = static_cast<int64_t>(n0) + h * COLS;
+      const bool mine = row < p.M && col0 < p.N;  // rows/columns beyond M, N were zero-filled by TMA
+      double* dbase = p.ksplit > 1 ? p.ws + static_cast<int64_t>(wi / tiles) * p.M * p.N : p.C;
+      double2* dstp = reinterpret_cast<double2*>(dbase + (mine ? row * p.N + col0 : 0));
+#pragma unroll
+      for (int j = 0; j < COLS; ++j) acc[j] = 0.0f;
+      for (int kb = kb0; kb < kb1; ++kb) {
+        const int b = buf;
+        int w = 1;
+        if (lane == 0) w = mbar_wait(accf0 + 8 * b, bphase, p.wait_ns, p.status, 13) ? 1 : 0;
+        if (++buf == NB) {
+          buf = 0;
+          bphase ^= 1u;
+        }
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+        if (!ok || *abort_flag) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t col = static_cast<uint32_t>(b * BN + h * COLS);
+#pragma unroll
+        for (int c0 = 0; c0 < COLS; c0 += CH) {
+          uint32_t r[CH];
+#pragma unroll
+          for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + c0 + c1, r + c1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce0 + 8 * b);
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t col = static_cast<uint32_t>(b * BN + h * HALF);
+      if (!ok) break;
+      // the MMA warp is already filling the next buffers while this tile is written
+      if (mine) {
 #pragma unroll
-      for (int c0 = 0; c0 < HALF; c0 += CH) {
-        uint32_t r[CH];
-#pragma unroll
-        for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + c0 + c1, r + c1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        for (int j = 0; j < COLS / 2; ++j)
+          dstp[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale, static_cast<double>(acc[2 * j + 1]) * p.scale);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
-    if (ok && !*abort_flag) {
-      // rows and columns beyond M and N were zero-filled by TMA and are not stored
-      const int64_t row = m0 + 32 * q + lane;
-      const int64_t col0 = n0 + h * HALF;
-      if (row < p.M && col0 < p.N) {
-        double2* dst = reinterpret_cast<double2*>(p.C + row * p.N + col0);
-#pragma unroll
-        for (int j = 0; j < HALF / 2; ++j)
-          dst[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale, static_cast<double>(acc[2 * j + 1]) * p.scale);
-      }
-    } else {
-      *abort_flag = 1;
-    }
+    if (!ok) *abort_flag = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -393,15 +479,23 @@ cudaError_t launch_tile(TcParams p, int64_t M, int64_t N, cudaStream_t s) {
   const size_t smem = size_t(p.slots) * p.slot_bytes + 1024 /* barriers */ + 1024 /* alignment */;
   const int64_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt;
-  if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  if (mt > 0x7FFFFFFF || nt > 0x7FFFFFFF) return cudaErrorInvalidValue;
   p.ntn = static_cast<int32_t>(nt);
+  p.mtn = static_cast<int32_t>(mt);
+  p.group = static_cast<int32_t>(mt < 8 ? mt : 8);
+  p.tiles = tiles;
+  // persistent grid: one CTA per SM (the kernel holds 1 CTA/SM), each walking tiles with a stride
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = tiles < sms ? tiles : sms;
   const uint32_t fmt = BF16 ? 1u : 2u;  // A/B type: TF32 = 2, BF16 = 1; D = F32; both K-major
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
             (static_cast<uint32_t>(kBM >> 4) << 24);
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_gemm_tc<BN, BF16><<<static_cast<unsigned>(tiles), kThreads, smem, s>>>(p);
+  k_gemm_tc<BN, BF16><<<static_cast<unsigned>(grid), kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -416,17 +510,52 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind) {
   return pow2 && M >= 32 && N >= 16 && K * es >= 32 && M * N <= (int64_t(1) << 40) && K * es <= (int64_t(1) << 38);
 }
 
+int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind) {
+  const int64_t es = kind == 1 ? 2 : 4;
+  const int64_t bn = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+  const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + bn - 1) / bn);
+  const int64_t kblocks = (K * es + kRowBytes - 1) / kRowBytes;
+  // accuracy: at most kMaxBlocksPerSplit K blocks per split
+  int64_t ks = (kblocks + kMaxBlocksPerSplit - 1) / kMaxBlocksPerSplit;
+  // parallelism: with fewer tiles than SMs, about two work items per SM, at least 8 K blocks each
+  if (tiles < kPlanSMs) {
+    int64_t kp = (2 * kPlanSMs + tiles - 1) / tiles;
+    if (kp > kblocks / 8) kp = kblocks / 8;
+    if (kp > ks) ks = kp;
+  }
+  // workspace of ksplit * M * N doubles: at most 8 GiB (beyond that, fewer and longer splits)
+  while (ks > 1 && ks * M * N * 8 > (int64_t(8) << 30)) --ks;
+  if (ks <= 1) return 1;
+  const int64_t per = (kblocks + ks - 1) / ks;
+  return static_cast<int>((kblocks + per - 1) / per);
+}
+
+namespace {
+
+// C[i] = sum over splits s (in order) of W[s][i]
+__global__ void __launch_bounds__(256) k_split_sum(const double* __restrict__ W, int ksplit, int64_t n,
+                                                   double* __restrict__ C) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    double v = 0;
+    for (int s = 0; s < ksplit; ++s) v += W[s * n + i];
+    C[i] = v;
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                           int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s) {
-  return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, d_status, s, kWaitNs, 0);
+                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s) {
+  return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, s, kWaitNs, 0);
 }
 
 cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                              int64_t N, int64_t K, int kind, int* d_status, cudaStream_t s,
+                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
                               unsigned long long wait_ns, int stall_loads) {
   if (!tc_gemm_supported(M, N, K, kind) || terms < 1 || terms > kMaxTerms) return cudaErrorNotSupported;
+  if (ksplit < 1 || (ksplit > 1 && !ws)) return cudaErrorInvalidValue;
   const bool bf16 = kind == 1;
-  // BN = 256 would need 128 FP32 accumulators per epilogue thread and spills at 320 threads.
+  // BN = 256 would need 256 FP32 accumulators per epilogue thread.
   const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
   TcParams p;
   std::memset(&p, 0, sizeof(p));
@@ -435,6 +564,7 @@ cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b
     if (!make_map(&p.bmap[t], base + b_off[t], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
   }
   p.C = C;
+  p.ws = ws;
   p.status = d_status;
   p.M = M;
   p.N = N;
@@ -444,14 +574,24 @@ cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b
   p.stall_loads = stall_loads;
   const int64_t row_elems = kRowBytes / (bf16 ? 2 : 4);
   p.kblocks = static_cast<int32_t>((K + row_elems - 1) / row_elems);
+  p.kb_split = (p.kblocks + ksplit - 1) / ksplit;
+  p.ksplit = (p.kblocks + p.kb_split - 1) / p.kb_split;
+  if (p.ksplit != ksplit) return cudaErrorInvalidValue;  // the workspace was sized for `ksplit` splits
+  cudaError_t e;
   if (bf16) {
-    if (bn == 128) return launch_tile<128, true>(p, M, N, s);
-    if (bn == 64) return launch_tile<64, true>(p, M, N, s);
-    return launch_tile<32, true>(p, M, N, s);
+    if (bn == 128) e = launch_tile<128, true>(p, M, N, s);
+    else if (bn == 64) e = launch_tile<64, true>(p, M, N, s);
+    else e = launch_tile<32, true>(p, M, N, s);
+  } else {
+    if (bn == 128) e = launch_tile<128, false>(p, M, N, s);
+    else if (bn == 64) e = launch_tile<64, false>(p, M, N, s);
+    else e = launch_tile<32, false>(p, M, N, s);
   }
-  if (bn == 128) return launch_tile<128, false>(p, M, N, s);
-  if (bn == 64) return launch_tile<64, false>(p, M, N, s);
-  return launch_tile<32, false>(p, M, N, s);
+  if (e != cudaSuccess || ksplit == 1) return e;
+  const int64_t n = M * N;
+  const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_split_sum<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ws, ksplit, n, C);
+  return cudaGetLastError();
 }
 
 }  // namespace ajf
