@@ -298,7 +298,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
     ProfScope ps(c, s, kClass[ln.kind], ln.flops, ln.bytes);
     switch (ln.kind) {
       case LK_DOT:
-        e = launch_dot(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, s);
+        e = launch_dot(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, ln.op_f64 == 0, s);
         break;
       case LK_SMALL:
         e = launch_small(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, f64, s);
@@ -307,7 +307,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
         e = launch_splitk(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, f64, s);
         break;
       case LK_PERM:
-        e = launch_perm(perms + ln.first, ln.count, ln.blocks, ln.smem, arena, base, f64, s);
+        e = launch_perm(perms + ln.first, ln.count, ln.blocks, ln.smem, arena, base, ln.op_f64 != 0, s);
         break;
       case LK_GEMM_SIMT:
         e = launch_gemm_simt(base + ln.a_off[0], base + ln.b_off[0], base + ln.c_off, ln.M, ln.N, ln.K, ln.op_f64 != 0,

@@ -261,6 +261,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       while (j < S && info[order[j]].level == lev && info[order[j]].cls == cls) ++j;
       Launch ln;
       ln.kind = cls == C_SMALL ? LK_SMALL : (cls == C_SPLITK ? LK_SPLITK : LK_DOT);
+      ln.op_f64 = precision == AJF_PREC_F64 ? 1 : 0;  // tiled dot: FP32 products in reduced modes
       ln.first = static_cast<int>(P.steps.size());
       ln.count = j - i;
       int blocks = 0;
@@ -396,6 +397,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       }
       Launch lp;
       lp.kind = LK_PERM;
+      lp.op_f64 = gmode == OPM_F64 ? 1 : 0;
       lp.first = static_cast<int>(P.perms.size());
       lp.count = 2;
       const int64_t tiles = std::max<int64_t>(int64_t(1) << std::max(0, I.m + I.k - 10),

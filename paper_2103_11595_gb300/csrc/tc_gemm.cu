@@ -66,14 +66,17 @@ constexpr int64_t kPlanSMs = 152;
 constexpr int kMaxTerms = 3;
 constexpr uint32_t kSmemBudget = 192 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;
-// Mean relative shrink per GEMM of promoted K blocks (four leading-term instructions after the
-// corrections), fitted on GB300 so that F_J of held-out circuits (n=16 line, U3/CX, 10 noises;
-// generator seeds 100-105, not the test seeds) matches the FP64 path: TF32 (K = 32 per block)
-// 8.51e-8 +- 0.15e-8, bf16 (K = 64 per block) 6.40e-8 +- 0.27e-8 across seeds. Positive random
-// operands shrink more (1.2e-7 and 7.5e-8): structured operands often sum exactly. Recompute
-// with paper_2103_11595_gb300/calibrate_tc_bias.py.
-constexpr double kBlockBiasTF32 = 8.51e-8;
-constexpr double kBlockBiasBF16 = 6.40e-8;
+// Mean relative shrink of a promoted K block with all four leading-term instructions (K = 64 bf16
+// or 32 TF32 elements), fitted on GB300 so that F_J of held-out circuits matches the FP64 path
+// (Alg. II of the n = 16 line workload, seeds 100-105, and Alg. I of the batching workload, seeds
+// 1000-1007; the tests and bench use other seeds). Recompute with
+// paper_2103_11595_gb300/calibrate_tc_bias.py. A block whose K holds fewer instructions (K = 16
+// or 32 bf16, 8 or 16 TF32; the rest of the 128-byte row is zero-filled) truncates fewer times at
+// full magnitude: the i-th of n accumulating instructions truncates at about i/n of the block's
+// magnitude, so the shrink scales as (n + 1) / 5 of the four-instruction value.
+// Fitted values: TF32 8.69e-8 +- 0.51e-8, bf16 7.02e-8 +- 0.60e-8 (spread across circuits).
+constexpr double kBlockBiasTF32 = 8.69e-8;
+constexpr double kBlockBiasBF16 = 7.02e-8;
 
 struct TcParams {
   CUtensorMap amap[kMaxTerms];
@@ -458,15 +461,18 @@ bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// De-biasing factor: 1 + (mean shrink per promoted block). AJF_TC_BIAS overrides the calibrated
-// constant (calibration runs set it to 0 and measure the shrink).
-double debias_scale(bool bf16) {
+// De-biasing factor: 1 + (mean shrink per promoted block) for a GEMM with K elements of K.
+// AJF_TC_BIAS overrides the four-instruction constant (calibration runs set it to 0 and measure
+// the shrink).
+double debias_scale(bool bf16, int64_t K) {
   static const double forced = [] {
     const char* e = std::getenv("AJF_TC_BIAS");
     return e ? std::atof(e) : -1.0;
   }();
-  const double e = forced >= 0 ? forced : (bf16 ? kBlockBiasBF16 : kBlockBiasTF32);
-  return 1.0 + e;
+  const double e4 = forced >= 0 ? forced : (bf16 ? kBlockBiasBF16 : kBlockBiasTF32);
+  const int64_t per_instr = bf16 ? 16 : 8;  // K elements per tcgen05.mma (32 bytes)
+  const int64_t n = K / per_instr >= 4 ? 4 : (K / per_instr < 1 ? 1 : K / per_instr);
+  return 1.0 + e4 * static_cast<double>(n + 1) / 5.0;
 }
 
 template <int BN, bool BF16>
@@ -568,7 +574,7 @@ cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b
   p.status = d_status;
   p.M = M;
   p.N = N;
-  p.scale = debias_scale(bf16);
+  p.scale = debias_scale(bf16, K);
   p.terms = terms;
   p.wait_ns = wait_ns;
   p.stall_loads = stall_loads;
