@@ -69,6 +69,10 @@ struct ajf_ctx {
   // structural plan cache: the path is reused when the network's shape and options repeat
   std::vector<int64_t> plan_key;
   bool path_valid = false;
+  // lowered-program cache: a re-plan of the same structure, precision and lowering keeps the
+  // program, its descriptor image and its CUDA graph; only the packed input values change
+  std::vector<int64_t> prog_key;
+  bool prog_valid = false;
   // profiling
   struct ProfRec {
     cudaEvent_t a, b;
@@ -142,14 +146,19 @@ double tp_error(const double* ks, int nk, int dim) {
   return std::sqrt(err);
 }
 
-void invalidate(ajf_ctx* c) {
-  c->planned = false;
-  c->uploaded = false;
-  c->have_alg1 = false;
+// The CUDA graph of a context replays its current program on its current arena; it is dropped
+// when either changes.
+void drop_graph(ajf_ctx* c) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+}
+
+void invalidate(ajf_ctx* c) {
+  c->planned = false;
+  c->uploaded = false;
+  c->have_alg1 = false;
 }
 
 // Pack the caller's matrices into one complex128 buffer and fill the index structures.
@@ -191,10 +200,12 @@ ajf_status ensure_arena(ajf_ctx* c) {
     if (c->user_ws_bytes < need)
       return fail(c, AJF_E_NOMEM, "workspace of " + std::to_string(c->user_ws_bytes) + " bytes < " +
                                        std::to_string(need) + " needed");
+    if (c->arena != static_cast<char*>(c->user_ws)) drop_graph(c);
     c->arena = static_cast<char*>(c->user_ws);
     return AJF_OK;
   }
   if (c->own_arena && c->arena && c->arena_cap >= need) return AJF_OK;
+  drop_graph(c);
   if (c->own_arena && c->arena) {
     cudaFree(c->arena);
     c->arena = nullptr;
@@ -598,37 +609,6 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
       return fail(c, AJF_E_BUDGET, "Alg. I result tensor would hold 2^" + std::to_string(open_bits) +
                                        " traces (more than 2^40); use Alg. II");
   }
-  c->net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
-  PlanParams pp;
-  pp.planner = o.planner;
-  pp.precision = o.precision;
-  pp.trials = o.trials;
-  pp.seed = o.seed;
-  pp.elem_bytes = o.precision == AJF_PREC_F64 ? 16 : 8;
-  switch (o.precision) {
-    case AJF_PREC_F64: pp.peak_flops = 1.0e12; break;
-    case AJF_PREC_F32: pp.peak_flops = 40e12; break;
-    case AJF_PREC_TF32: pp.peak_flops = 500e12; break;
-    case AJF_PREC_BF16X3: pp.peak_flops = 400e12; break;
-    default: pp.peak_flops = 200e12; break;
-  }
-  cudaError_t score_err = cudaSuccess;
-  if (o.planner == AJF_PLANNER_LEARNED && static_cast<int>(c->mlp_weights.size()) == kMlpParams) {
-    pp.mlp = c->mlp_weights.data();
-    if (c->device >= 0) {
-      pp.scorer = [c, &score_err](const float* w, const float* x, int n, float* out) {
-        const cudaError_t e = c->mlp_scorer.score(w, x, n, out);
-        if (e != cudaSuccess) {
-          score_err = e;
-          for (int i = 0; i < n; ++i) out[i] = 0.0f;
-        }
-      };
-    } else {
-      pp.scorer = [](const float* w, const float* x, int n, float* out) {
-        for (int i = 0; i < n; ++i) out[i] = mlp_score_host(w, x + static_cast<size_t>(i) * kMlpFeatures);
-      };
-    }
-  }
   std::vector<int64_t> key = {alg, c->n, c->has_impl, o.planner, o.precision, o.trials, static_cast<int64_t>(o.seed),
                               c->mlp_version};
   auto key_gates = [&](const std::vector<GateData>& gs) {
@@ -638,40 +618,83 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   key_gates(c->ideal);
   if (c->has_impl) key_gates(c->impl);
   for (auto& nz : c->noises) key.insert(key.end(), {nz.after, nz.arity, nz.q[0], nz.q[1], nz.q[2], nz.nk});
-  const bool cached = c->path_valid && key == c->plan_key;
-  try {
-    if (!cached) {
+  // the lowered program depends on the structure, the precision, the lowering and the device
+  std::vector<int64_t> pkey = key;
+  pkey.push_back(o.lowering);
+  pkey.push_back(c->tc_device ? 1 : 0);
+  const bool prog_hit = c->prog_valid && pkey == c->prog_key;
+  bool cached = prog_hit;
+  if (!prog_hit) {
+    drop_graph(c);
+    c->prog_valid = false;
+    cached = c->path_valid && key == c->plan_key;
+    c->net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
+    PlanParams pp;
+    pp.planner = o.planner;
+    pp.precision = o.precision;
+    pp.trials = o.trials;
+    pp.seed = o.seed;
+    pp.elem_bytes = o.precision == AJF_PREC_F64 ? 16 : 8;
+    switch (o.precision) {
+      case AJF_PREC_F64: pp.peak_flops = 1.0e12; break;
+      case AJF_PREC_F32: pp.peak_flops = 40e12; break;
+      case AJF_PREC_TF32: pp.peak_flops = 500e12; break;
+      case AJF_PREC_BF16X3: pp.peak_flops = 400e12; break;
+      default: pp.peak_flops = 200e12; break;
+    }
+    cudaError_t score_err = cudaSuccess;
+    if (o.planner == AJF_PLANNER_LEARNED && static_cast<int>(c->mlp_weights.size()) == kMlpParams) {
+      pp.mlp = c->mlp_weights.data();
+      if (c->device >= 0) {
+        pp.scorer = [c, &score_err](const float* w, const float* x, int n, float* out) {
+          const cudaError_t e = c->mlp_scorer.score(w, x, n, out);
+          if (e != cudaSuccess) {
+            score_err = e;
+            for (int i = 0; i < n; ++i) out[i] = 0.0f;
+          }
+        };
+      } else {
+        pp.scorer = [](const float* w, const float* x, int n, float* out) {
+          for (int i = 0; i < n; ++i) out[i] = mlp_score_host(w, x + static_cast<size_t>(i) * kMlpFeatures);
+        };
+      }
+    }
+    try {
+      if (!cached) {
+        c->path_valid = false;
+        c->path = plan_path(c->net, pp);
+        c->plan_key = key;
+        c->path_valid = true;
+      }
+      if (score_err == cudaSuccess && c->path.width > kMaxBits - 2) {
+        // too wide to address: report the path's cost and width with the budget error
+        ajf_plan_info pi{};
+        pi.cmacs = c->path.cmacs;
+        pi.flops = 8.0 * c->path.cmacs;
+        pi.width = c->path.width;
+        pi.n_steps = static_cast<int32_t>(c->path.steps.size());
+        pi.n_leaves = static_cast<int32_t>(c->net.leaf_labels.size());
+        pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
+        pi.planner_used = c->path.planner;
+        pi.arena_bytes = std::ldexp(1.0, c->path.width) * 16.0;
+        pi.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        c->info = pi;
+        if (info) *info = pi;
+        return fail(c, AJF_E_BUDGET, "planned width 2^" + std::to_string(c->path.width) +
+                                         " elements is beyond what one device can hold");
+      }
+      if (score_err == cudaSuccess)
+        c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device,
+                        o.lowering == AJF_LOWER_PERSISTENT);
+    } catch (const std::exception& ex) {
+      return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
+    }
+    if (score_err != cudaSuccess) {
       c->path_valid = false;
-      c->path = plan_path(c->net, pp);
-      c->plan_key = key;
-      c->path_valid = true;
+      return cuda_fail(c, score_err, "learned merge scorer");
     }
-    if (score_err == cudaSuccess && c->path.width > kMaxBits - 2) {
-      // too wide to address: report the path's cost and width with the budget error
-      ajf_plan_info pi{};
-      pi.cmacs = c->path.cmacs;
-      pi.flops = 8.0 * c->path.cmacs;
-      pi.width = c->path.width;
-      pi.n_steps = static_cast<int32_t>(c->path.steps.size());
-      pi.n_leaves = static_cast<int32_t>(c->net.leaf_labels.size());
-      pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
-      pi.planner_used = c->path.planner;
-      pi.arena_bytes = std::ldexp(1.0, c->path.width) * 16.0;
-      pi.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      c->info = pi;
-      if (info) *info = pi;
-      return fail(c, AJF_E_BUDGET, "planned width 2^" + std::to_string(c->path.width) +
-                                       " elements is beyond what one device can hold");
-    }
-    if (score_err == cudaSuccess)
-      c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device,
-                      o.lowering == AJF_LOWER_PERSISTENT);
-  } catch (const std::exception& ex) {
-    return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
-  }
-  if (score_err != cudaSuccess) {
-    c->path_valid = false;
-    return cuda_fail(c, score_err, "learned merge scorer");
+    c->prog_key = pkey;
+    c->prog_valid = true;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // descriptor image

@@ -255,9 +255,8 @@ __global__ void __launch_bounds__(256) k_dot(const StepDev* __restrict__ steps, 
   const int64_t ntiles = int64_t(1) << (st.rk - ntl);
   const T* A = arena + st.a;
   const T* B = arena + st.b;
-  double re = 0, im = 0;
-  for (int64_t t = split; t < ntiles; t += st.nsplit) {
-    // contracted-index value of the tile's base: the tile number spread over the non-tile bits
+  // the tile's base offsets in A and B: the tile number spread over the non-tile bits
+  auto tile_base = [&](int64_t t, int64_t& ba, int64_t& bb) {
     uint64_t base = 0;
     int64_t rem = t;
     for (int i = 0; i < st.rk && rem; ++i) {
@@ -265,39 +264,83 @@ __global__ void __launch_bounds__(256) k_dot(const StepDev* __restrict__ steps, 
       if (rem & 1) base |= uint64_t(1) << i;
       rem >>= 1;
     }
-    const int64_t ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
-    const int64_t bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
-    // staged A values sit at index l ^ ((l >> 5) & 31): B-ordered reads that stride across A's
-    // index (B's low bits on A's high bits) then fall into distinct shared-memory banks
-    for (int l = threadIdx.x; l < nt; l += blockDim.x) {
-      const int sl = l ^ ((l >> 5) & 31);
-      sre[sl] = A[ba + locA[l]];
-      sim[sl] = A[st.pa + ba + locA[l]];
+    ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
+    bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
+  };
+  // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
+  // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
+  // so the loads of two tiles are in flight. Staged A values sit at index l ^ ((l >> 5) & 31):
+  // B-ordered reads that stride across A's index (B's low bits on A's high bits) then fall into
+  // distinct shared-memory banks.
+  constexpr int kPer = 4;
+  double are[kPer], aim[kPer], bre[kPer], bim[kPer];
+  auto load_tile = [&](int64_t t) {
+    int64_t ba, bb;
+    tile_base(t, ba, bb);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int l = threadIdx.x + q * blockDim.x;
+      if (l < nt) {
+        are[q] = A[ba + locA[l]];
+        aim[q] = A[st.pa + ba + locA[l]];
+        bre[q] = B[bb + locB[l]];
+        bim[q] = B[st.pb + bb + locB[l]];
+      }
+    }
+  };
+  double re = 0, im = 0;
+  int64_t t = split;
+  if (t < ntiles) load_tile(t);
+  while (t < ntiles) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int l = threadIdx.x + q * blockDim.x;
+      if (l < nt) {
+        const int sl = l ^ ((l >> 5) & 31);
+        sre[sl] = are[q];
+        sim[sl] = aim[q];
+      }
+    }
+    double cbr[kPer], cbi[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      cbr[q] = bre[q];
+      cbi[q] = bim[q];
     }
     __syncthreads();
+    const int64_t tn = t + st.nsplit;
+    if (tn < ntiles) load_tile(tn);
     if (kF32) {
       float fre = 0.0f, fim = 0.0f;
-      for (int l = threadIdx.x; l < nt; l += blockDim.x) {
-        const float br = static_cast<float>(B[bb + locB[l]]), bi = static_cast<float>(B[st.pb + bb + locB[l]]);
-        const int la = a_of_b[l];
-        const int sl = la ^ ((la >> 5) & 31);
-        const float ar = static_cast<float>(sre[sl]), ai = static_cast<float>(sim[sl]);
-        fre += ar * br - ai * bi;
-        fim += ar * bi + ai * br;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int l = threadIdx.x + q * blockDim.x;
+        if (l < nt) {
+          const int la = a_of_b[l];
+          const int sl = la ^ ((la >> 5) & 31);
+          const float ar = static_cast<float>(sre[sl]), ai = static_cast<float>(sim[sl]);
+          const float br = static_cast<float>(cbr[q]), bi = static_cast<float>(cbi[q]);
+          fre += ar * br - ai * bi;
+          fim += ar * bi + ai * br;
+        }
       }
       re += fre;
       im += fim;
     } else {
-      for (int l = threadIdx.x; l < nt; l += blockDim.x) {
-        const double br = B[bb + locB[l]], bi = B[st.pb + bb + locB[l]];
-        const int la = a_of_b[l];
-        const int sl = la ^ ((la >> 5) & 31);
-        const double ar = sre[sl], ai = sim[sl];
-        re += ar * br - ai * bi;
-        im += ar * bi + ai * br;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int l = threadIdx.x + q * blockDim.x;
+        if (l < nt) {
+          const int la = a_of_b[l];
+          const int sl = la ^ ((la >> 5) & 31);
+          const double ar = sre[sl], ai = sim[sl];
+          re += ar * cbr[q] - ai * cbi[q];
+          im += ar * cbi[q] + ai * cbr[q];
+        }
       }
     }
     __syncthreads();
+    t = tn;
   }
   red_re[threadIdx.x] = re;
   red_im[threadIdx.x] = im;
@@ -372,74 +415,6 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Eight consecutive operand elements (idx a multiple of 8) with 16-byte vector stores per split
-// term; the values are sign * src[0..7] (src in shared memory).
-template <typename S>
-__device__ __forceinline__ void store_operand8(const PermDev& p, char* base, int64_t idx, const S* src,
-                                               double sign) {
-  double v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = sign * src[i];
-  switch (p.mode) {
-    case OPM_F64: {
-      double2* d = reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) d[i] = make_double2(v[2 * i], v[2 * i + 1]);
-      break;
-    }
-    case OPM_F32:
-    case OPM_TF32: {
-      float f[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) f[i] = p.mode == OPM_TF32 ? to_tf32(static_cast<float>(v[i])) : static_cast<float>(v[i]);
-      float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(base + p.dst[0]) + idx);
-      d[0] = make_float4(f[0], f[1], f[2], f[3]);
-      d[1] = make_float4(f[4], f[5], f[6], f[7]);
-      break;
-    }
-    case OPM_TF32X2: {
-      float h[8], l[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float x = static_cast<float>(v[i]);
-        h[i] = to_tf32(x);
-        l[i] = to_tf32(x - h[i]);
-      }
-      float4* dh = reinterpret_cast<float4*>(reinterpret_cast<float*>(base + p.dst[0]) + idx);
-      float4* dl = reinterpret_cast<float4*>(reinterpret_cast<float*>(base + p.dst[1]) + idx);
-      dh[0] = make_float4(h[0], h[1], h[2], h[3]);
-      dh[1] = make_float4(h[4], h[5], h[6], h[7]);
-      dl[0] = make_float4(l[0], l[1], l[2], l[3]);
-      dl[1] = make_float4(l[4], l[5], l[6], l[7]);
-      break;
-    }
-    default: {  // OPM_BF16X2, OPM_BF16X3: hi, (mid,) lo
-      const int terms = p.mode == OPM_BF16X3 ? 3 : 2;
-      uint32_t w[3][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float x0 = static_cast<float>(v[2 * i]), x1 = static_cast<float>(v[2 * i + 1]);
-        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-        const float2 hf = __bfloat1622float2(h);
-        const float r0 = x0 - hf.x, r1 = x1 - hf.y;
-        const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
-        const float2 mf = __bfloat1622float2(m);
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-        w[0][i] = *reinterpret_cast<const uint32_t*>(&h);
-        // two-term split: the second term is the residual itself
-        w[1][i] = *reinterpret_cast<const uint32_t*>(&m);
-        w[2][i] = *reinterpret_cast<const uint32_t*>(&lo);
-      }
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t < terms)
-          *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[t]) + idx) =
-              make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
-      break;
-    }
-  }
-}
-
 // Two consecutive operand elements (idx even) with one vector store per split term.
 __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, double v0, double v1) {
   switch (p.mode) {
@@ -487,20 +462,15 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
   }
 }
 
-// Tiles of TR rows x TK k (TK = min(64, K), TR = min(R, 2048 / TK, 256)) per iteration, 256 threads.
-// The source offsets of the tile's rows and columns are computed once per tile. Loads run with
-// lanes along whichever index is contiguous in the source and go through shared memory (row
-// pitch TK + 1, no bank conflicts on either pass); stores write 8 consecutive k of one row per
-// thread (16-byte vector stores per split term), so a warp writes whole 128-byte row segments.
-// S: staging type in shared memory -- double for FP64 operands, float otherwise (every reduced
-// operand format rounds the value to FP32 before splitting it, so staging in float loses nothing).
-template <typename T, typename S>
-__global__ void __launch_bounds__(256, 4) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
-                                                 char* __restrict__ base) {
+// Tile of 32 rows x 32 k per iteration, 256 threads. The source offsets of the tile's rows and
+// columns are computed once per tile; loads run with lanes along whichever index is contiguous in
+// the source, stores with lanes along k and two elements per vector store.
+template <typename T>
+__global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
+                                              char* __restrict__ base) {
   extern __shared__ int64_t tab[];
-  constexpr int kTile = 2048, kPitchMax = 2048 + 256;
-  __shared__ S tre[kPitchMax], tim[kPitchMax];
-  __shared__ int64_t roff[256], koff[64];
+  __shared__ T tre[32][33], tim[32][33];
+  __shared__ int64_t roff[32], koff[32];
   const PermDev& p = perms[blockIdx.y];
   const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
   int64_t* t_r = tab;
@@ -508,55 +478,53 @@ __global__ void __launch_bounds__(256, 4) k_perm(const PermDev* __restrict__ per
   build_table(p.rows, t_r);
   build_table(p.cols, t_k);
   __syncthreads();
-  const int TK = p.kbits >= 6 ? 64 : (1 << p.kbits);
+  const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
+  const int TK = p.kbits >= 5 ? 32 : (1 << p.kbits);
   const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
-  const int64_t tr_max = kTile / TK < 256 ? kTile / TK : 256;
-  const int TR = static_cast<int>(R < tr_max ? R : tr_max);
-  const int pitch = TK + 1;
   const int64_t ntr = R / TR, ntk = K / TK;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const T* src = arena + p.src;
   const int64_t ld = 2 * K;
-  const int CK = TK < 8 ? TK : 8;  // k per store item
   for (int64_t tile = blockIdx.x; tile < ntr * ntk; tile += gridDim.x) {
     const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
-    for (int i = threadIdx.x; i < TR; i += blockDim.x) roff[i] = lookup(t_r, c_r, r0 + i);
-    for (int i = threadIdx.x; i < TK; i += blockDim.x) koff[i] = lookup(t_k, c_k, k0 + i);
+    if (threadIdx.x < 32) roff[tx] = tx < TR ? lookup(t_r, c_r, r0 + tx) : 0;
+    else if (threadIdx.x < 64) koff[tx] = tx < TK ? lookup(t_k, c_k, k0 + tx) : 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < TR * TK; e += blockDim.x) {
-      const int rr = p.rows_fast ? e % TR : e / TK, kk = p.rows_fast ? e / TR : e % TK;
-      const int64_t off = roff[rr] + koff[kk];
-      tre[rr * pitch + kk] = static_cast<S>(src[off]);
-      tim[rr * pitch + kk] = static_cast<S>(src[p.plane + off]);
+    // the four loads (x 2 planes) of a thread are issued before its shared-memory stores
+    T vr[4], vi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 8 * q;
+      const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
+      if (rr < TR && kk < TK) {
+        const int64_t off = roff[rr] + koff[kk];
+        vr[q] = src[off];
+        vi[q] = src[p.plane + off];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 8 * q;
+      const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
+      if (rr < TR && kk < TK) {
+        tre[rr][kk] = vr[q];
+        tim[rr][kk] = vi[q];
+      }
     }
     __syncthreads();
-    const int per_row = TK / CK;
-    for (int w = threadIdx.x; w < TR * per_row; w += blockDim.x) {
-      const int i = w / per_row, j = (w % per_row) * CK;
+    const int pairs = TK >> 1;
+    for (int w = threadIdx.x; w < TR * pairs; w += blockDim.x) {
+      const int i = w / pairs, j = 2 * (w % pairs);
+      const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
       const int64_t r = r0 + i, k = k0 + j;
-      const S* sre = tre + i * pitch + j;
-      const S* sim = tim + i * pitch + j;
-      if (CK == 8) {
-        if (p.embed) {
-          store_operand8(p, base, r * ld + k, sre, 1.0);             // (s=0, t=0):  Re
-          store_operand8(p, base, r * ld + K + k, sim, -1.0);        // (s=0, t=1): -Im
-          store_operand8(p, base, (R + r) * ld + k, sim, 1.0);       // (s=1, t=0):  Im
-          store_operand8(p, base, (R + r) * ld + K + k, sre, 1.0);   // (s=1, t=1):  Re
-        } else {
-          store_operand8(p, base, r * ld + k, sre, 1.0);
-          store_operand8(p, base, r * ld + K + k, sim, 1.0);
-        }
+      if (p.embed) {
+        store_operand2(p, base, r * ld + k, re0, re1);             // (s=0, t=0):  Re
+        store_operand2(p, base, r * ld + K + k, -im0, -im1);       // (s=0, t=1): -Im
+        store_operand2(p, base, (R + r) * ld + k, im0, im1);       // (s=1, t=0):  Im
+        store_operand2(p, base, (R + r) * ld + K + k, re0, re1);   // (s=1, t=1):  Re
       } else {
-        for (int c = 0; c < CK; c += 2) {
-          if (p.embed) {
-            store_operand2(p, base, r * ld + k + c, sre[c], sre[c + 1]);
-            store_operand2(p, base, r * ld + K + k + c, -sim[c], -sim[c + 1]);
-            store_operand2(p, base, (R + r) * ld + k + c, sim[c], sim[c + 1]);
-            store_operand2(p, base, (R + r) * ld + K + k + c, sre[c], sre[c + 1]);
-          } else {
-            store_operand2(p, base, r * ld + k + c, sre[c], sre[c + 1]);
-            store_operand2(p, base, r * ld + K + k + c, sim[c], sim[c + 1]);
-          }
-        }
+        store_operand2(p, base, r * ld + k, re0, re1);
+        store_operand2(p, base, r * ld + K + k, im0, im1);
       }
     }
     __syncthreads();
@@ -917,11 +885,9 @@ cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t sm
                         bool op_f64, cudaStream_t s) {
   if (nperm == 0) return cudaSuccess;
   dim3 grid(grid_x, nperm);
-  // tensors are FP64 in every mode; operands in FP64 need FP64 staging, every other format FP32
-  if (op_f64)
-    k_perm<double, double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
-  else
-    k_perm<double, float><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
+  // tensors are FP64 in every mode; the operand format (FP64 or a reduced one) is in each PermDev
+  (void)op_f64;
+  k_perm<double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
   return cudaGetLastError();
 }
 
@@ -967,10 +933,7 @@ cudaError_t set_kernel_smem_limits() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_perm<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_perm<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;

@@ -316,3 +316,24 @@ def test_mid_config_alg1_vs_alg2(mid0_oracle):
             idx = idx * d + choice[j]
         val = network.alg1_trace(inst, choice, order="minfill")
         assert abs(t[idx] - val) <= 1e-12 * 2 ** inst.n
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_replan_same_structure_new_values(use_graph):
+    """A re-plan of the same circuit structure with new gate and noise values reuses the lowered
+    program (and its CUDA graph) and uploads only the new values: F_J follows the new values."""
+    base = W.random_small(5, n=6, n_gates=40, n_noises=3)
+    rng = np.random.default_rng(11)
+    def same_kind(nz, k):  # new values, same number of Kraus operators
+        kr = W.depolarising(0.05 * (k + 1)) if nz.n_kraus == 4 else W.amplitude_damping(0.1 * (k + 1))
+        assert kr.shape == nz.kraus.shape
+        return W.Noise(nz.after_gate, nz.qubits, kr)
+    other = W.Instance(base.n, [W.Gate(g.qubits, W.haar_unitary(rng, 2 ** len(g.qubits))) for g in base.ideal],
+                       [same_kind(nz, k) for k, nz in enumerate(base.noises)])
+    with ajf.Context(0) as c:
+        for k, inst in enumerate([base, other, base]):
+            ajf.load_instance(c.handle, inst)
+            info = ajf.ajf_plan(c.handle, 2, precision="f64", trials=4, use_graph=use_graph)
+            assert info["plan_cached"] == (1 if k > 0 else 0)
+            r = ajf.ajf_fidelity_alg2(c.handle)
+            assert abs(r["F"] - dense.fidelity(inst)["F"]) <= 1e-12

@@ -107,3 +107,15 @@ def test_unsupported_shape_is_reported():
     with pytest.raises(ajf.AjfError) as e:
         ajf.ajf_selftest_gemm(0, 0, A, B, 16, 32, 32)
     assert e.value.status == ajf.AJF_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("M,N,K,T", [(128, 64, 16384, 3), (256, 32, 8192, 2), (1024, 512, 2048, 1)])
+def test_k_split_gemm(M, N, K, T):
+    """Few tiles and long K: the GEMM splits K over CTAs (FP64 partial tiles summed in order)."""
+    rng = np.random.default_rng(7 + M + K)
+    A = bf16_bits(rng.standard_normal((T, M, K)).astype(np.float32))
+    B = bf16_bits(rng.standard_normal((T, N, K)).astype(np.float32))
+    C = ajf.ajf_selftest_gemm(0, 1, A, B, M, N, K)
+    ref, bound = split_ref(bits_to_f64(A), bits_to_f64(B))
+    # per split at most 4096 K elements are summed in FP32; the splits add in FP64
+    assert np.all(np.abs(C - ref) <= 4 * 4096 * 2.0 ** -23 * bound + 1e-30)
