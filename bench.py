@@ -338,7 +338,7 @@ def main():
     h2d = d2h = 0
     for c, inst in zip(e2e_ctx, insts):  # first pass fills the structural plan cache
         ajf.load_instance(c.handle, inst)
-        ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials)
+        ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials, use_graph=True)
     ajf.ajf_fidelity_batch(handles, 2)
     torch.cuda.synchronize()
     barrier(world)
@@ -347,7 +347,7 @@ def main():
         h2d = d2h = 0
         for c, inst in zip(e2e_ctx, insts):
             ajf.load_instance(c.handle, inst)
-            info = ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials)
+            info = ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials, use_graph=True)
             h2d += int(info["upload_bytes"])
             d2h += 24
         ajf.ajf_fidelity_batch(handles, 2)

@@ -49,6 +49,25 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
 // CTAs, each writing an FP64 partial tile to a workspace of ksplit * M * N doubles that a
 // deterministic pass then sums into C. 1 = no split (no workspace).
 int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind);
+// A tensor-core GEMM launch prepared on the host (tensor maps, tiling, kernel parameters), so that
+// enqueueing it later costs one kernel launch (two with a K split) and no host set-up.
+struct TcPrepared {
+  alignas(64) unsigned char params[1024];  // the kernel's parameter block
+  void (*run)(const void* params, unsigned grid, size_t smem, cudaStream_t s) = nullptr;
+  unsigned grid = 0;
+  size_t smem = 0;
+  int ksplit = 1;
+  double* ws = nullptr;
+  double* C = nullptr;
+  int64_t n = 0;  // M * N
+  bool ready = false;
+};
+cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, const int64_t* b_off, int terms,
+                            double* C, int64_t M, int64_t N, int64_t K, int kind, double* ws, int ksplit,
+                            int* d_status, unsigned long long wait_ns, int stall_loads);
+cudaError_t tc_gemm_run(const TcPrepared& t, cudaStream_t s);
+// Bound of every device-side wait in the GEMM (nanoseconds).
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s);
 // Same with an explicit bound on every device-side wait and a test hook: stall_loads = 1 makes the

@@ -65,7 +65,7 @@ constexpr int kMaxBlocksPerSplit = 64;
 constexpr int64_t kPlanSMs = 152;
 constexpr int kMaxTerms = 3;
 constexpr uint32_t kSmemBudget = 192 * 1024;
-constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kWaitNs = kTcWaitNs;
 // Mean relative shrink of a promoted K block with all four leading-term instructions (K = 64 bf16
 // or 32 TF32 elements), fitted on GB300 so that F_J of held-out circuits matches the FP64 path
 // (Alg. II of the n = 16 line workload, seeds 100-105, and Alg. I of the batching workload, seeds
@@ -195,12 +195,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int BN, bool kBF16>
@@ -263,7 +257,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int kblocks = p.kblocks;
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles
@@ -380,9 +373,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       work_item(wi, m0, n0, kb0, kb1);
       const int64_t row = static_cast<int64_t>(m0) + 32 * q + lane;
       const int64_t col0 = static_cast<int64_t>(n0) + h * COLS;
-      const bool mine = row < p.M && col0 < p.N;  // rows/columns beyond M, N were zero-filled by TMA
+      // rows/columns beyond M, N were zero-filled by TMA and are not stored; M and N are powers of
+      // two >= 32 and >= 16, so a warp's 32 rows and COLS columns are all inside or all outside
+      const bool mine = row < p.M && col0 < p.N;
       double* dbase = p.ksplit > 1 ? p.ws + static_cast<int64_t>(wi / tiles) * p.M * p.N : p.C;
-      double2* dstp = reinterpret_cast<double2*>(dbase + (mine ? row * p.N + col0 : 0));
 #pragma unroll
       for (int j = 0; j < COLS; ++j) acc[j] = 0.0f;
       for (int kb = kb0; kb < kb1; ++kb) {
@@ -416,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       if (!ok) break;
       // the MMA warp is already filling the next buffers while this tile is written
       if (mine) {
+        double2* dstp = reinterpret_cast<double2*>(dbase + row * p.N + col0);
 #pragma unroll
         for (int j = 0; j < COLS / 2; ++j)
           dstp[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale, static_cast<double>(acc[2 * j + 1]) * p.scale);
@@ -475,8 +470,23 @@ double debias_scale(bool bf16, int64_t K) {
   return 1.0 + e4 * static_cast<double>(n + 1) / 5.0;
 }
 
+// SM count of the current device (queried once per device).
+int sm_count() {
+  static int counts[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (counts[dev] == 0) cudaDeviceGetAttribute(&counts[dev], cudaDevAttrMultiProcessorCount, dev);
+  return counts[dev];
+}
+
 template <int BN, bool BF16>
-cudaError_t launch_tile(TcParams p, int64_t M, int64_t N, cudaStream_t s) {
+void run_tile(const void* params, unsigned grid, size_t smem, cudaStream_t s) {
+  k_gemm_tc<BN, BF16><<<grid, kThreads, smem, s>>>(*static_cast<const TcParams*>(params));
+}
+
+// Fill the tile geometry of `p` and the launch shape of `t` (host only; nothing is enqueued).
+template <int BN, bool BF16>
+cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   p.slot_bytes = static_cast<uint32_t>((kBM + BN) * kRowBytes);
   p.slots = static_cast<int32_t>(kSmemBudget / p.slot_bytes);
   if (p.slots > kMaxSlots) p.slots = kMaxSlots;
@@ -491,18 +501,27 @@ cudaError_t launch_tile(TcParams p, int64_t M, int64_t N, cudaStream_t s) {
   p.group = static_cast<int32_t>(mt < 8 ? mt : 8);
   p.tiles = tiles;
   // persistent grid: one CTA per SM (the kernel holds 1 CTA/SM), each walking tiles with a stride
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
+  const int sms = sm_count();
+  if (sms <= 0) return cudaErrorInvalidDevice;
   const int64_t grid = tiles < sms ? tiles : sms;
   const uint32_t fmt = BF16 ? 1u : 2u;  // A/B type: TF32 = 2, BF16 = 1; D = F32; both K-major
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
             (static_cast<uint32_t>(kBM >> 4) << 24);
-  e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  // the shared-memory opt-in is a per-function attribute: set once per device (the size is the
+  // same for every launch of one instantiation)
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  k_gemm_tc<BN, BF16><<<static_cast<unsigned>(grid), kThreads, smem, s>>>(p);
-  return cudaGetLastError();
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  t->grid = static_cast<unsigned>(grid);
+  t->smem = smem;
+  t->run = &run_tile<BN, BF16>;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -550,24 +569,21 @@ __global__ void __launch_bounds__(256) k_split_sum(const double* __restrict__ W,
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s) {
-  return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, s, kWaitNs, 0);
-}
-
-cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
-                              unsigned long long wait_ns, int stall_loads) {
+cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, const int64_t* b_off, int terms,
+                            double* C, int64_t M, int64_t N, int64_t K, int kind, double* ws, int ksplit,
+                            int* d_status, unsigned long long wait_ns, int stall_loads) {
+  static_assert(sizeof(TcParams) <= sizeof(t->params), "kernel parameters exceed the prepared-launch buffer");
+  t->ready = false;
   if (!tc_gemm_supported(M, N, K, kind) || terms < 1 || terms > kMaxTerms) return cudaErrorNotSupported;
   if (ksplit < 1 || (ksplit > 1 && !ws)) return cudaErrorInvalidValue;
   const bool bf16 = kind == 1;
-  // BN = 256 would need 256 FP32 accumulators per epilogue thread.
+  // BN = 256 would need 128 FP32 accumulators per epilogue thread and spill at 320 threads.
   const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
   TcParams p;
   std::memset(&p, 0, sizeof(p));
-  for (int t = 0; t < terms; ++t) {
-    if (!make_map(&p.amap[t], base + a_off[t], M, K, kBM, bf16)) return cudaErrorInvalidValue;
-    if (!make_map(&p.bmap[t], base + b_off[t], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
+  for (int i = 0; i < terms; ++i) {
+    if (!make_map(&p.amap[i], base + a_off[i], M, K, kBM, bf16)) return cudaErrorInvalidValue;
+    if (!make_map(&p.bmap[i], base + b_off[i], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
   }
   p.C = C;
   p.ws = ws;
@@ -585,19 +601,47 @@ cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b
   if (p.ksplit != ksplit) return cudaErrorInvalidValue;  // the workspace was sized for `ksplit` splits
   cudaError_t e;
   if (bf16) {
-    if (bn == 128) e = launch_tile<128, true>(p, M, N, s);
-    else if (bn == 64) e = launch_tile<64, true>(p, M, N, s);
-    else e = launch_tile<32, true>(p, M, N, s);
+    if (bn == 128) e = prepare_tile<128, true>(p, t, M, N);
+    else if (bn == 64) e = prepare_tile<64, true>(p, t, M, N);
+    else e = prepare_tile<32, true>(p, t, M, N);
   } else {
-    if (bn == 128) e = launch_tile<128, false>(p, M, N, s);
-    else if (bn == 64) e = launch_tile<64, false>(p, M, N, s);
-    else e = launch_tile<32, false>(p, M, N, s);
+    if (bn == 128) e = prepare_tile<128, false>(p, t, M, N);
+    else if (bn == 64) e = prepare_tile<64, false>(p, t, M, N);
+    else e = prepare_tile<32, false>(p, t, M, N);
   }
-  if (e != cudaSuccess || ksplit == 1) return e;
-  const int64_t n = M * N;
-  const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
-  k_split_sum<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ws, ksplit, n, C);
+  if (e != cudaSuccess) return e;
+  std::memcpy(t->params, &p, sizeof(p));
+  t->ksplit = ksplit;
+  t->ws = ws;
+  t->C = C;
+  t->n = M * N;
+  t->ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t tc_gemm_run(const TcPrepared& t, cudaStream_t s) {
+  if (!t.ready) return cudaErrorInvalidValue;
+  t.run(t.params, t.grid, t.smem, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || t.ksplit == 1) return e;
+  const int64_t blocks = (t.n + 255) / 256 < 4096 ? (t.n + 255) / 256 : 4096;
+  k_split_sum<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t.ws, t.ksplit, t.n, t.C);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
+                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s) {
+  return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, s, kWaitNs, 0);
+}
+
+cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
+                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
+                              unsigned long long wait_ns, int stall_loads) {
+  TcPrepared t;
+  cudaError_t e = tc_gemm_prepare(&t, base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, wait_ns,
+                                  stall_loads);
+  if (e != cudaSuccess) return e;
+  return tc_gemm_run(t, s);
 }
 
 }  // namespace ajf
