@@ -184,7 +184,7 @@ def main():
                     help="mid-config seeds per step (small values for profiler captures)")
     ap.add_argument("--persistent-flops", type=float, default=2e6,
                     help="batching workload: networks up to this many flops run in the persistent kernel")
-    ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "batching"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "batching", "precision"],
                     help="mid: the headline workload; tiny / batching: the small-network workloads "
                          "run through the persistent kernel")
     args = ap.parse_args()
@@ -192,6 +192,9 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "precision":
+        run_precision(args, world, rank, local)
         return
     if args.workload != "mid":
         run_small_networks(args, world, rank, local)
@@ -638,6 +641,90 @@ def run_small_networks(args, world, rank, local):
                             * args.steps,
             "clocks": clocks,
         }
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+PRECISION = ("precision: 4x5 grid, depth-4 brickwork of Haar SU(4), depolarising p~U[1e-4,1e-3] on both "
+             "qubits after every gate (62 noises), Alg. II (width 2^24), seeds 0-4")
+
+
+def run_precision(args, world, rank, local):
+    """Error of F_J and of 1 - F_J per precision mode against the FP64 GPU path (and, for seed 0,
+    the CPU oracle), with the evaluation rate of each mode (CUDA graphs, CUDA events)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    __graft_entry__.build()
+    from paper_2103_11595_gb300 import ajf
+    from paper_2103_11595_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    seeds = [rank * 5 + i for i in range(5)]
+    insts = [W.precision(s, depth=4) for s in seeds]
+    modes = ["f64", "f32", "tf32", "tf32x3", "bf16x3", "bf16x6"]
+    out = torch.zeros(len(insts), 3, dtype=torch.float64, device=dev)
+    F, rate = {}, {}
+    steps = max(1, args.steps)
+    with ClockSampler(dev) as clk:
+        for mode in modes:
+            ctxs = []
+            for inst in insts:
+                c = ajf.Context(dev, stream.cuda_stream)
+                ajf.load_instance(c.handle, inst)
+                ajf.ajf_plan(c.handle, 2, precision=mode, trials=args.trials, use_graph=True)
+                ajf.ajf_upload(c.handle)
+                ctxs.append(c)
+            with torch.cuda.stream(stream):
+                for _ in range(max(1, args.warmup)):
+                    for i, c in enumerate(ctxs):
+                        ajf.ajf_launch(c.handle, out[i].data_ptr())
+                torch.cuda.synchronize()
+                total = 0.0
+                for _ in range(steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for i, c in enumerate(ctxs):
+                        ajf.ajf_launch(c.handle, out[i].data_ptr())
+                    e1.record(stream)
+                    e1.synchronize()
+                    total += e0.elapsed_time(e1)
+            F[mode] = out[:, 1].cpu().numpy().copy()
+            rate[mode] = len(insts) * steps / (total / 1e3)
+            for c in ctxs:
+                c.close()
+    clocks = clk.summary()
+    ref = F["f64"]
+    per_mode = {}
+    for mode in modes:
+        dF = np.abs(F[mode] - ref)
+        rel = np.abs((1 - F[mode]) - (1 - ref)) / np.abs(1 - ref)
+        per_mode[mode] = {"evals_per_s": rate[mode], "max_abs_dF_vs_f64": float(dF.max()),
+                          "max_rel_err_one_minus_F": float(rel.max()),
+                          "conforming_1e-6": bool(dF.max() <= 1e-6 and rel.max() <= 1e-3)}
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import network
+        t0 = time.perf_counter()
+        r = network.alg2_fidelity(insts[0], order="minfill")
+        oracle = {"seed": seeds[0], "F": r["F"], "abs_dF_f64_gpu_vs_oracle": abs(float(ref[0]) - r["F"]),
+                  "seconds": time.perf_counter() - t0, "cores": os.cpu_count()}
+    if rank == 0:
+        best = "bf16x6"
+        line = {"metric": "fidelity evals/s", "value": per_mode[best]["evals_per_s"] * world, "unit": "evals/s",
+                "n_gpus": world, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": best + " (GEMM operands; FP64 tensors, trace and F)", "data": "synthetic",
+                "config": {"workload": PRECISION, "trials": args.trials, "l2": "flushed (256 MiB write) before every step"},
+                "per_mode": per_mode, "oracle": oracle, "clocks": clocks}
         print(json.dumps(line), flush=True)
     barrier(world)
 
