@@ -14,10 +14,12 @@
 //                split bf16).
 //  k_gemm_simt   real "TN" GEMM on CUDA cores (FP32 or FP64) writing the planar result.
 //  k_open/k_final  the FP64 end of the path: t_i for Alg. I, sum |t_i|^2, F_J and 1 - F_J.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.h"
+#include "fp_bits.h"
 #include "kernels.h"
 
 namespace ajf {
@@ -531,6 +533,13 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   }
 }
 
+// Check of the integer-pipe conversion (test entry point): FP32 x -> FP64 x * (1 + q * 2^-46).
+__global__ void k_convert_check(const float* __restrict__ in, double* __restrict__ out, int64_t n, int64_t q,
+                                double scale) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = f32_to_f64_scaled(in[i], q, scale);
+}
+
 // ------------------------------------------------------------------ CUDA-core GEMM
 
 // C[M][N] (row-major, ldc = N, FP64) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous;
@@ -867,6 +876,13 @@ size_t dot_smem_bytes(const StepDev& st) {
   const BitMap* maps[2] = {&st.ka, &st.kb};
   const size_t nt = size_t(1) << st.ntl;
   return table_bytes(maps, 2) + nt * (8 + 8 + 8 + 8 + 2) + 16;
+}
+
+cudaError_t launch_convert_check(const float* in, double* out, int64_t n, int64_t q, double scale, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  k_convert_check<<<static_cast<unsigned>(blocks), 256, 0, s>>>(in, out, n, q, scale);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,

@@ -40,10 +40,12 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 
+#include "fp_bits.h"
 #include "kernels.h"
 
 namespace ajf {
@@ -85,6 +87,8 @@ struct TcParams {
   int* status;
   int64_t M, N;
   double scale;                      // de-biasing factor applied at the store
+  int64_t scale_q;                   // the same factor as 1 + scale_q * 2^-46 (integer-pipe store)
+  int32_t scale_int;                 // 1: the store converts on the integer pipe (|scale - 1| < 2^-10)
   int32_t terms, kblocks, ntn, slots, bufs;
   int32_t mtn;                       // tiles along M
   int32_t group;                     // M tiles per raster group (L2 reuse of B tiles)
@@ -409,11 +413,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       }
       if (!ok) break;
       // the MMA warp is already filling the next buffers while this tile is written
+      // FP32 -> scaled FP64 on the integer pipe: at GB300's FP64 rate a hardware conversion and
+      // multiply per element would cost about 8 us per 128 x 128 tile
       if (mine) {
         double2* dstp = reinterpret_cast<double2*>(dbase + row * p.N + col0);
+        if (p.scale_int) {
 #pragma unroll
-        for (int j = 0; j < COLS / 2; ++j)
-          dstp[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale, static_cast<double>(acc[2 * j + 1]) * p.scale);
+          for (int j = 0; j < COLS / 2; ++j)
+            dstp[j] = make_double2(f32_to_f64_scaled(acc[2 * j], p.scale_q, p.scale),
+                                   f32_to_f64_scaled(acc[2 * j + 1], p.scale_q, p.scale));
+        } else {
+#pragma unroll
+          for (int j = 0; j < COLS / 2; ++j)
+            dstp[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale,
+                                   static_cast<double>(acc[2 * j + 1]) * p.scale);
+        }
       }
     }
     if (!ok) *abort_flag = 1;
@@ -591,6 +605,10 @@ cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, con
   p.M = M;
   p.N = N;
   p.scale = debias_scale(bf16, K);
+  if (std::fabs(p.scale - 1.0) < std::ldexp(1.0, -10)) {
+    p.scale_q = std::llround(std::ldexp(p.scale - 1.0, kScaleFracBits));
+    p.scale_int = 1;
+  }
   p.terms = terms;
   p.wait_ns = wait_ns;
   p.stall_loads = stall_loads;
