@@ -109,9 +109,28 @@ def dist_setup():
     return world, rank, local
 
 
-def shard_seeds(rank: int, n_inst: int) -> list:
+def shard_seeds(rank: int, n_inst: int, first: int = 0) -> list:
     """Weak scaling: rank r evaluates its own block of workload seeds (no data is exchanged)."""
-    return [rank * n_inst + i for i in range(n_inst)]
+    return [first + rank * n_inst + i for i in range(n_inst)]
+
+
+# DRAM traffic of the tensor-core GEMM (dram__bytes_read.sum + dram__bytes_write.sum) per launch,
+# averaged over the GEMM launches of one step of the mid workload (seeds 0-9, bf16x6), from one
+# ncu capture per seed (each seed alone: the whole step holds ~8.5 GB on the device). The figures
+# belong to the GEMM kernel's source as hashed below; a changed kernel reports traffic null until
+# it is captured again (the capture commands are in profiles/k_gemm_tc_mid_bf16x6.md).
+TC_TRAFFIC = {"sha256": None, "precision": "bf16x6", "bytes_per_launch": None, "launches": None}
+TC_SOURCES = ("paper_2103_11595_gb300/csrc/tc_gemm.cu", "paper_2103_11595_gb300/csrc/fp_bits.h",
+              "paper_2103_11595_gb300/csrc/kernels.h")
+
+
+def tc_source_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TC_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def barrier(world):
@@ -172,7 +191,7 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x6")
@@ -182,6 +201,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--instances", type=int, default=N_INSTANCES,
                     help="mid-config seeds per step (small values for profiler captures)")
+    ap.add_argument("--first-seed", type=int, default=0,
+                    help="first mid-config seed (per-seed profiler captures)")
     ap.add_argument("--persistent-flops", type=float, default=2e6,
                     help="batching workload: networks up to this many flops run in the persistent kernel")
     ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "batching", "precision"],
@@ -214,7 +235,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()  # timing stream; every instance runs on a stream of its own
-    insts = [W.mid(s) for s in shard_seeds(rank, n_inst)]
+    insts = [W.mid(s) for s in shard_seeds(rank, n_inst, args.first_seed)]
     streams = [torch.cuda.Stream() for _ in insts]
 
     def make_contexts(precision, use_graph=True):
@@ -313,7 +334,12 @@ def main():
     else:
         roof = {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"], "peak_src": pk["src"] + " copy bandwidth"}
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-    roof.update({"kernel_class": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None,
+    traffic = None
+    if (dom == "gemm_tc" and TC_TRAFFIC["sha256"] == tc_source_sha256() and args.precision == TC_TRAFFIC["precision"]
+            and n_inst == N_INSTANCES and args.first_seed == 0 and d["launches"] == TC_TRAFFIC["launches"] * world):
+        traffic = TC_TRAFFIC["bytes_per_launch"]
+        roof["traffic_src"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_gemm_tc_mid_bf16x6.md"
+    roof.update({"kernel_class": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
                  "launches_per_step": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                  "share_of_step": d["ms"] / max(1e-9, sum(v["ms"] for v in classes.values()))})
 
@@ -374,7 +400,9 @@ def main():
             "dtype": {"f64": "f64", "f32": "f32"}.get(args.precision, args.precision) +
                      (" (GEMM operands; FP32 accumulate; FP64 tensors, trace and F)" if args.precision != "f64" else ""),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if n_inst == N_INSTANCES else WORKLOAD + f" (only {n_inst} seeds)", "precision": args.precision, "planner": "auto",
+            "config": {"workload": WORKLOAD if (n_inst == N_INSTANCES and args.first_seed == 0)
+                       else WORKLOAD + f" (only seeds {args.first_seed}..{args.first_seed + n_inst - 1})",
+                       "precision": args.precision, "planner": "auto",
                        "trials": args.trials, "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"{world} independent ranks (weak scaling)"},
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,

@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles
+    // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles. A block's
+    // terms are loaded highest first, the order in which the MMA issuer frees their slots.
     int slot = 0;
     uint32_t phase = 0;  // position in the slot ring, continued across tiles
     bool ok = !p.stall_loads;
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       int kb0, kb1;
       work_item(wi, m0, n0, kb0, kb1);
       for (int kb = kb0; kb < kb1 && ok; ++kb) {
-        for (int t = 0; t < T; ++t) {
+        for (int j = 0; j < T; ++j) {
+          const int t = T - 1 - j;
           if (*abort_flag || !mbar_wait(empty0 + 8 * slot, phase ^ 1u, p.wait_ns, p.status, 11)) {
             *abort_flag = 1;
             ok = false;
@@ -309,31 +311,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           buf = 0;
           bphase ^= 1u;
         }
-        // slots of the block's terms, in ring order; descriptors are kept in registers (a
+        // ring positions of the block's slots (the producer loads term T-1 first), then the slot
+        // and phase of each term; all in scalars -- descriptors and slots kept in registers (a
         // dynamically indexed array would live in local memory and stall every MMA issue)
-        int st[3] = {0, 0, 0};
-        bool got = true;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          if (t < T) {
-            st[t] = slot;
-            got = got && mbar_wait(full0 + 8 * slot, phase, p.wait_ns, p.status, 12);
-            if (++slot == S) {
-              slot = 0;
-              phase ^= 1u;
-            }
+        int r0 = slot, r1 = 0, r2 = 0;
+        uint32_t f0 = phase, f1 = 0u, f2 = 0u;
+        auto advance = [&]() {
+          if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
           }
+        };
+        advance();
+        if (T > 1) {
+          r1 = slot;
+          f1 = phase;
+          advance();
         }
-        if (!got) {
-          ok = false;
-          break;
+        if (T > 2) {
+          r2 = slot;
+          f2 = phase;
+          advance();
         }
-        const int s0 = st[0], s1 = st[1], s2 = st[2];
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int st0 = T == 3 ? r2 : (T == 2 ? r1 : r0), st1 = T == 3 ? r1 : r0, st2 = r0;
+        const uint32_t ph0 = T == 3 ? f2 : (T == 2 ? f1 : f0), ph1 = T == 3 ? f1 : f0, ph2 = f0;
         const uint32_t base = smem_u32(smem);
-        const uint64_t ad0 = smem_desc(base + s0 * p.slot_bytes), bd0 = smem_desc(base + s0 * p.slot_bytes + a_bytes);
-        const uint64_t ad1 = smem_desc(base + s1 * p.slot_bytes), bd1 = smem_desc(base + s1 * p.slot_bytes + a_bytes);
-        const uint64_t ad2 = smem_desc(base + s2 * p.slot_bytes), bd2 = smem_desc(base + s2 * p.slot_bytes + a_bytes);
+        const uint64_t ad0 = smem_desc(base + st0 * p.slot_bytes), bd0 = smem_desc(base + st0 * p.slot_bytes + a_bytes);
+        const uint64_t ad1 = smem_desc(base + st1 * p.slot_bytes), bd1 = smem_desc(base + st1 * p.slot_bytes + a_bytes);
+        const uint64_t ad2 = smem_desc(base + st2 * p.slot_bytes), bd2 = smem_desc(base + st2 * p.slot_bytes + a_bytes);
         const uint32_t dst = tmem + static_cast<uint32_t>(b * BN);
         uint32_t acc = 0;
         // one product A_i . B_j over the block: 4 instructions, 32 bytes of K each (+2 in the
@@ -345,20 +350,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             acc = 1;
           }
         };
-        // correction products (i + j >= 1), smallest first, then the leading product
+        auto arrived = [&](int sl, uint32_t ph) {
+          const bool w = mbar_wait(full0 + 8 * sl, ph, p.wait_ns, p.status, 12);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          return w;
+        };
+        // all of the block's terms are resident before its first MMA (a failed wait then leaves
+        // nothing in flight); correction products (i + j >= 1) go first, smallest first, the
+        // leading product last, and a term's slot is released (commit: freed once the MMAs issued
+        // so far complete) right after its last use
+        const bool got = (T < 3 || arrived(st2, ph2)) && (T < 2 || arrived(st1, ph1)) && arrived(st0, ph0);
+        if (!got) {
+          ok = false;
+          break;
+        }
         if (T == 3) {
           product(ad0, bd2);
           product(ad1, bd1);
           product(ad2, bd0);
+          mma_commit(empty0 + 8 * st2);
         }
         if (T >= 2) {
           product(ad0, bd1);
           product(ad1, bd0);
+          mma_commit(empty0 + 8 * st1);
         }
         product(ad0, bd0);
-        mma_commit(empty0 + 8 * s0);
-        if (T > 1) mma_commit(empty0 + 8 * s1);
-        if (T > 2) mma_commit(empty0 + 8 * s2);
+        mma_commit(empty0 + 8 * st0);
         mma_commit(accf0 + 8 * b);
       }
     }
@@ -433,6 +451,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     if (!ok) *abort_flag = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // __syncthreads (bar.sync, the aligned form) must be executed by all threads of a warp
+  // together; warps 0 and 1 get here diverged (lane 0 ran the producer / MMA loop, lanes 1-31 came
+  // straight through), so they reconverge first. The barrier then orders warp 1's TMEM release
+  // after every epilogue warp's last TMEM read.
+  __syncwarp();
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
