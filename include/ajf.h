@@ -83,6 +83,19 @@ enum {
                               (ajf_launch_persistent); meant for small networks                */
 };
 
+/* Simplifications of the closed composed sequence (implementation, then the ideal circuit's
+ * adjoint, wires joined) before the network is built (Sec. IV-C; the paper's experiments run
+ * without them). Flags for ajf_plan_opts.simplify; F_J is unchanged up to rounding.
+ *   AJF_SIMPLIFY_SWAP: "SWAP elimination" -- every SWAP gate is dropped and the later elements are
+ *     rewired, the closure joining each output wire to the input wire the SWAPs lead it to.
+ *   AJF_SIMPLIFY_CANCEL: "local optimisations" -- adjacent unitary elements on the same ordered
+ *     wires whose product is the identity are removed (also across the closed trace, "both ends"),
+ *     as are elements equal to the identity; noises are never removed and block cancellation on
+ *     their wires. Matrices count as the identity / SWAP within 1e-12 per entry.
+ * The simplification depends on the gate matrices, not only the structure: a re-plan with new
+ * values keeps its cached path only when the simplified sequence is the same. */
+enum { AJF_SIMPLIFY_SWAP = 1, AJF_SIMPLIFY_CANCEL = 2 };
+
 typedef struct ajf_ctx ajf_ctx;
 
 typedef struct ajf_plan_opts {
@@ -93,7 +106,8 @@ typedef struct ajf_plan_opts {
   uint64_t seed;           /* planner random seed                                             */
   double mem_budget_bytes; /* 0 = 60% of the device's free memory at plan time                 */
   int32_t lowering;        /* AJF_LOWER_*; AJF_LOWER_PERSISTENT requires AJF_PREC_F64          */
-  int32_t reserved[7];     /* must be zero                                                     */
+  int32_t simplify;        /* AJF_SIMPLIFY_* flags; 0 = the sequence as given                  */
+  int32_t reserved[6];     /* must be zero                                                     */
 } ajf_plan_opts;
 
 typedef struct ajf_plan_info {
@@ -113,7 +127,7 @@ typedef struct ajf_plan_info {
   int32_t n_launches;    /* kernel launches one evaluation enqueues                              */
   int32_t n_tc_gemms;    /* GEMM launches that run on the tcgen05 tensor cores                   */
   int32_t plan_cached;   /* 1: the path was reused from the previous plan of the same structure  */
-  int32_t reserved;
+  int32_t n_removed;     /* gates removed by opts.simplify (SWAPs, cancelled pairs, identities)  */
   double upload_bytes;   /* host -> device bytes of one upload (descriptors + packed inputs)     */
 } ajf_plan_info;
 

@@ -29,7 +29,7 @@ PLANNERS = {"auto": AJF_PLANNER_AUTO, "greedy": AJF_PLANNER_GREEDY, "minfill": A
 class PlanOpts(ctypes.Structure):
     _fields_ = [("planner", ctypes.c_int32), ("precision", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_double),
-                ("lowering", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("lowering", ctypes.c_int32), ("simplify", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("width", ctypes.c_int32), ("n_steps", ctypes.c_int32),
                 ("n_gemm_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32), ("n_open_bits", ctypes.c_int32),
                 ("planner_used", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("n_tc_gemms", ctypes.c_int32),
-                ("plan_cached", ctypes.c_int32), ("reserved", ctypes.c_int32), ("upload_bytes", ctypes.c_double)]
+                ("plan_cached", ctypes.c_int32), ("n_removed", ctypes.c_int32), ("upload_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -50,6 +50,9 @@ class KernelStats(ctypes.Structure):
 
 
 AJF_LOWER_DEFAULT, AJF_LOWER_PERSISTENT = 0, 1
+AJF_SIMPLIFY_SWAP, AJF_SIMPLIFY_CANCEL = 1, 2
+SIMPLIFY = {"none": 0, "swap": AJF_SIMPLIFY_SWAP, "cancel": AJF_SIMPLIFY_CANCEL,
+            "all": AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL}
 LOWERINGS = {"default": AJF_LOWER_DEFAULT, "persistent": AJF_LOWER_PERSISTENT}
 KERNEL_CLASSES = ["leaves", "small", "splitk", "gather", "gemm_simt", "gemm_tc", "final", "persistent"]
 
@@ -176,8 +179,9 @@ def ajf_clear_noise(ctx) -> None:
 
 
 def ajf_plan(ctx, alg: int, planner="auto", precision="f64", trials: int = 0, use_graph: bool = False,
-             seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default") -> dict:
+             seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default", simplify="none") -> dict:
     o = PlanOpts()
+    o.simplify = SIMPLIFY[simplify] if isinstance(simplify, str) else int(simplify)
     o.lowering = LOWERINGS[lowering] if isinstance(lowering, str) else int(lowering)
     o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

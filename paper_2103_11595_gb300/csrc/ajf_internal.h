@@ -106,9 +106,28 @@ Path plan_learned(const Network& net, const PlanParams& p, uint64_t seed, bool* 
 // Replay `ref` and append (chosen merge, other candidate) feature pairs; returns the pair count.
 int learned_dataset(const Network& net, const Path& ref, uint64_t seed, int negatives, std::vector<float>& out);
 
+// ------------------------------------------------------------------ composed sequence
+
+// One element of the closed composed sequence: an implementation gate, the adjoint of an ideal
+// gate, or a noise, on wires w[0..arity) (rewired by SWAP elimination).
+enum SeqKind : int32_t { SEQ_GATE = 0, SEQ_ADJ = 1, SEQ_NOISE = 2 };
+struct SeqOp {
+  int32_t kind = SEQ_GATE;
+  int32_t index = 0;  // skeleton gate (SEQ_GATE), ideal gate (SEQ_ADJ) or noise (SEQ_NOISE)
+  int32_t arity = 0;
+  int32_t w[3] = {0, 0, 0};
+};
+struct Sequence {
+  std::vector<SeqOp> ops;    // time order: implementation, then the ideal circuit's adjoint
+  std::vector<int> closure;  // closure[w]: the input wire joined to output wire w
+  int removed = 0;           // gates removed by the simplifications
+};
+// The sequence of `in`, simplified by AJF_SIMPLIFY_* `flags`.
+Sequence compose_sequence(const Inputs& in, int flags);
+
 // ------------------------------------------------------------------ network builders
 
-Network build_alg1(const Inputs& in);
-Network build_alg2(const Inputs& in);
+Network build_alg1(const Inputs& in, const Sequence& seq);
+Network build_alg2(const Inputs& in, const Sequence& seq);
 
 }  // namespace ajf

@@ -611,8 +611,9 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   if (o.trials <= 0) o.trials = 32;
   if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
   if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < 6; ++i)
     if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
+  if (o.simplify & ~(AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL)) return fail(c, AJF_E_ARG, "unknown simplify flags");
   if (o.lowering != AJF_LOWER_DEFAULT && o.lowering != AJF_LOWER_PERSISTENT) return fail(c, AJF_E_ARG, "bad lowering");
   if (o.lowering == AJF_LOWER_PERSISTENT && o.precision != AJF_PREC_F64)
     return fail(c, AJF_E_ARG, "the persistent lowering computes in FP64: precision must be AJF_PREC_F64");
@@ -641,6 +642,14 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   key_gates(c->ideal);
   if (c->has_impl) key_gates(c->impl);
   for (auto& nz : c->noises) key.insert(key.end(), {nz.after, nz.arity, nz.q[0], nz.q[1], nz.q[2], nz.nk});
+  // a simplified sequence depends on the matrices: it becomes part of the structure
+  const Sequence seq = compose_sequence(c->in, o.simplify);
+  key.push_back(o.simplify);
+  if (o.simplify) {
+    key.push_back(static_cast<int64_t>(seq.ops.size()));
+    for (auto& op : seq.ops) key.insert(key.end(), {op.kind, op.index, op.w[0], op.w[1], op.w[2]});
+    key.insert(key.end(), seq.closure.begin(), seq.closure.end());
+  }
   // the lowered program depends on the structure, the precision, the lowering and the device
   std::vector<int64_t> pkey = key;
   pkey.push_back(o.lowering);
@@ -651,7 +660,7 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     drop_graph(c);
     c->prog_valid = false;
     cached = c->path_valid && key == c->plan_key;
-    c->net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
+    c->net = (alg == 1) ? build_alg1(c->in, seq) : build_alg2(c->in, seq);
     PlanParams pp;
     pp.planner = o.planner;
     pp.precision = o.precision;
@@ -750,6 +759,7 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     pi.n_launches += (ln.kind == LK_SPLITK || ln.kind == LK_DOT || (ln.kind == LK_GEMM_TC && ln.ksplit > 1)) ? 2 : 1;
   pi.n_tc_gemms = P.tensor_cores;
   pi.plan_cached = cached ? 1 : 0;
+  pi.n_removed = seq.removed;
   pi.upload_bytes = static_cast<double>(P.desc_bytes + P.input_bytes);
   c->info = pi;
   if (info) *info = pi;
@@ -1049,7 +1059,8 @@ ajf_status ajf_learned_dataset(ajf_ctx* c, int alg, int32_t trials, uint64_t see
     for (auto& nz : c->in.noises) open_bits += nz.kbits;
     if (open_bits > 40) return fail(c, AJF_E_BUDGET, "Alg. I result tensor too large");
   }
-  const Network net = (alg == 1) ? build_alg1(c->in) : build_alg2(c->in);
+  const Sequence seq = compose_sequence(c->in, 0);
+  const Network net = (alg == 1) ? build_alg1(c->in, seq) : build_alg2(c->in, seq);
   PlanParams pp;
   pp.planner = AJF_PLANNER_AUTO;
   pp.trials = std::max(1, trials);

@@ -1,9 +1,9 @@
 // Miter-network builders (host side).
 //
 // Sec. IV (Fig. 3): the trace of a circuit's matrix is its gate network with every qubit's
-// output wire joined to its input wire. Both builders walk the noisy implementation in time
-// order (noises placed after gate g follow g; after_gate = -1 comes first), then the ideal
-// circuit's adjoint (gates in reverse order, each conjugate-transposed), and close the wires.
+// output wire joined to its input wire. Both builders walk the composed sequence (the noisy
+// implementation in time order, then the ideal circuit's adjoint; see simplify.cpp) and close the
+// wires -- output wire w to input wire closure[w], the identity unless SWAPs were eliminated.
 //
 // Alg. I (Sec. IV-A): one wire per qubit. Noisy gate k becomes one tensor holding all of its Kraus
 // operators, indexed by an extra open index kappa_k (padded to a power of two with zero
@@ -61,13 +61,18 @@ struct Builder {
     return extra;
   }
 
-  // Join each wire's last label to its first. A wire with one operation would make that leaf
-  // carry the same label twice; an identity leaf delta[last][first] keeps labels pairwise.
-  void close() {
+  // Join each wire's last label to the first label of wire closure[w]. A wire closed on itself
+  // with one operation would make that leaf carry the same label twice, and a permuted closure
+  // could join a leaf's output to its own input: an identity leaf delta[last][first] keeps labels
+  // pairwise in both cases (a permuted closure always joins through one).
+  void close(const std::vector<int>& closure) {
     std::map<int, int> rename;
     std::vector<std::pair<int, int>> deltas;
     for (size_t w = 0; w < start.size(); ++w) {
-      if (nops[w] == 0) {
+      const size_t to = static_cast<size_t>(closure[w]);
+      if (to != w) {
+        deltas.push_back({cur[w], start[to]});
+      } else if (nops[w] == 0) {
         net.loops++;
       } else if (nops[w] == 1) {
         deltas.push_back({cur[w], start[w]});
@@ -90,24 +95,10 @@ struct Builder {
   }
 };
 
-std::vector<int> gate_wires(const GateIn& g, int offset) {
-  std::vector<int> w(g.arity);
-  for (int i = 0; i < g.arity; ++i) w[i] = g.q[i] + offset;
+std::vector<int> op_wires(const SeqOp& op, int offset) {
+  std::vector<int> w(op.arity);
+  for (int i = 0; i < op.arity; ++i) w[i] = op.w[i] + offset;
   return w;
-}
-
-// Time order of the implementation: (-1 - j) for noise j, g >= 0 for skeleton gate g.
-std::vector<int> timeline(const Inputs& in) {
-  std::vector<int> ops;
-  for (size_t j = 0; j < in.noises.size(); ++j)
-    if (in.noises[j].after < 0) ops.push_back(-1 - static_cast<int>(j));
-  const auto& sk = in.skeleton();
-  for (size_t g = 0; g < sk.size(); ++g) {
-    ops.push_back(static_cast<int>(g));
-    for (size_t j = 0; j < in.noises.size(); ++j)
-      if (in.noises[j].after == static_cast<int>(g)) ops.push_back(-1 - static_cast<int>(j));
-  }
-  return ops;
 }
 
 LeafSpec gate_spec(const GateIn& g, int kind) {
@@ -120,32 +111,30 @@ LeafSpec gate_spec(const GateIn& g, int kind) {
 
 }  // namespace
 
-Network build_alg1(const Inputs& in) {
+Network build_alg1(const Inputs& in, const Sequence& seq) {
   Network net;
   net.alg = 1;
   net.n_qubits = in.n;
   Builder b(net, in.n);
   std::vector<std::vector<int>> kappa(in.noises.size());
   const auto& sk = in.skeleton();
-  for (int op : timeline(in)) {
-    if (op >= 0) {
-      b.op(gate_spec(sk[op], LEAF_GATE), gate_wires(sk[op], 0), 0);
+  for (const SeqOp& op : seq.ops) {
+    if (op.kind == SEQ_GATE) {
+      b.op(gate_spec(sk[op.index], LEAF_GATE), op_wires(op, 0), 0);
+    } else if (op.kind == SEQ_ADJ) {
+      b.op(gate_spec(in.ideal[op.index], LEAF_GATE_DAG), op_wires(op, 0), 0);
     } else {
-      const int j = -1 - op;
-      const NoiseIn& nz = in.noises[j];
+      const NoiseIn& nz = in.noises[op.index];
       LeafSpec s;
       s.kind = LEAF_KRAUS_OPEN;
       s.a = nz.arity;
       s.src = nz.kraus_off;
       s.nk = nz.nk;
       s.kbits = nz.kbits;
-      std::vector<int> w(nz.q, nz.q + nz.arity);
-      kappa[j] = b.op(s, w, nz.kbits);
+      kappa[op.index] = b.op(s, op_wires(op, 0), nz.kbits);
     }
   }
-  for (auto it = in.ideal.rbegin(); it != in.ideal.rend(); ++it)
-    b.op(gate_spec(*it, LEAF_GATE_DAG), gate_wires(*it, 0), 0);
-  b.close();
+  b.close(seq.closure);
   // Result layout: the last-added noise's Kraus index in the lowest bits, so the linear index of
   // t follows Alg. I's lexicographic enumeration (after removing the zero padding).
   for (int j = static_cast<int>(in.noises.size()) - 1; j >= 0; --j)
@@ -153,35 +142,39 @@ Network build_alg1(const Inputs& in) {
   return net;
 }
 
-Network build_alg2(const Inputs& in) {
+Network build_alg2(const Inputs& in, const Sequence& seq) {
   Network net;
   net.alg = 2;
   net.n_qubits = in.n;
   const int n = in.n;
   Builder b(net, 2 * n);
   const auto& sk = in.skeleton();
-  for (int op : timeline(in)) {
-    if (op >= 0) {
-      b.op(gate_spec(sk[op], LEAF_GATE), gate_wires(sk[op], 0), 0);
-      b.op(gate_spec(sk[op], LEAF_GATE_CONJ), gate_wires(sk[op], n), 0);
+  for (const SeqOp& op : seq.ops) {
+    if (op.kind == SEQ_GATE) {
+      b.op(gate_spec(sk[op.index], LEAF_GATE), op_wires(op, 0), 0);
+      b.op(gate_spec(sk[op.index], LEAF_GATE_CONJ), op_wires(op, n), 0);
+    } else if (op.kind == SEQ_ADJ) {
+      b.op(gate_spec(in.ideal[op.index], LEAF_GATE_DAG), op_wires(op, 0), 0);
+      b.op(gate_spec(in.ideal[op.index], LEAF_GATE_TRANS), op_wires(op, n), 0);
     } else {
-      const NoiseIn& nz = in.noises[-1 - op];
+      const NoiseIn& nz = in.noises[op.index];
       LeafSpec s;
       s.kind = LEAF_SUPEROP;
       s.a = 2 * nz.arity;
       s.src = nz.kraus_off;
       s.nk = nz.nk;
-      std::vector<int> w;
-      for (int i = 0; i < nz.arity; ++i) w.push_back(nz.q[i]);
-      for (int i = 0; i < nz.arity; ++i) w.push_back(nz.q[i] + n);
+      std::vector<int> w = op_wires(op, 0);
+      for (int i = 0; i < op.arity; ++i) w.push_back(op.w[i] + n);
       b.op(s, w, 0);
     }
   }
-  for (auto it = in.ideal.rbegin(); it != in.ideal.rend(); ++it) {
-    b.op(gate_spec(*it, LEAF_GATE_DAG), gate_wires(*it, 0), 0);
-    b.op(gate_spec(*it, LEAF_GATE_TRANS), gate_wires(*it, n), 0);
+  // the q' wires close like their q wires
+  std::vector<int> closure(2 * n);
+  for (int w = 0; w < n; ++w) {
+    closure[w] = seq.closure[w];
+    closure[w + n] = seq.closure[w] + n;
   }
-  b.close();
+  b.close(closure);
   return net;
 }
 
