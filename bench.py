@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--trials", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-simplified", action="store_true",
+                    help="skip the run with SWAP elimination and local optimisations")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--instances", type=int, default=N_INSTANCES,
                     help="mid-config seeds per step (small values for profiler captures)")
@@ -248,12 +250,13 @@ def main():
     insts = [W.mid(s) for s in shard_seeds(rank, n_inst, args.first_seed)]
     streams = [torch.cuda.Stream() for _ in insts]
 
-    def make_contexts(precision, use_graph=True):
+    def make_contexts(precision, use_graph=True, simplify="none"):
         ctxs, infos = [], []
         for inst, s in zip(insts, streams):
             c = ajf.Context(dev, s.cuda_stream)
             ajf.load_instance(c.handle, inst)
-            infos.append(ajf.ajf_plan(c.handle, 2, precision=precision, trials=args.trials, use_graph=use_graph))
+            infos.append(ajf.ajf_plan(c.handle, 2, precision=precision, trials=args.trials, use_graph=use_graph,
+                                      simplify=simplify))
             ajf.ajf_upload(c.handle)
             ctxs.append(c)
         return ctxs, infos
@@ -369,6 +372,25 @@ def main():
             c.close()
         ctxs = []
 
+    # ---- the same evaluations with SWAP elimination and local optimisations (Sec. IV-C)
+    simplified = None
+    if not args.no_simplified:
+        for c in ctxs:
+            c.close()
+        ctxs = []
+        sctx, sinfos = make_contexts(args.precision, simplify="all")
+        s_ms = timed_steps(sctx, args.steps, args.warmup)
+        F_simp = out[:, 1].cpu().numpy().copy()
+        s_s = max_over_ranks(s_ms / 1e3, world)
+        simplified = {"value": n_inst * args.steps * world / s_s, "unit": "evals/s",
+                      "flops_per_step": float(sum(i["flops"] for i in sinfos)),
+                      "gates_removed": [int(i["n_removed"]) for i in sinfos],
+                      "max_abs_dF_vs_unsimplified": float(np.max(np.abs(F_simp - F_fast))),
+                      "note": "AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL (Sec. IV-C), same precision and timing; "
+                              "the paper's experiments run without them"}
+        for c in sctx:
+            c.close()
+
     # ---- end to end through the C ABI from host arrays
     for c in ctxs:
         c.close()
@@ -418,7 +440,7 @@ def main():
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,
             "flops_per_step": flops_per_step,
             "F_J": [float(x) for x in F_fast],
-            "roofline": roof, "kernel_classes": classes, "plain": plain, "e2e": e2e,
+            "roofline": roof, "kernel_classes": classes, "plain": plain, "simplified": simplified, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
