@@ -107,7 +107,9 @@ typedef struct ajf_plan_opts {
   double mem_budget_bytes; /* 0 = 60% of the device's free memory at plan time                 */
   int32_t lowering;        /* AJF_LOWER_*; AJF_LOWER_PERSISTENT requires AJF_PREC_F64          */
   int32_t simplify;        /* AJF_SIMPLIFY_* flags; 0 = the sequence as given                  */
-  int32_t reserved[6];     /* must be zero                                                     */
+  int32_t alg1_slices;     /* Alg. I only: fix the Kraus index of this many noises per slice   */
+                           /* (0 = none; see ajf_fidelity_alg1 for the early exit it enables)  */
+  int32_t reserved[5];     /* must be zero                                                     */
 } ajf_plan_opts;
 
 typedef struct ajf_plan_info {
@@ -186,13 +188,27 @@ ajf_status ajf_add_noise(ajf_ctx *ctx, int32_t after_gate, int32_t arity, const 
 ajf_status ajf_clear_noise(ajf_ctx *ctx);
 
 /* Build the network of algorithm `alg` (1: Alg. I with open Kraus indices, Sec. IV-A;
- * 2: Alg. II doubled network, Sec. IV-B), choose a pairwise contraction order, lower it to
- * device kernels and size the device arena. opts may be NULL (defaults: AUTO planner,
- * AJF_PREC_F64, 32 trials, no graph). info may be NULL.
+ * 2: Alg. II doubled network, Sec. IV-B; 0 = AJF_ALG_AUTO: plan both and keep the one whose
+ * estimated run time is lower -- Sec. IV-B and V note that Alg. I wins when noises are few and
+ * Alg. II when they are many; ajf_planned_alg tells which), choose a pairwise contraction
+ * order, lower it to device kernels and size the device arena. opts may be NULL (defaults: AUTO
+ * planner, AJF_PREC_F64, 32 trials, no graph). info may be NULL.
+ * opts.alg1_slices = s > 0 (Alg. I, and Alg. I under AJF_ALG_AUTO): the s noises with the most
+ * Kraus operators (earlier noise first on ties) get a fixed Kraus index; the network keeps the
+ * open indices of the others, and ajf_fidelity_alg1 runs it once per combination of the fixed
+ * indices. s must not exceed the number of noises; not with AJF_LOWER_PERSISTENT.
  * Errors: AJF_E_STATE (no circuit), AJF_E_ARG (bad alg/option), AJF_E_BUDGET (the best plan's
  * arena exceeds the budget; info is still filled), AJF_E_UNSUPPORTED (tensor-core precision on
  * a device without tcgen05). */
 ajf_status ajf_plan(ajf_ctx *ctx, int alg, const ajf_plan_opts *opts, ajf_plan_info *info);
+
+enum { AJF_ALG_AUTO = 0 };
+
+/* The algorithm (1 or 2) of the current plan. Errors: AJF_E_ARG, AJF_E_STATE (no plan). */
+ajf_status ajf_planned_alg(const ajf_ctx *ctx, int *alg);
+
+/* Run the planned algorithm: ajf_fidelity_alg1 or ajf_fidelity_alg2, whichever ajf_plan chose. */
+ajf_status ajf_fidelity(ajf_ctx *ctx, double eps, ajf_result *out);
 
 /* Lend the context `bytes` of device memory at `dev_ptr` (256-byte aligned) for its arena.
  * The caller keeps ownership and must keep it alive until ajf_destroy or the next
@@ -206,6 +222,12 @@ ajf_status ajf_workspace_size(const ajf_ctx *ctx, size_t *bytes);
 /* Alg. I (Sec. IV-A): F_J from all prod_k n_k traces tr(U^dagger E_i), accumulated as
  * sum |t|^2 in FP64 on the device. eps < 0: no decision (equivalent = -1); eps in [0, 1]: also
  * decide Definition 1. Requires ajf_plan(ctx, 1, ...). Synchronises the context's stream.
+ * Sliced plans (opts.alg1_slices > 0) run one contraction per combination of the fixed Kraus
+ * indices, in decreasing order of weight prod ||K||_F^2 / 2^a, and add the slices' sums in FP64
+ * on the host. With eps >= 0 they stop early once the partial F_J exceeds 1 - eps (the remark
+ * after Alg. I: every term is non-negative, so the partial sum already decides equivalence):
+ * then F, S and 1 - F describe the traces done (F is a lower bound of F_J), traces_done counts
+ * them, equivalent = 1, and ajf_alg1_traces reports AJF_E_STATE.
  * Errors: AJF_E_STATE, AJF_E_ARG (eps > 1), AJF_E_NOMEM, AJF_E_CUDA. */
 ajf_status ajf_fidelity_alg1(ajf_ctx *ctx, double eps, ajf_result *out);
 

@@ -29,7 +29,8 @@ PLANNERS = {"auto": AJF_PLANNER_AUTO, "greedy": AJF_PLANNER_GREEDY, "minfill": A
 class PlanOpts(ctypes.Structure):
     _fields_ = [("planner", ctypes.c_int32), ("precision", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_double),
-                ("lowering", ctypes.c_int32), ("simplify", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("lowering", ctypes.c_int32), ("simplify", ctypes.c_int32), ("alg1_slices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -50,6 +51,7 @@ class KernelStats(ctypes.Structure):
 
 
 AJF_LOWER_DEFAULT, AJF_LOWER_PERSISTENT = 0, 1
+AJF_ALG_AUTO = 0
 AJF_SIMPLIFY_SWAP, AJF_SIMPLIFY_CANCEL = 1, 2
 SIMPLIFY = {"none": 0, "swap": AJF_SIMPLIFY_SWAP, "cancel": AJF_SIMPLIFY_CANCEL,
             "all": AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL}
@@ -98,6 +100,8 @@ def lib() -> ctypes.CDLL:
             "ajf_workspace_size": (I32, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "ajf_fidelity_alg1": (I32, [P, D, ctypes.POINTER(Result)]),
             "ajf_fidelity_alg2": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_fidelity": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
             "ajf_alg1_traces": (I32, [P, P, I64]),
             "ajf_launch": (I32, [P, P]),
             "ajf_upload": (I32, [P]),
@@ -179,9 +183,12 @@ def ajf_clear_noise(ctx) -> None:
 
 
 def ajf_plan(ctx, alg: int, planner="auto", precision="f64", trials: int = 0, use_graph: bool = False,
-             seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default", simplify="none") -> dict:
+             seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default", simplify="none",
+             alg1_slices: int = 0) -> dict:
+    """alg: 1, 2 or AJF_ALG_AUTO (0)."""
     o = PlanOpts()
     o.simplify = SIMPLIFY[simplify] if isinstance(simplify, str) else int(simplify)
+    o.alg1_slices = int(alg1_slices)
     o.lowering = LOWERINGS[lowering] if isinstance(lowering, str) else int(lowering)
     o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -216,6 +223,19 @@ def ajf_fidelity_alg1(ctx, eps: float = -1.0) -> dict:
     r = Result()
     _check(ctx, lib().ajf_fidelity_alg1(ctx, float(eps), ctypes.byref(r)))
     return r.as_dict()
+
+
+def ajf_fidelity(ctx, eps: float = -1.0) -> dict:
+    """The planned algorithm (ajf_plan's choice under AJF_ALG_AUTO)."""
+    r = Result()
+    _check(ctx, lib().ajf_fidelity(ctx, float(eps), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ajf_planned_alg(ctx) -> int:
+    a = ctypes.c_int()
+    _check(ctx, lib().ajf_planned_alg(ctx, ctypes.byref(a)))
+    return int(a.value)
 
 
 def ajf_fidelity_alg2(ctx, eps: float = -1.0) -> dict:

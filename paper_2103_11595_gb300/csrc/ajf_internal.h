@@ -67,6 +67,7 @@ struct Network {
   std::vector<int> open_labels;  // bit order of the Alg. I result tensor t
   int loops = 0;                 // wires touched by no tensor: each a factor tr(I_2) = 2
   int n_qubits = 0;
+  std::vector<int> noise_leaf;   // leaf of each noise (-1: removed or absent)
 };
 
 // ------------------------------------------------------------------ contraction path
@@ -127,7 +128,9 @@ Sequence compose_sequence(const Inputs& in, int flags);
 
 // ------------------------------------------------------------------ network builders
 
-Network build_alg1(const Inputs& in, const Sequence& seq);
+// `sliced[j]` (may be empty): noise j gets a single-operator leaf (its first Kraus operator; the
+// caller points the leaf at another one per slice) and no open index.
+Network build_alg1(const Inputs& in, const Sequence& seq, const std::vector<char>& sliced = {});
 Network build_alg2(const Inputs& in, const Sequence& seq);
 
 }  // namespace ajf

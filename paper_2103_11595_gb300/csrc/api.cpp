@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -66,6 +67,9 @@ struct ajf_ctx {
   cudaGraphExec_t graph = nullptr;
   bool tc_device = false;
   bool have_alg1 = false;
+  // sliced Alg. I plan: noises with a fixed Kraus index and their leaves; traces gathered per slice
+  std::vector<int> slice_noises, slice_leaves;
+  std::vector<double> slice_traces;
   // structural plan cache: the path is reused when the network's shape and options repeat
   std::vector<int64_t> plan_key;
   bool path_valid = false;
@@ -427,6 +431,117 @@ int64_t real_combinations(const ajf_ctx* c) {
   return n;
 }
 
+bool is_sliced(const ajf_ctx* c) { return c->planned && !c->slice_noises.empty(); }
+
+// Sliced Alg. I (the remark after Alg. I on stopping early): one run of the program per
+// combination of the fixed Kraus indices, heaviest first; each run's sum |t|^2 is added in FP64
+// and its traces are scattered into the full, lexicographically ordered trace array.
+ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) {
+  const Program& P = c->prog;
+  const auto& nz = c->in.noises;
+  const int m = static_cast<int>(nz.size());
+  const int ns = static_cast<int>(c->slice_noises.size());
+  std::vector<char> fixed(m, 0);
+  for (int j : c->slice_noises) fixed[j] = 1;
+  // weight of Kraus operator k of noise j: ||K||_F^2 / 2^a (these sum to 1 over k for a channel)
+  auto weight = [&](int j, int k) {
+    const int d = 1 << nz[j].arity;
+    const double* K = c->in.packed.data() + 2 * (nz[j].kraus_off + static_cast<int64_t>(k) * d * d);
+    double w = 0;
+    for (int i = 0; i < 2 * d * d; ++i) w += K[i] * K[i];
+    return w / d;
+  };
+  struct Slice {
+    std::vector<int> k;
+    double w;
+  };
+  std::vector<Slice> slices(1, Slice{std::vector<int>(ns, 0), 1.0});
+  for (int i = 0; i < ns; ++i) {
+    std::vector<Slice> next;
+    const int j = c->slice_noises[i];
+    for (auto& sl : slices)
+      for (int k = 0; k < nz[j].nk; ++k) {
+        Slice t = sl;
+        t.k[i] = k;
+        t.w *= weight(j, k);
+        next.push_back(t);
+      }
+    slices.swap(next);
+  }
+  std::stable_sort(slices.begin(), slices.end(), [](const Slice& a, const Slice& b) { return a.w > b.w; });
+  // trace layout: full index = lexicographic over all noises (last fastest); the program's padded
+  // index holds the open (unfixed) noises' Kraus indices, the last-added noise in the lowest bits
+  std::vector<int64_t> radix(m, 1);
+  for (int j = m - 2; j >= 0; --j) radix[j] = radix[j + 1] * nz[j + 1].nk;
+  std::vector<int> shift(m, 0);
+  for (int j = m - 1, acc = 0; j >= 0; --j) {
+    shift[j] = acc;
+    if (!fixed[j]) acc += nz[j].kbits;
+  }
+  const int64_t total = real_combinations(c);
+  int64_t per_slice = 1;
+  for (int j = 0; j < m; ++j)
+    if (!fixed[j]) per_slice *= nz[j].nk;
+  c->slice_traces.assign(2 * static_cast<size_t>(total), 0.0);
+  std::vector<double> padded(2 * static_cast<size_t>(P.n_traces));
+  const size_t leaves_at = P.off_leaves - P.off_desc;
+  const int nsq = 2 * c->n;
+  double S = 0;
+  int64_t done = 0;
+  bool early = false;
+  for (const Slice& sl : slices) {
+    for (int i = 0; i < ns; ++i) {
+      const int j = c->slice_noises[i];
+      const int d = 1 << nz[j].arity;
+      const int64_t src = nz[j].kraus_off + static_cast<int64_t>(sl.k[i]) * d * d;
+      std::memcpy(c->desc_image.data() + leaves_at + c->slice_leaves[i] * sizeof(LeafDev) + offsetof(LeafDev, src),
+                  &src, sizeof(src));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, c->desc_image.data() + leaves_at,
+                                P.leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, c->stream));
+    ajf_status st = run_program(c);
+    if (st != AJF_OK) return st;
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + P.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + P.off_traces, padded.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    S += res[0];
+    // scatter: odometer over the open noises' Kraus indices
+    std::vector<int> digit(m, 0);
+    for (int i = 0; i < ns; ++i) digit[c->slice_noises[i]] = sl.k[i];
+    for (int64_t t = 0; t < per_slice; ++t) {
+      int64_t idx = 0, pidx = 0;
+      for (int j = 0; j < m; ++j) {
+        idx += digit[j] * radix[j];
+        if (!fixed[j]) pidx |= int64_t(digit[j]) << shift[j];
+      }
+      c->slice_traces[2 * idx] = padded[2 * pidx];
+      c->slice_traces[2 * idx + 1] = padded[2 * pidx + 1];
+      for (int j = m - 1; j >= 0; --j) {
+        if (fixed[j]) continue;
+        if (++digit[j] < nz[j].nk) break;
+        digit[j] = 0;
+      }
+    }
+    done += per_slice;
+    if (eps >= 0 && done < total && std::ldexp(S, -nsq) > 1.0 - eps) {
+      early = true;
+      break;
+    }
+  }
+  out->S = S;
+  out->F = std::ldexp(S, -nsq);
+  out->one_minus_F = std::ldexp(std::ldexp(1.0, nsq) - S, -nsq);
+  out->traces_done = done;
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->reserved = 0;
+  c->have_alg1 = !early;
+  return AJF_OK;
+}
+
 ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
   if (!c) return AJF_E_ARG;
   if (!out) return fail(c, AJF_E_ARG, "out is NULL");
@@ -438,6 +553,7 @@ ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
     ajf_status st = do_upload(c);
     if (st != AJF_OK) return st;
   }
+  if (alg == 1 && is_sliced(c)) return fidelity_sliced(c, eps, out);
   ajf_status st = run_program(c);
   if (st != AJF_OK) return st;
   double res[3];
@@ -599,10 +715,12 @@ ajf_status ajf_clear_noise(ajf_ctx* c) {
   return AJF_OK;
 }
 
-ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_info* info) {
+namespace {
+
+ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_info* info) {
   if (!c) return AJF_E_ARG;
   if (!c->has_ideal) return fail(c, AJF_E_STATE, "ajf_plan before ajf_load_circuit");
-  if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 1 or 2");
+  if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 0, 1 or 2");
   ajf_plan_opts o{};
   o.planner = AJF_PLANNER_AUTO;
   o.precision = AJF_PREC_F64;
@@ -611,8 +729,13 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   if (o.trials <= 0) o.trials = 32;
   if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
   if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
+  if (o.alg1_slices < 0 || o.alg1_slices > static_cast<int>(c->noises.size()))
+    return fail(c, AJF_E_ARG, "alg1_slices must be between 0 and the number of noises");
+  if (o.alg1_slices > 0 && alg != 1) return fail(c, AJF_E_ARG, "alg1_slices applies to Alg. I only");
+  if (o.alg1_slices > 0 && o.lowering == AJF_LOWER_PERSISTENT)
+    return fail(c, AJF_E_ARG, "a sliced Alg. I plan cannot use the persistent lowering");
   if (o.simplify & ~(AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL)) return fail(c, AJF_E_ARG, "unknown simplify flags");
   if (o.lowering != AJF_LOWER_DEFAULT && o.lowering != AJF_LOWER_PERSISTENT) return fail(c, AJF_E_ARG, "bad lowering");
   if (o.lowering == AJF_LOWER_PERSISTENT && o.precision != AJF_PREC_F64)
@@ -626,12 +749,25 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   invalidate(c);
   const auto t0 = std::chrono::steady_clock::now();
   pack_inputs(c);
+  // sliced noises: the alg1_slices noises with the most Kraus operators (earlier first on ties)
+  std::vector<int> slice_noises;
+  std::vector<char> sliced(c->in.noises.size(), 0);
+  if (o.alg1_slices > 0) {
+    std::vector<int> order(c->in.noises.size());
+    for (size_t j = 0; j < order.size(); ++j) order[j] = static_cast<int>(j);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return c->in.noises[x].nk > c->in.noises[y].nk; });
+    slice_noises.assign(order.begin(), order.begin() + o.alg1_slices);
+    std::sort(slice_noises.begin(), slice_noises.end());
+    for (int j : slice_noises) sliced[j] = 1;
+  }
   if (alg == 1) {
     int open_bits = 0;
-    for (auto& nz : c->in.noises) open_bits += nz.kbits;
+    for (size_t j = 0; j < c->in.noises.size(); ++j)
+      if (!sliced[j]) open_bits += c->in.noises[j].kbits;
     if (open_bits > 40)
       return fail(c, AJF_E_BUDGET, "Alg. I result tensor would hold 2^" + std::to_string(open_bits) +
-                                       " traces (more than 2^40); use Alg. II");
+                                       " traces (more than 2^40); use Alg. II or slice more noises");
   }
   std::vector<int64_t> key = {alg, c->n, c->has_impl, o.planner, o.precision, o.trials, static_cast<int64_t>(o.seed),
                               c->mlp_version};
@@ -645,6 +781,8 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   // a simplified sequence depends on the matrices: it becomes part of the structure
   const Sequence seq = compose_sequence(c->in, o.simplify);
   key.push_back(o.simplify);
+  key.push_back(o.alg1_slices);
+  key.insert(key.end(), slice_noises.begin(), slice_noises.end());
   if (o.simplify) {
     key.push_back(static_cast<int64_t>(seq.ops.size()));
     for (auto& op : seq.ops) key.insert(key.end(), {op.kind, op.index, op.w[0], op.w[1], op.w[2]});
@@ -660,7 +798,7 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     drop_graph(c);
     c->prog_valid = false;
     cached = c->path_valid && key == c->plan_key;
-    c->net = (alg == 1) ? build_alg1(c->in, seq) : build_alg2(c->in, seq);
+    c->net = (alg == 1) ? build_alg1(c->in, seq, sliced) : build_alg2(c->in, seq);
     PlanParams pp;
     pp.planner = o.planner;
     pp.precision = o.precision;
@@ -776,9 +914,54 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
                                      std::to_string(c->path.width) + ")");
   c->opts = o;
   c->alg = alg;
+  c->slice_noises = slice_noises;
+  c->slice_leaves.clear();
+  for (int j : slice_noises) c->slice_leaves.push_back(c->net.noise_leaf[j]);
   c->planned = true;
   c->plan_gen++;
   c->err.clear();
+  return AJF_OK;
+}
+
+}  // namespace
+
+ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_info* info) {
+  if (!c) return AJF_E_ARG;
+  if (alg != AJF_ALG_AUTO) return plan_one(c, alg, opts, info);
+  // AJF_ALG_AUTO: the cheaper of the two by the planner's time model (a sliced Alg. I plan runs
+  // once per slice). Alg. II is planned first; Alg. I only when its result tensor is addressable.
+  ajf_plan_opts o2{};
+  o2.planner = AJF_PLANNER_AUTO;
+  o2.precision = AJF_PREC_F64;
+  o2.trials = 32;
+  if (opts) o2 = *opts;
+  o2.alg1_slices = 0;
+  ajf_plan_info i2{};
+  ajf_status st = plan_one(c, 2, &o2, &i2);
+  const bool have2 = st == AJF_OK;
+  const double t2 = have2 ? c->path.est_seconds : 0.0;
+  if (st != AJF_OK && st != AJF_E_BUDGET) return st;
+  ajf_plan_info i1{};
+  const ajf_status st1 = plan_one(c, 1, opts, &i1);
+  if (st1 == AJF_OK) {
+    double slices = 1;
+    for (int j : c->slice_noises) slices *= c->noises[j].nk;
+    if (!have2 || c->path.est_seconds * slices <= t2) {
+      if (info) *info = i1;
+      return AJF_OK;
+    }
+  } else if (!have2) {
+    return st1;
+  }
+  st = plan_one(c, 2, &o2, &i2);  // Alg. II was cheaper: plan it again (its path is recomputed)
+  if (info) *info = i2;
+  return st;
+}
+
+ajf_status ajf_planned_alg(const ajf_ctx* c, int* alg) {
+  if (!c || !alg) return AJF_E_ARG;
+  if (!c->planned) return AJF_E_STATE;
+  *alg = c->alg;
   return AJF_OK;
 }
 
@@ -822,6 +1005,12 @@ ajf_status ajf_fidelity_alg1(ajf_ctx* c, double eps, ajf_result* out) { return f
 
 ajf_status ajf_fidelity_alg2(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 2, eps, out); }
 
+ajf_status ajf_fidelity(ajf_ctx* c, double eps, ajf_result* out) {
+  if (!c) return AJF_E_ARG;
+  if (!c->planned) return fail(c, AJF_E_STATE, "no plan");
+  return fidelity(c, c->alg, eps, out);
+}
+
 ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out) {
   if (!c) return AJF_E_ARG;
   if (!out) return fail(c, AJF_E_ARG, "out is NULL");
@@ -829,6 +1018,7 @@ ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out
   if (!c->planned || c->alg != alg) return fail(c, AJF_E_STATE, "no Alg. " + std::to_string(alg) + " plan");
   if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
   if (eps > 1.0) return fail(c, AJF_E_ARG, "eps > 1");
+  if (is_sliced(c)) return fail(c, AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
   const Program& P = c->prog;
   if (P.arena_bytes > kStaticArenaBytes)
     return fail(c, AJF_E_NOMEM, "plan needs " + std::to_string(P.arena_bytes) + " bytes of device memory; the fixed " +
@@ -879,6 +1069,10 @@ ajf_status ajf_alg1_traces(ajf_ctx* c, double* traces, int64_t count) {
   if (!traces) return fail(c, AJF_E_ARG, "traces is NULL");
   const int64_t real = real_combinations(c);
   if (count != real) return fail(c, AJF_E_ARG, "count must be " + std::to_string(real));
+  if (is_sliced(c)) {  // gathered on the host slice by slice
+    std::memcpy(traces, c->slice_traces.data(), 2 * static_cast<size_t>(real) * sizeof(double));
+    return AJF_OK;
+  }
   CUDA_TRY(c, cudaSetDevice(c->device));
   std::vector<double> padded(2 * static_cast<size_t>(c->prog.n_traces));
   CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + c->prog.off_traces, padded.size() * sizeof(double),
@@ -910,6 +1104,7 @@ ajf_status ajf_launch(ajf_ctx* c, double* dev_result) {
   if (!c) return AJF_E_ARG;
   if (!c->planned || !c->uploaded || c->device < 0)
     return fail(c, AJF_E_STATE, "ajf_launch needs a plan and uploaded inputs on a device context");
+  if (is_sliced(c)) return fail(c, AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
   CUDA_TRY(c, cudaSetDevice(c->device));
   ajf_status st = run_program(c);
   if (st != AJF_OK) return st;
@@ -1122,6 +1317,7 @@ ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double e
       return fail(ctxs[0], AJF_E_ARG, "contexts must share one device");
     if (!ctxs[i]->planned || ctxs[i]->alg != alg)
       return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
+    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
     if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
   }
   // every context runs on its own stream so independent circuits overlap on the GPU
@@ -1159,6 +1355,7 @@ ajf_status ajf_fidelity_alg1_batch(ajf_ctx* const* ctxs, int n_ctx, double eps, 
     if (!ctxs[i]) return AJF_E_ARG;
     if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[0], AJF_E_ARG, "contexts on different devices");
     if (!ctxs[i]->planned || ctxs[i]->alg != 1) return fail(ctxs[i], AJF_E_STATE, "context without an Alg. I plan");
+    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
     if (ctxs[i]->opts.precision != ctxs[0]->opts.precision) return fail(ctxs[0], AJF_E_ARG, "mixed precision");
   }
   // every context runs on its own stream so independent circuits overlap on the GPU
@@ -1345,6 +1542,7 @@ ajf_status ajf_fidelity_batch_persistent(ajf_ctx* const* ctxs, int n_ctx, int al
   for (int i = 0; i < n_ctx; ++i) {
     if (!ctxs[i]->planned || ctxs[i]->alg != alg)
       return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
+    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
     (ctxs[i]->prog.persistent ? pers : rest).push_back(ctxs[i]);
   }
   CUDA_TRY(ctxs[0], cudaSetDevice(ctxs[0]->device));

@@ -111,10 +111,11 @@ LeafSpec gate_spec(const GateIn& g, int kind) {
 
 }  // namespace
 
-Network build_alg1(const Inputs& in, const Sequence& seq) {
+Network build_alg1(const Inputs& in, const Sequence& seq, const std::vector<char>& sliced) {
   Network net;
   net.alg = 1;
   net.n_qubits = in.n;
+  net.noise_leaf.assign(in.noises.size(), -1);
   Builder b(net, in.n);
   std::vector<std::vector<int>> kappa(in.noises.size());
   const auto& sk = in.skeleton();
@@ -125,13 +126,15 @@ Network build_alg1(const Inputs& in, const Sequence& seq) {
       b.op(gate_spec(in.ideal[op.index], LEAF_GATE_DAG), op_wires(op, 0), 0);
     } else {
       const NoiseIn& nz = in.noises[op.index];
+      const bool fixed = !sliced.empty() && sliced[op.index];
       LeafSpec s;
       s.kind = LEAF_KRAUS_OPEN;
       s.a = nz.arity;
       s.src = nz.kraus_off;
-      s.nk = nz.nk;
-      s.kbits = nz.kbits;
-      kappa[op.index] = b.op(s, op_wires(op, 0), nz.kbits);
+      s.nk = fixed ? 1 : nz.nk;
+      s.kbits = fixed ? 0 : nz.kbits;
+      net.noise_leaf[op.index] = static_cast<int>(net.leaf_specs.size());
+      kappa[op.index] = b.op(s, op_wires(op, 0), s.kbits);
     }
   }
   b.close(seq.closure);
