@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--trials", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="small-network workloads: keep 256 threads per persistent block")
     ap.add_argument("--no-simplified", action="store_true",
                     help="skip the run with SWAP elimination and local optimisations")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -557,6 +559,14 @@ def run_small_networks(args, world, rank, local):
             torch.cuda.synchronize()
         return total
 
+    # block size of each persistent launch: autotuned on this batch before anything is timed
+    pers_threads = {}
+    if not args.no_autotune:
+        with torch.cuda.stream(stream):
+            for alg in sorted(groups):
+                pers_threads[alg] = ajf.ajf_autotune_persistent([pers[i].handle for i in groups[alg]], reps=5)
+        torch.cuda.synchronize()
+
     # a tiny step takes well under a millisecond: time enough steps for the clock sampler (200 ms)
     if args.workload == "tiny":
         args.steps = max(args.steps, 2000)
@@ -692,6 +702,7 @@ def run_small_networks(args, world, rank, local):
             "vs_baseline": None, "dtype": "f64 (persistent kernel); " + args.precision + " GEMM operands elsewhere",
             "data": "synthetic",
             "config": {"workload": workload, "persistent_networks": len(pers), "other_networks": len(big),
+                       "persistent_threads": {f"alg{a}": t for a, t in pers_threads.items()} or "256 (not tuned)",
                        "persistent_flops_max": None if pers_flops_max == float("inf") else pers_flops_max,
                        "l2": "flushed (256 MiB write) before every step", "trials": args.trials,
                        "parallelism": f"{world} independent ranks (weak scaling)"},

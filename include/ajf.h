@@ -350,6 +350,17 @@ ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double e
  * AJF_E_STATE (a context without a persistent-lowered plan), AJF_E_NOMEM, AJF_E_CUDA. */
 ajf_status ajf_launch_persistent(ajf_ctx *const *ctxs, int n_ctx, double *dev_results);
 
+/* Autotune the persistent launch of this batch (no paper counterpart): its block size -- how many
+ * output elements of a step one network's thread block computes at once -- is measured at 256,
+ * 128 and 64 threads (CUDA events around `reps` launches each, after a warm-up launch), and the
+ * fastest is kept (a smaller block must be at least 3% faster). The choice is remembered for
+ * the process under the batch's signature (device and the networks' structures in order) and used
+ * by every later persistent launch of a batch with that signature; *threads receives it. The
+ * timed launches compute the batch's results as ajf_launch_persistent does. Synchronises the
+ * leading context's stream. Errors: as ajf_launch_persistent, plus AJF_E_ARG (reps < 1,
+ * threads NULL). */
+ajf_status ajf_autotune_persistent(ajf_ctx *const *ctxs, int n_ctx, int reps, int32_t *threads);
+
 /* Like ajf_fidelity_batch, with the contexts planned with AJF_LOWER_PERSISTENT run together in
  * one launch of the persistent kernel (ajf_launch_persistent) and the others on their own
  * streams, concurrently; waits and fills out[i] for every context. *n_persistent (may be NULL)

@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "ajf_fidelity_alg1": (I32, [P, D, ctypes.POINTER(Result)]),
             "ajf_fidelity_alg2": (I32, [P, D, ctypes.POINTER(Result)]),
             "ajf_fidelity": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_autotune_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32)]),
             "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
             "ajf_alg1_traces": (I32, [P, P, I64]),
             "ajf_launch": (I32, [P, P]),
@@ -383,6 +384,17 @@ def ajf_launch_persistent(ctxs: Sequence, dev_results: int = 0) -> None:
     st = lib().ajf_launch_persistent(arr, len(ctxs), ctypes.c_void_p(dev_results) if dev_results else None)
     if st != AJF_OK:
         raise AjfError(st, "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c)))
+
+
+def ajf_autotune_persistent(ctxs: Sequence, reps: int = 5) -> int:
+    """Measure the persistent launch of this batch at 256, 128 and 64 threads per block and keep
+    the fastest for batches of the same signature; returns the block size."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    t = ctypes.c_int32()
+    st = lib().ajf_autotune_persistent(arr, len(ctxs), int(reps), ctypes.byref(t))
+    if st != AJF_OK:
+        raise AjfError(st, "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c)))
+    return int(t.value)
 
 
 def ajf_fidelity_batch_persistent(ctxs: Sequence, alg: int, eps: float = -1.0) -> tuple:

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -103,6 +105,7 @@ struct ajf_ctx {
   std::vector<char> pers_host;
   std::vector<uintptr_t> pers_key;
   size_t pers_smem = 0;
+  int pers_threads = 256;  // block size of the persistent launch (autotuned per batch)
   cudaEvent_t sync_ev = nullptr;  // cross-stream ordering of persistent launches
 };
 
@@ -1399,6 +1402,28 @@ ajf_status sync_event(ajf_ctx* c, cudaEvent_t* ev) {
 
 // Job and op table of a persistent launch over `ctxs`, kept in ctxs[0]'s device buffer and
 // rebuilt only when a context, its arena, its plan or the result pointer changed.
+// ---- block-size autotuning of the persistent launch
+// A batch's signature is its device and the structures (plan keys) of its networks in order; the
+// fastest block size measured for a signature is kept for the process and used by every later
+// persistent launch of a batch with that signature (256 threads until one is measured).
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, int> g_tuned_threads;
+
+std::vector<int64_t> batch_signature(ajf_ctx* const* ctxs, int n) {
+  std::vector<int64_t> sig = {ctxs[0]->device, n};
+  for (int i = 0; i < n; ++i) {
+    sig.push_back(static_cast<int64_t>(ctxs[i]->prog_key.size()));
+    sig.insert(sig.end(), ctxs[i]->prog_key.begin(), ctxs[i]->prog_key.end());
+  }
+  return sig;
+}
+
+int tuned_threads(ajf_ctx* const* ctxs, int n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_threads.find(batch_signature(ctxs, n));
+  return it == g_tuned_threads.end() ? 256 : it->second;
+}
+
 ajf_status persistent_table(ajf_ctx* const* ctxs, int n, double* dev_results) {
   ajf_ctx* lead = ctxs[0];
   std::vector<uintptr_t> key;
@@ -1439,6 +1464,7 @@ ajf_status persistent_table(ajf_ctx* const* ctxs, int n, double* dev_results) {
       ops.push_back(InterpOp{ln.kind, ln.first, ln.count, 0});
     }
   }
+  lead->pers_threads = tuned_threads(ctxs, n);
   const size_t jb = (sizeof(InterpJob) * static_cast<size_t>(n) + 255) & ~size_t(255);
   const size_t bytes = jb + sizeof(InterpOp) * std::max<size_t>(1, ops.size());
   lead->pers_host.assign(bytes, 0);
@@ -1506,7 +1532,7 @@ ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_r
     ProfScope ps(lead, s0, 7, fl, by);
     const cudaError_t e = launch_persistent(reinterpret_cast<const InterpJob*>(lead->pers_dev), n_ctx,
                                             reinterpret_cast<const InterpOp*>(lead->pers_dev + persistent_ops_offset(n_ctx)),
-                                            lead->pers_smem, s0);
+                                            lead->pers_smem, lead->pers_threads, s0);
     if (e != cudaSuccess) return cuda_fail(lead, e, "persistent kernel");
   }
   cudaEvent_t ev0;
@@ -1530,6 +1556,59 @@ ajf_status ajf_launch_persistent(ajf_ctx* const* ctxs, int n_ctx, double* dev_re
     if (!ctxs[i]->planned || !ctxs[i]->prog.persistent)
       return fail(ctxs[i], AJF_E_STATE, "context without a plan made with AJF_LOWER_PERSISTENT");
   return launch_persistent_ctxs(ctxs, n_ctx, dev_results);
+}
+
+ajf_status ajf_autotune_persistent(ajf_ctx* const* ctxs, int n_ctx, int reps, int32_t* threads) {
+  ajf_status st = check_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  if (reps < 1 || !threads) return fail(ctxs[0], AJF_E_ARG, "reps must be >= 1 and threads non-NULL");
+  for (int i = 0; i < n_ctx; ++i)
+    if (!ctxs[i]->planned || !ctxs[i]->prog.persistent)
+      return fail(ctxs[i], AJF_E_STATE, "context without a plan made with AJF_LOWER_PERSISTENT");
+  ajf_ctx* lead = ctxs[0];
+  CUDA_TRY(lead, cudaSetDevice(lead->device));
+  st = launch_persistent_ctxs(ctxs, n_ctx, nullptr);  // uploads, job table, first-launch costs
+  if (st != AJF_OK) return st;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(lead, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(lead, cudaGetLastError(), "cudaEventCreate");
+  }
+  int best = 256;
+  float best_ms = 0;
+  for (int t : {256, 128, 64}) {
+    lead->pers_threads = t;
+    st = launch_persistent_ctxs(ctxs, n_ctx, nullptr);  // warm-up at this block size
+    cudaError_t e = cudaEventRecord(e0, lead->stream);
+    for (int r = 0; st == AJF_OK && e == cudaSuccess && r < reps; ++r) {
+      lead->pers_threads = t;
+      st = launch_persistent_ctxs(ctxs, n_ctx, nullptr);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, lead->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (st == AJF_OK && e != cudaSuccess) st = cuda_fail(lead, e, "autotune timing");
+    if (st != AJF_OK) break;
+    if (t == 256 || ms < 0.97f * best_ms) {  // a smaller block must win clearly
+      best = t;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != AJF_OK) {
+    lead->pers_threads = tuned_threads(ctxs, n_ctx);
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_threads[batch_signature(ctxs, n_ctx)] = best;
+  }
+  lead->pers_threads = best;
+  *threads = best;
+  return AJF_OK;
 }
 
 ajf_status ajf_fidelity_batch_persistent(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out,

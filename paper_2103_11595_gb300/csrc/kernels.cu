@@ -959,15 +959,17 @@ cudaError_t set_kernel_smem_limits() {
 
 namespace ajf {
 
-cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem,
+cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem, int threads,
                               cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
+  // block size: a power of two from one warp to the kernel's 256 (its reduction buffer)
+  if (threads < 32 || threads > 256 || (threads & (threads - 1))) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
   }
-  k_persistent<<<n_jobs, 256, smem, s>>>(d_jobs, d_ops);
+  k_persistent<<<n_jobs, threads, smem, s>>>(d_jobs, d_ops);
   return cudaGetLastError();
 }
 

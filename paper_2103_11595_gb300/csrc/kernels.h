@@ -37,7 +37,7 @@ cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblock
 // Persistent kernel: one thread block per network runs that network's whole program (leaves,
 // all steps level by level, the FP64 trace and F) -- n_jobs networks in one launch. `smem`:
 // dynamic shared memory per block (the largest work region among the jobs with job.smem = 1).
-cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem,
+cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpOp* d_ops, size_t smem, int threads,
                               cudaStream_t s);
 constexpr size_t kPersistentSmemMax = 96 * 1024;
 

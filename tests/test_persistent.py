@@ -198,3 +198,42 @@ def test_launch_persistent_device_results_repeat(gpu):
         assert abs(r["F"] - refs[0]) <= 1e-12
     finally:
         _close(ctxs)
+
+
+def test_autotune_needs_device_batch():
+    with ajf.Context(-1) as c:
+        ajf.load_instance(c.handle, W.tiny(0))
+        ajf.ajf_plan(c.handle, 2, lowering="persistent")
+        with pytest.raises(ajf.AjfError) as e:
+            ajf.ajf_autotune_persistent([c.handle])
+        assert e.value.status == ajf.AJF_E_ARG  # host-only context
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("alg", [1, 2])
+def test_autotuned_block_size_keeps_results(gpu, alg):
+    """The autotuner times the batch at 256, 128 and 64 threads per block; the chosen size is
+    used by later launches of the same batch, and every size gives the oracle's F_J."""
+    from oracle import dense
+    insts = [W.tiny(s) for s in range(40)]
+    refs = [dense.fidelity(i)["F"] for i in insts]
+    ctxs = _contexts(insts, alg)
+    try:
+        with pytest.raises(ajf.AjfError):
+            ajf.ajf_autotune_persistent([c.handle for c in ctxs], reps=0)
+        t = ajf.ajf_autotune_persistent([c.handle for c in ctxs], reps=3)
+        assert t in (64, 128, 256)
+        res, n_p = ajf.ajf_fidelity_batch_persistent([c.handle for c in ctxs], alg)
+        assert n_p == len(insts)
+        for r, ref in zip(res, refs):
+            assert abs(r["F"] - ref) <= 1e-12
+        # a new batch of the same structures (fresh contexts) runs at the remembered size
+        again = _contexts(insts, alg)
+        try:
+            res2, _ = ajf.ajf_fidelity_batch_persistent([c.handle for c in again], alg)
+            for r, ref in zip(res2, refs):
+                assert abs(r["F"] - ref) <= 1e-12
+        finally:
+            _close(again)
+    finally:
+        _close(ctxs)
