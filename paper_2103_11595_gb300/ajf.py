@@ -417,7 +417,7 @@ def pack_gates(gates) -> tuple:
     qubits = np.array([q for g in gates for q in g.qubits], dtype=np.int32)
     mats = (np.concatenate([np.asarray(g.mat, dtype=np.complex128).reshape(-1) for g in gates])
             if gates else np.zeros(0, dtype=np.complex128))
-    return arity, qubits, mats
+    return arity, qubits, np.ascontiguousarray(mats)
 
 
 def load_instance(ctx, inst) -> None:
@@ -427,6 +427,28 @@ def load_instance(ctx, inst) -> None:
         ajf_load_circuit(ctx, AJF_IMPL, inst.n, *pack_gates(inst.impl))
     for nz in inst.noises:
         ajf_add_noise(ctx, nz.after_gate, nz.qubits, nz.kraus)
+
+
+def pack_instance(inst) -> tuple:
+    """The flat C-ABI arrays of an instance, made once: (n, ideal arrays, implementation arrays or
+    None, [(after_gate, qubits, kraus)]), each array contiguous in the ABI's dtype."""
+    impl = getattr(inst, "impl", None)
+    noises = [(int(nz.after_gate), np.ascontiguousarray(nz.qubits, dtype=np.int32),
+               np.ascontiguousarray(nz.kraus, dtype=np.complex128)) for nz in inst.noises]
+    return (int(inst.n), pack_gates(inst.ideal), pack_gates(impl) if impl is not None else None, noises)
+
+
+def load_packed(ctx, packed) -> None:
+    """load_instance from pack_instance's arrays: the C-ABI calls only."""
+    n, ideal, impl, noises = packed
+    L = lib()
+    a, q, m = ideal
+    _check(ctx, L.ajf_load_circuit(ctx, AJF_IDEAL, n, int(a.size), _ptr(a), _ptr(q), _ptr(m)))
+    if impl is not None:
+        a, q, m = impl
+        _check(ctx, L.ajf_load_circuit(ctx, AJF_IMPL, n, int(a.size), _ptr(a), _ptr(q), _ptr(m)))
+    for after, qq, k in noises:
+        _check(ctx, L.ajf_add_noise(ctx, after, int(qq.size), _ptr(qq), int(k.shape[0]), _ptr(k)))
 
 
 class Context:

@@ -166,3 +166,16 @@ def test_precision_config_as_written_is_over_budget():
         ajf.load_instance(c.handle, W.precision(0, depth=4))
         info = ajf.ajf_plan(c.handle, 2, trials=2, mem_budget_bytes=280e9)
         assert info["width"] <= 26
+
+
+def test_load_packed_matches_load_instance():
+    """The flat-array loader (the C-ABI calls alone) gives the same plan as load_instance."""
+    inst = W.random_small(5, n=4, n_gates=20, n_noises=3, two_qubit_noise=True)
+    inst.impl = list(inst.ideal)
+    infos = []
+    for loader in (lambda c: ajf.load_instance(c, inst), lambda c: ajf.load_packed(c, ajf.pack_instance(inst))):
+        with host_ctx() as c:
+            loader(c.handle)
+            infos.append(ajf.ajf_plan(c.handle, 2, trials=2))
+    for k in ("cmacs", "width", "n_leaves", "upload_bytes"):
+        assert infos[0][k] == infos[1][k]
