@@ -231,6 +231,36 @@ ajf_status ajf_workspace_size(const ajf_ctx *ctx, size_t *bytes);
  * Errors: AJF_E_STATE, AJF_E_ARG (eps > 1), AJF_E_NOMEM, AJF_E_CUDA. */
 ajf_status ajf_fidelity_alg1(ajf_ctx *ctx, double eps, ajf_result *out);
 
+/* Progress of a sliced Alg. I evaluation (checkpoint / resume; no paper counterpart). For Alg. I
+ * over very many Kraus combinations the work can be split over calls, processes or machines:
+ * the state is the next slice (in the plan's order, heaviest first) and the partial sum. */
+typedef struct ajf_alg1_state {
+  int64_t next_slice;  /* slices done                                                          */
+  int64_t n_slices;    /* slices of the plan: prod of n_k over the fixed noises               */
+  double S;            /* sum |t_i|^2 over the traces of the slices done (FP64)                */
+  int64_t traces_done; /* traces of the slices done                                            */
+  uint64_t plan_sig;   /* the plan's structure, slicing, precision and input values (hash)     */
+} ajf_alg1_state;
+
+/* Run up to max_slices more slices (max_slices <= 0: all that remain) of a sliced Alg. I plan,
+ * from where the context stopped (the first call after ajf_plan starts at slice 0). eps >= 0
+ * stops as soon as the partial F exceeds 1 - eps. out describes the slices done so far: F is a
+ * lower bound of F_J until n_slices are done; equivalent = 1 once the partial F exceeds 1 - eps,
+ * 0 once every slice is done and it does not, -1 while undecided (or eps < 0).
+ * Errors: AJF_E_STATE (no sliced Alg. I plan, host-only context), AJF_E_ARG, AJF_E_CUDA. */
+ajf_status ajf_alg1_continue(ajf_ctx *ctx, double eps, int64_t max_slices, ajf_result *out);
+
+/* Copy the progress of the context's sliced Alg. I evaluation into *state (host only).
+ * Errors: AJF_E_ARG, AJF_E_STATE (no sliced Alg. I plan). */
+ajf_status ajf_alg1_checkpoint(const ajf_ctx *ctx, ajf_alg1_state *state);
+
+/* Resume from a checkpoint: the context must hold the same sliced Alg. I plan of the same input
+ * values (plan_sig). The next ajf_alg1_continue starts at state->next_slice with the partial
+ * sum. The traces of the slices done before the checkpoint are not part of it, so
+ * ajf_alg1_traces reports AJF_E_STATE after a resumed evaluation (F, S and 1 - F are complete).
+ * Errors: AJF_E_ARG (NULL, another plan or other values, fields out of range), AJF_E_STATE. */
+ajf_status ajf_alg1_restore(ajf_ctx *ctx, const ajf_alg1_state *state);
+
 /* Alg. II (Sec. IV-B): F_J from the one doubled network. Same contract as ajf_fidelity_alg1,
  * requiring ajf_plan(ctx, 2, ...). */
 ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);

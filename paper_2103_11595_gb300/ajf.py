@@ -72,6 +72,14 @@ class Result(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class Alg1State(ctypes.Structure):
+    _fields_ = [("next_slice", ctypes.c_int64), ("n_slices", ctypes.c_int64), ("S", ctypes.c_double),
+                ("traces_done", ctypes.c_int64), ("plan_sig", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class AjfError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"ajf status {status}: {message}")
@@ -101,6 +109,9 @@ def lib() -> ctypes.CDLL:
             "ajf_fidelity_alg1": (I32, [P, D, ctypes.POINTER(Result)]),
             "ajf_fidelity_alg2": (I32, [P, D, ctypes.POINTER(Result)]),
             "ajf_fidelity": (I32, [P, D, ctypes.POINTER(Result)]),
+            "ajf_alg1_continue": (I32, [P, D, I64, ctypes.POINTER(Result)]),
+            "ajf_alg1_checkpoint": (I32, [P, ctypes.POINTER(Alg1State)]),
+            "ajf_alg1_restore": (I32, [P, ctypes.POINTER(Alg1State)]),
             "ajf_autotune_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32)]),
             "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
             "ajf_alg1_traces": (I32, [P, P, I64]),
@@ -231,6 +242,24 @@ def ajf_fidelity(ctx, eps: float = -1.0) -> dict:
     r = Result()
     _check(ctx, lib().ajf_fidelity(ctx, float(eps), ctypes.byref(r)))
     return r.as_dict()
+
+
+def ajf_alg1_continue(ctx, eps: float = -1.0, max_slices: int = 0) -> dict:
+    """Run up to max_slices more slices of a sliced Alg. I plan (0: all that remain)."""
+    r = Result()
+    _check(ctx, lib().ajf_alg1_continue(ctx, float(eps), int(max_slices), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ajf_alg1_checkpoint(ctx) -> dict:
+    st = Alg1State()
+    _check(ctx, lib().ajf_alg1_checkpoint(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ajf_alg1_restore(ctx, state: dict) -> None:
+    st = Alg1State(**state)
+    _check(ctx, lib().ajf_alg1_restore(ctx, ctypes.byref(st)))
 
 
 def ajf_planned_alg(ctx) -> int:

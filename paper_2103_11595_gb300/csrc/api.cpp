@@ -72,6 +72,11 @@ struct ajf_ctx {
   // sliced Alg. I plan: noises with a fixed Kraus index and their leaves; traces gathered per slice
   std::vector<int> slice_noises, slice_leaves;
   std::vector<double> slice_traces;
+  // progress of a sliced Alg. I evaluation: slices done (in the plan's order), their sum |t|^2,
+  // traces done, and whether slice_traces holds every trace done (false after a restore)
+  int64_t slice_next = 0, slice_done = 0;
+  double slice_S = 0;
+  bool slice_traces_valid = true;
   // structural plan cache: the path is reused when the network's shape and options repeat
   std::vector<int64_t> plan_key;
   bool path_valid = false;
@@ -439,7 +444,9 @@ bool is_sliced(const ajf_ctx* c) { return c->planned && !c->slice_noises.empty()
 // Sliced Alg. I (the remark after Alg. I on stopping early): one run of the program per
 // combination of the fixed Kraus indices, heaviest first; each run's sum |t|^2 is added in FP64
 // and its traces are scattered into the full, lexicographically ordered trace array.
-ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) {
+// Runs up to max_slices (<= 0: all) further slices from the context's progress (reset: from the
+// first); stops early once the partial F exceeds 1 - eps (eps >= 0).
+ajf_status run_slices(ajf_ctx* c, double eps, int64_t max_slices, bool reset, ajf_result* out) {
   const Program& P = c->prog;
   const auto& nz = c->in.noises;
   const int m = static_cast<int>(nz.size());
@@ -485,14 +492,20 @@ ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) {
   int64_t per_slice = 1;
   for (int j = 0; j < m; ++j)
     if (!fixed[j]) per_slice *= nz[j].nk;
-  c->slice_traces.assign(2 * static_cast<size_t>(total), 0.0);
+  if (reset) {
+    c->slice_next = 0;
+    c->slice_done = 0;
+    c->slice_S = 0;
+    c->slice_traces_valid = true;
+    c->slice_traces.assign(2 * static_cast<size_t>(total), 0.0);
+  }
   std::vector<double> padded(2 * static_cast<size_t>(P.n_traces));
   const size_t leaves_at = P.off_leaves - P.off_desc;
   const int nsq = 2 * c->n;
-  double S = 0;
-  int64_t done = 0;
-  bool early = false;
-  for (const Slice& sl : slices) {
+  const int64_t n_slices = static_cast<int64_t>(slices.size());
+  for (int64_t ran = 0; c->slice_next < n_slices && (max_slices <= 0 || ran < max_slices); ++ran) {
+    if (eps >= 0 && std::ldexp(c->slice_S, -nsq) > 1.0 - eps) break;  // already decided
+    const Slice& sl = slices[c->slice_next];
     for (int i = 0; i < ns; ++i) {
       const int j = c->slice_noises[i];
       const int d = 1 << nz[j].arity;
@@ -511,7 +524,7 @@ ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     st = check_status_words(c);
     if (st != AJF_OK) return st;
-    S += res[0];
+    c->slice_S += res[0];
     // scatter: odometer over the open noises' Kraus indices
     std::vector<int> digit(m, 0);
     for (int i = 0; i < ns; ++i) digit[c->slice_noises[i]] = sl.k[i];
@@ -529,20 +542,44 @@ ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) {
         digit[j] = 0;
       }
     }
-    done += per_slice;
-    if (eps >= 0 && done < total && std::ldexp(S, -nsq) > 1.0 - eps) {
-      early = true;
-      break;
-    }
+    c->slice_done += per_slice;
+    c->slice_next++;
   }
+  const double S = c->slice_S;
+  const bool all = c->slice_next == n_slices;
   out->S = S;
   out->F = std::ldexp(S, -nsq);
   out->one_minus_F = std::ldexp(std::ldexp(1.0, nsq) - S, -nsq);
-  out->traces_done = done;
-  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->traces_done = c->slice_done;
+  // decided "yes" by any partial sum above 1 - eps; "no" only once every slice is in
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : (all ? 0 : -1));
   out->reserved = 0;
-  c->have_alg1 = !early;
+  c->have_alg1 = all && c->slice_traces_valid;
   return AJF_OK;
+}
+
+ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) { return run_slices(c, eps, 0, true, out); }
+
+int64_t slice_count(const ajf_ctx* c) {
+  int64_t n = 1;
+  for (int j : c->slice_noises) n *= c->in.noises[j].nk;
+  return n;
+}
+
+// Signature of a sliced plan and its input values (FNV-1a over the plan key and the packed
+// matrices): a checkpoint resumes only where the same slices would sum the same traces.
+uint64_t slice_signature(const ajf_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(c->prog_key.data(), c->prog_key.size() * sizeof(int64_t));
+  mix(c->in.packed.data(), c->in.packed.size() * sizeof(double));
+  return h;
 }
 
 ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
@@ -918,6 +955,10 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   c->opts = o;
   c->alg = alg;
   c->slice_noises = slice_noises;
+  c->slice_next = c->slice_done = 0;
+  c->slice_S = 0;
+  c->slice_traces_valid = true;
+  c->slice_traces.clear();
   c->slice_leaves.clear();
   for (int j : slice_noises) c->slice_leaves.push_back(c->net.noise_leaf[j]);
   c->planned = true;
@@ -1007,6 +1048,50 @@ ajf_status ajf_upload(ajf_ctx* c) {
 ajf_status ajf_fidelity_alg1(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 1, eps, out); }
 
 ajf_status ajf_fidelity_alg2(ajf_ctx* c, double eps, ajf_result* out) { return fidelity(c, 2, eps, out); }
+
+ajf_status ajf_alg1_continue(ajf_ctx* c, double eps, int64_t max_slices, ajf_result* out) {
+  if (!c) return AJF_E_ARG;
+  if (!out) return fail(c, AJF_E_ARG, "out is NULL");
+  if (!c->planned || c->alg != 1 || !is_sliced(c)) return fail(c, AJF_E_STATE, "needs a sliced Alg. I plan");
+  if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
+  if (eps > 1.0) return fail(c, AJF_E_ARG, "eps > 1");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (!c->uploaded) {
+    ajf_status st = do_upload(c);
+    if (st != AJF_OK) return st;
+  }
+  const bool fresh = c->slice_next == 0 && c->slice_traces.empty();
+  return run_slices(c, eps, max_slices, fresh, out);
+}
+
+ajf_status ajf_alg1_checkpoint(const ajf_ctx* c, ajf_alg1_state* st) {
+  if (!c || !st) return AJF_E_ARG;
+  if (!c->planned || c->alg != 1 || !is_sliced(c)) return AJF_E_STATE;
+  st->next_slice = c->slice_next;
+  st->n_slices = slice_count(c);
+  st->S = c->slice_S;
+  st->traces_done = c->slice_done;
+  st->plan_sig = slice_signature(c);
+  return AJF_OK;
+}
+
+ajf_status ajf_alg1_restore(ajf_ctx* c, const ajf_alg1_state* st) {
+  if (!c) return AJF_E_ARG;
+  if (!st) return fail(c, AJF_E_ARG, "state is NULL");
+  if (!c->planned || c->alg != 1 || !is_sliced(c)) return fail(c, AJF_E_STATE, "needs a sliced Alg. I plan");
+  const int64_t n = slice_count(c);
+  if (st->plan_sig != slice_signature(c) || st->n_slices != n)
+    return fail(c, AJF_E_ARG, "checkpoint is of another plan or other input values");
+  if (st->next_slice < 0 || st->next_slice > n || !(st->S >= 0) || st->traces_done < 0)
+    return fail(c, AJF_E_ARG, "checkpoint fields out of range");
+  c->slice_next = st->next_slice;
+  c->slice_S = st->S;
+  c->slice_done = st->traces_done;
+  c->slice_traces.assign(2 * static_cast<size_t>(real_combinations(c)), 0.0);
+  c->slice_traces_valid = st->next_slice == 0;  // the traces of earlier slices are not in a checkpoint
+  c->have_alg1 = false;
+  return AJF_OK;
+}
 
 ajf_status ajf_fidelity(ajf_ctx* c, double eps, ajf_result* out) {
   if (!c) return AJF_E_ARG;

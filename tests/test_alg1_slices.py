@@ -159,3 +159,63 @@ def test_auto_matches_both_algorithms(gpu):
         ref = dense.fidelity(inst)["F"]
         r, _, alg = _run(inst, alg=ajf.AJF_ALG_AUTO)
         assert alg in (1, 2) and abs(r["F"] - ref) <= 1e-12
+
+
+def test_checkpoint_of_a_host_plan():
+    inst = _mixed(0)
+    with ajf.Context(-1) as c:
+        ajf.load_instance(c.handle, inst)
+        ajf.ajf_plan(c.handle, 1, trials=2, alg1_slices=2)
+        st = ajf.ajf_alg1_checkpoint(c.handle)
+        assert st["next_slice"] == 0 and st["n_slices"] == 4 * 2 and st["S"] == 0
+        ajf.ajf_alg1_restore(c.handle, dict(st, next_slice=3, S=1.5, traces_done=6))
+        assert ajf.ajf_alg1_checkpoint(c.handle)["next_slice"] == 3
+        for bad in (dict(st, plan_sig=st["plan_sig"] ^ 1), dict(st, next_slice=9), dict(st, n_slices=5)):
+            with pytest.raises(ajf.AjfError) as e:
+                ajf.ajf_alg1_restore(c.handle, bad)
+            assert e.value.status == ajf.AJF_E_ARG
+        with pytest.raises(ajf.AjfError) as e:
+            ajf.ajf_alg1_continue(c.handle)
+        assert e.value.status == ajf.AJF_E_STATE  # host-only context
+        # other input values: the checkpoint does not apply
+        other = _mixed(1)
+        ajf.load_instance(c.handle, other)
+        ajf.ajf_plan(c.handle, 1, trials=2, alg1_slices=2)
+        with pytest.raises(ajf.AjfError):
+            ajf.ajf_alg1_restore(c.handle, st)
+        # an unsliced plan has no progress to checkpoint
+        ajf.ajf_plan(c.handle, 1, trials=2)
+        with pytest.raises(ajf.AjfError) as e:
+            ajf.ajf_alg1_checkpoint(c.handle)
+        assert e.value.status == ajf.AJF_E_STATE
+
+
+@pytest.mark.gpu
+def test_resume_from_checkpoint_in_a_new_context(gpu):
+    """Slices 0..2 in one context, a checkpoint, the rest in another context: the same F, S and
+    1 - F as one full evaluation (and as the oracle)."""
+    from oracle import dense
+    for s in range(3):
+        inst = _mixed(s)
+        ref = dense.fidelity(inst)
+        with ajf.Context(0) as a:
+            ajf.load_instance(a.handle, inst)
+            ajf.ajf_plan(a.handle, 1, trials=2, alg1_slices=2)
+            part = ajf.ajf_alg1_continue(a.handle, max_slices=3)
+            assert part["equivalent"] == -1 and part["traces_done"] == 3 * 2
+            st = ajf.ajf_alg1_checkpoint(a.handle)
+            assert st["next_slice"] == 3
+        with ajf.Context(0) as b:
+            ajf.load_instance(b.handle, inst)
+            ajf.ajf_plan(b.handle, 1, trials=2, alg1_slices=2)
+            ajf.ajf_alg1_restore(b.handle, st)
+            r = ajf.ajf_alg1_continue(b.handle, eps=1e-9)
+            assert r["traces_done"] == inst.n_combinations() and r["equivalent"] == 0
+            assert abs(r["F"] - ref["F"]) <= 1e-12 and abs(r["one_minus_F"] - ref["one_minus_F"]) <= 1e-12
+            with pytest.raises(ajf.AjfError) as e:
+                ajf.ajf_alg1_traces(b.handle, inst.n_combinations())
+            assert e.value.status == ajf.AJF_E_STATE
+            # the same context, continued in single slices without a restore, keeps its traces
+            full = ajf.ajf_fidelity_alg1(b.handle)
+            assert abs(full["F"] - ref["F"]) <= 1e-12
+            np.testing.assert_allclose(ajf.ajf_alg1_traces(b.handle, inst.n_combinations()), ref["traces"], atol=1e-12 * 8)
