@@ -109,8 +109,15 @@ typedef struct ajf_plan_opts {
   int32_t simplify;        /* AJF_SIMPLIFY_* flags; 0 = the sequence as given                  */
   int32_t alg1_slices;     /* Alg. I only: fix the Kraus index of this many noises per slice   */
                            /* (0 = none; see ajf_fidelity_alg1 for the early exit it enables)  */
-  int32_t reserved[5];     /* must be zero                                                     */
+  int32_t slice_bonds;     /* bond slicing: 0 = none; s > 0 = slice s closed labels; AJF_SLICE_AUTO */
+                           /* = the fewest that bring the arena within mem_budget_bytes        */
+  int32_t reserved[4];     /* must be zero                                                     */
 } ajf_plan_opts;
+
+/* opts.slice_bonds = AJF_SLICE_AUTO: slice only as far as the memory budget needs. */
+enum { AJF_SLICE_AUTO = -1 };
+/* At most this many sliced labels (2^24 contractions of the sliced network per evaluation). */
+enum { AJF_MAX_SLICE_BONDS = 24 };
 
 typedef struct ajf_plan_info {
   double cmacs;          /* sum over pairwise steps of M*N*K complex multiply-adds             */
@@ -131,6 +138,10 @@ typedef struct ajf_plan_info {
   int32_t plan_cached;   /* 1: the path was reused from the previous plan of the same structure  */
   int32_t n_removed;     /* gates removed by opts.simplify (SWAPs, cancelled pairs, identities)  */
   double upload_bytes;   /* host -> device bytes of one upload (descriptors + packed inputs)     */
+  int32_t n_sliced_bonds; /* labels sliced (opts.slice_bonds): the evaluation runs 2^n_sliced_bonds */
+                          /* contractions; cmacs, flops, bytes, gemm_* count all of them, width   */
+                          /* and arena_bytes describe one                                          */
+  int32_t reserved;
 } ajf_plan_info;
 
 /* Per-kernel-class timing collected while profiling is on (CUDA events around every launch on
@@ -197,6 +208,20 @@ ajf_status ajf_clear_noise(ajf_ctx *ctx);
  * Kraus operators (earlier noise first on ties) get a fixed Kraus index; the network keeps the
  * open indices of the others, and ajf_fidelity_alg1 runs it once per combination of the fixed
  * indices. s must not exceed the number of noises; not with AJF_LOWER_PERSISTENT.
+ * opts.slice_bonds (bond slicing; the paper contracts each network whole, Sec. IV-C, and has
+ * no counterpart): a closed label b of the network is fixed to 0 in one contraction and to 1 in
+ * another, in both tensors that carry it, and the two results are added. This is the same sum
+ * over label values that the full contraction is, so the result is unchanged, while every tensor
+ * carrying b is half the size. s labels give 2^s contractions of a network whose widest tensor
+ * is up to 2^s times smaller: plans over the memory budget become runnable at the price of work.
+ * The labels are chosen greedily on the planned path (those carried by the most of its widest
+ * tensors first; Alg. I's open Kraus indices are never sliced, and no leaf loses its last
+ * label), and the same path runs on the sliced network. s > 0 slices s labels (fewer when no
+ * more can be sliced; info->n_sliced_bonds tells); AJF_SLICE_AUTO slices none when the plan fits the
+ * budget, else the fewest that make it fit, and reports AJF_E_BUDGET beyond
+ * AJF_MAX_SLICE_BONDS. Not with opts.alg1_slices or AJF_LOWER_PERSISTENT. Alg. II adds the
+ * slices' scalars, Alg. I the slices' traces (complex, FP64, before |t|^2 is formed), both on the
+ * host in FP64; eps decides only after every slice (no early exit).
  * Errors: AJF_E_STATE (no circuit), AJF_E_ARG (bad alg/option), AJF_E_BUDGET (the best plan's
  * arena exceeds the budget; info is still filled), AJF_E_UNSUPPORTED (tensor-core precision on
  * a device without tcgen05). */

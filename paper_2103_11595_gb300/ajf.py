@@ -30,7 +30,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("planner", ctypes.c_int32), ("precision", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_double),
                 ("lowering", ctypes.c_int32), ("simplify", ctypes.c_int32), ("alg1_slices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("slice_bonds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -39,7 +39,8 @@ class PlanInfo(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("width", ctypes.c_int32), ("n_steps", ctypes.c_int32),
                 ("n_gemm_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32), ("n_open_bits", ctypes.c_int32),
                 ("planner_used", ctypes.c_int32), ("n_launches", ctypes.c_int32), ("n_tc_gemms", ctypes.c_int32),
-                ("plan_cached", ctypes.c_int32), ("n_removed", ctypes.c_int32), ("upload_bytes", ctypes.c_double)]
+                ("plan_cached", ctypes.c_int32), ("n_removed", ctypes.c_int32), ("upload_bytes", ctypes.c_double),
+                ("n_sliced_bonds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -53,6 +54,7 @@ class KernelStats(ctypes.Structure):
 AJF_LOWER_DEFAULT, AJF_LOWER_PERSISTENT = 0, 1
 AJF_ALG_AUTO = 0
 AJF_SIMPLIFY_SWAP, AJF_SIMPLIFY_CANCEL = 1, 2
+AJF_SLICE_AUTO, AJF_MAX_SLICE_BONDS = -1, 24
 SIMPLIFY = {"none": 0, "swap": AJF_SIMPLIFY_SWAP, "cancel": AJF_SIMPLIFY_CANCEL,
             "all": AJF_SIMPLIFY_SWAP | AJF_SIMPLIFY_CANCEL}
 LOWERINGS = {"default": AJF_LOWER_DEFAULT, "persistent": AJF_LOWER_PERSISTENT}
@@ -196,9 +198,11 @@ def ajf_clear_noise(ctx) -> None:
 
 def ajf_plan(ctx, alg: int, planner="auto", precision="f64", trials: int = 0, use_graph: bool = False,
              seed: int = 0, mem_budget_bytes: float = 0.0, lowering="default", simplify="none",
-             alg1_slices: int = 0) -> dict:
-    """alg: 1, 2 or AJF_ALG_AUTO (0)."""
+             alg1_slices: int = 0, slice_bonds=0) -> dict:
+    """alg: 1, 2 or AJF_ALG_AUTO (0). slice_bonds: a count of labels to slice, or "auto"
+    (AJF_SLICE_AUTO: as many as the memory budget needs)."""
     o = PlanOpts()
+    o.slice_bonds = AJF_SLICE_AUTO if slice_bonds == "auto" else int(slice_bonds)
     o.simplify = SIMPLIFY[simplify] if isinstance(simplify, str) else int(simplify)
     o.alg1_slices = int(alg1_slices)
     o.lowering = LOWERINGS[lowering] if isinstance(lowering, str) else int(lowering)

@@ -55,6 +55,8 @@ struct LeafSpec {
   int64_t src = 0;      // complex offset of the source matrix / first Kraus operator
   int32_t nk = 0;       // Kraus operators (LEAF_KRAUS_OPEN, LEAF_SUPEROP)
   int32_t kbits = 0;    // open Kraus-index bits (LEAF_KRAUS_OPEN)
+  uint32_t fix_mask = 0;  // bond slicing: bits of the full leaf index (before slicing) whose
+                          // labels are sliced; their values are set per slice on the device
 };
 
 // A tensor's labels are listed from bit 0 (stride 1) upward: element index = sum_i bit_i * 2^i.
@@ -104,6 +106,14 @@ void evaluate_path(const Network& net, Path& path, const PlanParams& p);
 Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature);
 Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed);
 Path plan_learned(const Network& net, const PlanParams& p, uint64_t seed, bool* used);
+// Bond slicing. choose_slice_labels: `count` closed labels to fix, picked greedily on `path` so
+// that the widest tensors shrink first (labels whose removal would leave a leaf without labels
+// are never picked). slice_network: the network with those labels removed from its leaves
+// (LeafSpec::fix_mask marks where they were). restrict_path: `path` over the sliced network (a
+// step that becomes a scalar joins the final tensors), with its cost evaluated.
+std::vector<int> choose_slice_labels(const Network& net, const Path& path, int count);
+Network slice_network(const Network& net, const std::vector<int>& labels);
+Path restrict_path(const Network& sliced, const Path& path, const std::vector<int>& labels, const PlanParams& p);
 // Replay `ref` and append (chosen merge, other candidate) feature pairs; returns the pair count.
 int learned_dataset(const Network& net, const Path& ref, uint64_t seed, int negatives, std::vector<float>& out);
 

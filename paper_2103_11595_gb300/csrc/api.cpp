@@ -77,7 +77,18 @@ struct ajf_ctx {
   int64_t slice_next = 0, slice_done = 0;
   double slice_S = 0;
   bool slice_traces_valid = true;
+  // bond slicing: the sliced labels, and for each leaf that carries one, the positions of its
+  // sliced labels in the full leaf index with the label's index into bond_labels
+  std::vector<int> bond_labels;
+  struct BondLeaf {
+    int leaf;
+    std::vector<std::pair<int, int>> bits;  // (position in the full leaf index, sliced label)
+  };
+  std::vector<BondLeaf> bond_leaves;
+  std::vector<double> bond_traces;  // Alg. I: FP64 sums of the slices' traces (padded order)
   // structural plan cache: the path is reused when the network's shape and options repeat
+  // (path_full: the unsliced path; path: the one lowered, restricted to the sliced network)
+  Path path_full;
   std::vector<int64_t> plan_key;
   bool path_valid = false;
   // lowered-program cache: a re-plan of the same structure, precision and lowering keeps the
@@ -440,6 +451,9 @@ int64_t real_combinations(const ajf_ctx* c) {
 }
 
 bool is_sliced(const ajf_ctx* c) { return c->planned && !c->slice_noises.empty(); }
+bool bond_sliced(const ajf_ctx* c) { return c->planned && !c->bond_labels.empty(); }
+// plans that run the program more than once per evaluation (Kraus-index or bond slices)
+bool multi_run(const ajf_ctx* c) { return is_sliced(c) || bond_sliced(c); }
 
 // Sliced Alg. I (the remark after Alg. I on stopping early): one run of the program per
 // combination of the fixed Kraus indices, heaviest first; each run's sum |t|^2 is added in FP64
@@ -560,6 +574,66 @@ ajf_status run_slices(ajf_ctx* c, double eps, int64_t max_slices, bool reset, aj
 
 ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) { return run_slices(c, eps, 0, true, out); }
 
+// Bond-sliced plan: one run of the program per assignment of the sliced labels, the leaves that
+// carry them taking the assignment's bits (fix_val; only the leaf descriptors change between
+// runs, which also holds under CUDA-graph replay). Alg. II adds the runs' real scalars, Alg. I
+// the runs' complex traces before |t|^2 is formed: both are linear in the runs, F is not.
+// Sums are FP64 in run order (Neumaier-compensated for S).
+ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  const Program& P = c->prog;
+  const int nb = static_cast<int>(c->bond_labels.size());
+  const size_t leaves_at = P.off_leaves - P.off_desc;
+  const int64_t runs = int64_t(1) << nb;
+  std::vector<double> padded;
+  if (alg == 1) {
+    padded.assign(2 * static_cast<size_t>(P.n_traces), 0.0);
+    c->bond_traces.assign(padded.size(), 0.0);
+  }
+  double S = 0, comp = 0;
+  auto add = [&](double x) {  // Neumaier summation
+    const double t = S + x;
+    comp += std::fabs(S) >= std::fabs(x) ? (S - t) + x : (x - t) + S;
+    S = t;
+  };
+  for (int64_t v = 0; v < runs; ++v) {
+    for (auto& bl : c->bond_leaves) {
+      uint16_t val = 0;
+      for (auto& pb : bl.bits)
+        if ((v >> pb.second) & 1) val = static_cast<uint16_t>(val | (1u << pb.first));
+      std::memcpy(c->desc_image.data() + leaves_at + bl.leaf * sizeof(LeafDev) + offsetof(LeafDev, fix_val), &val,
+                  sizeof(val));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, c->desc_image.data() + leaves_at,
+                                P.leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, c->stream));
+    ajf_status st = run_program(c);
+    if (st != AJF_OK) return st;
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + P.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    if (alg == 1)
+      CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + P.off_traces, padded.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    if (alg == 2) add(res[0]);
+    else
+      for (size_t i = 0; i < padded.size(); ++i) c->bond_traces[i] += padded[i];
+  }
+  if (alg == 1)
+    for (size_t i = 0; i < c->bond_traces.size(); i += 2)
+      add(c->bond_traces[i] * c->bond_traces[i] + c->bond_traces[i + 1] * c->bond_traces[i + 1]);
+  S += comp;
+  const int nsq = 2 * c->n;
+  out->S = S;
+  out->F = std::ldexp(S, -nsq);
+  out->one_minus_F = std::ldexp(std::ldexp(1.0, nsq) - S, -nsq);
+  out->traces_done = alg == 1 ? real_combinations(c) : 0;
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->reserved = 0;
+  if (alg == 1) c->have_alg1 = true;
+  return AJF_OK;
+}
+
 int64_t slice_count(const ajf_ctx* c) {
   int64_t n = 1;
   for (int j : c->slice_noises) n *= c->in.noises[j].nk;
@@ -594,6 +668,7 @@ ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
     if (st != AJF_OK) return st;
   }
   if (alg == 1 && is_sliced(c)) return fidelity_sliced(c, eps, out);
+  if (bond_sliced(c)) return fidelity_bonds(c, alg, eps, out);
   ajf_status st = run_program(c);
   if (st != AJF_OK) return st;
   double res[3];
@@ -769,8 +844,14 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   if (o.trials <= 0) o.trials = 32;
   if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
   if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
+  if (o.slice_bonds < AJF_SLICE_AUTO || o.slice_bonds > AJF_MAX_SLICE_BONDS)
+    return fail(c, AJF_E_ARG, "slice_bonds must be AJF_SLICE_AUTO or between 0 and AJF_MAX_SLICE_BONDS");
+  if (o.slice_bonds != 0 && o.alg1_slices > 0)
+    return fail(c, AJF_E_ARG, "slice_bonds and alg1_slices cannot be combined");
+  if (o.slice_bonds != 0 && o.lowering == AJF_LOWER_PERSISTENT)
+    return fail(c, AJF_E_ARG, "a bond-sliced plan cannot use the persistent lowering");
   if (o.alg1_slices < 0 || o.alg1_slices > static_cast<int>(c->noises.size()))
     return fail(c, AJF_E_ARG, "alg1_slices must be between 0 and the number of noises");
   if (o.alg1_slices > 0 && alg != 1) return fail(c, AJF_E_ARG, "alg1_slices applies to Alg. I only");
@@ -828,17 +909,28 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     for (auto& op : seq.ops) key.insert(key.end(), {op.kind, op.index, op.w[0], op.w[1], op.w[2]});
     key.insert(key.end(), seq.closure.begin(), seq.closure.end());
   }
-  // the lowered program depends on the structure, the precision, the lowering and the device
+  double budget = o.mem_budget_bytes;
+  if (budget <= 0 && c->device < 0) budget = 1e18;
+  if (budget <= 0) {
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
+    budget = 0.6 * static_cast<double>(fr) + (c->own_arena ? static_cast<double>(c->arena_cap) : 0.0);
+  }
+  // the lowered program depends on the structure, the precision, the lowering, the device and
+  // the slicing (under AJF_SLICE_AUTO also the budget it was sized for)
   std::vector<int64_t> pkey = key;
   pkey.push_back(o.lowering);
   pkey.push_back(c->tc_device ? 1 : 0);
+  pkey.push_back(o.slice_bonds);
+  if (o.slice_bonds == AJF_SLICE_AUTO) pkey.push_back(static_cast<int64_t>(budget));
   const bool prog_hit = c->prog_valid && pkey == c->prog_key;
   bool cached = prog_hit;
   if (!prog_hit) {
     drop_graph(c);
     c->prog_valid = false;
     cached = c->path_valid && key == c->plan_key;
-    c->net = (alg == 1) ? build_alg1(c->in, seq, sliced) : build_alg2(c->in, seq);
+    const Network full = (alg == 1) ? build_alg1(c->in, seq, sliced) : build_alg2(c->in, seq);
+    c->net = full;
     PlanParams pp;
     pp.planner = o.planner;
     pp.precision = o.precision;
@@ -872,11 +964,47 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     try {
       if (!cached) {
         c->path_valid = false;
-        c->path = plan_path(c->net, pp);
+        c->path_full = plan_path(full, pp);
         c->plan_key = key;
         c->path_valid = true;
       }
-      if (score_err == cudaSuccess && c->path.width > kMaxBits - 2) {
+      // bond slicing: `count` labels of the full path; under AJF_SLICE_AUTO one more at a time
+      // until the lowered arena fits the budget (starting where the widest tensor is addressable)
+      auto apply_slices = [&](int count) {
+        c->bond_labels = count > 0 ? choose_slice_labels(full, c->path_full, count) : std::vector<int>{};
+        if (c->bond_labels.empty()) {
+          c->net = full;
+          c->path = c->path_full;
+        } else {
+          c->net = slice_network(full, c->bond_labels);
+          c->path = restrict_path(c->net, c->path_full, c->bond_labels, pp);
+        }
+      };
+      bool lowered = false;
+      if (score_err == cudaSuccess) {
+        int count = o.slice_bonds > 0 ? o.slice_bonds : 0;
+        if (o.slice_bonds == AJF_SLICE_AUTO) count = std::max(0, c->path_full.width - (kMaxBits - 2));
+        for (;;) {
+          apply_slices(std::min(count, static_cast<int>(AJF_MAX_SLICE_BONDS)));
+          lowered = c->path.width <= kMaxBits - 2;
+          if (lowered)
+            c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device,
+                            o.lowering == AJF_LOWER_PERSISTENT);
+          if (o.slice_bonds != AJF_SLICE_AUTO) break;
+          if (lowered && static_cast<double>(c->prog.arena_bytes) <= budget) break;
+          if (count >= AJF_MAX_SLICE_BONDS || static_cast<int>(c->bond_labels.size()) < count) break;
+          ++count;
+        }
+      }
+      c->bond_leaves.clear();
+      for (size_t l = 0; l < full.leaf_labels.size(); ++l) {
+        ajf_ctx::BondLeaf bl{static_cast<int>(l), {}};
+        for (size_t p = 0; p < full.leaf_labels[l].size(); ++p)
+          for (size_t j = 0; j < c->bond_labels.size(); ++j)
+            if (full.leaf_labels[l][p] == c->bond_labels[j]) bl.bits.emplace_back(static_cast<int>(p), static_cast<int>(j));
+        if (!bl.bits.empty()) c->bond_leaves.push_back(bl);
+      }
+      if (score_err == cudaSuccess && !lowered) {
         // too wide to address: report the path's cost and width with the budget error
         ajf_plan_info pi{};
         pi.cmacs = c->path.cmacs;
@@ -887,15 +1015,15 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
         pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
         pi.planner_used = c->path.planner;
         pi.arena_bytes = std::ldexp(1.0, c->path.width) * 16.0;
+        pi.n_sliced_bonds = static_cast<int32_t>(c->bond_labels.size());
+        pi.cmacs = std::ldexp(pi.cmacs, pi.n_sliced_bonds);
+        pi.flops = std::ldexp(pi.flops, pi.n_sliced_bonds);
         pi.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         c->info = pi;
         if (info) *info = pi;
         return fail(c, AJF_E_BUDGET, "planned width 2^" + std::to_string(c->path.width) +
                                          " elements is beyond what one device can hold");
       }
-      if (score_err == cudaSuccess)
-        c->prog = lower(c->net, c->path, o.precision, c->in.packed.size() / 2, c->tc_device,
-                        o.lowering == AJF_LOWER_PERSISTENT);
     } catch (const std::exception& ex) {
       return fail(c, AJF_E_BUDGET, std::string("planning failed: ") + ex.what());
     }
@@ -919,11 +1047,13 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     std::memcpy(c->desc_image.data() + (P.off_perms - P.off_desc), P.perms.data(), P.perms.size() * sizeof(PermDev));
   std::memcpy(c->desc_image.data() + (P.off_final - P.off_desc), &P.fin, sizeof(FinalDev));
   ajf_plan_info pi{};
-  pi.cmacs = c->path.cmacs;
-  pi.flops = P.flops;
-  pi.bytes = P.bytes;
-  pi.gemm_flops = P.gemm_flops;
-  pi.gemm_bytes = P.gemm_bytes;
+  const int nb = static_cast<int>(c->bond_labels.size());
+  pi.cmacs = std::ldexp(c->path.cmacs, nb);
+  pi.flops = std::ldexp(P.flops, nb);
+  pi.bytes = std::ldexp(P.bytes, nb);
+  pi.gemm_flops = std::ldexp(P.gemm_flops, nb);
+  pi.gemm_bytes = std::ldexp(P.gemm_bytes, nb);
+  pi.n_sliced_bonds = nb;
   pi.arena_bytes = static_cast<double>(P.arena_bytes);
   pi.plan_seconds = secs;
   pi.width = c->path.width;
@@ -941,17 +1071,11 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   pi.upload_bytes = static_cast<double>(P.desc_bytes + P.input_bytes);
   c->info = pi;
   if (info) *info = pi;
-  double budget = o.mem_budget_bytes;
-  if (budget <= 0 && c->device < 0) budget = 1e18;
-  if (budget <= 0) {
-    size_t fr = 0, tot = 0;
-    CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
-    budget = 0.6 * static_cast<double>(fr) + (c->own_arena ? static_cast<double>(c->arena_cap) : 0.0);
-  }
   if (static_cast<double>(P.arena_bytes) > budget)
     return fail(c, AJF_E_BUDGET, "plan needs " + std::to_string(P.arena_bytes) + " bytes, budget " +
                                      std::to_string(static_cast<size_t>(budget)) + " (width " +
-                                     std::to_string(c->path.width) + ")");
+                                     std::to_string(c->path.width) + ", " + std::to_string(nb) +
+                                     " sliced labels)");
   c->opts = o;
   c->alg = alg;
   c->slice_noises = slice_noises;
@@ -983,14 +1107,14 @@ ajf_status ajf_plan(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   ajf_plan_info i2{};
   ajf_status st = plan_one(c, 2, &o2, &i2);
   const bool have2 = st == AJF_OK;
-  const double t2 = have2 ? c->path.est_seconds : 0.0;
+  const double t2 = have2 ? std::ldexp(c->path.est_seconds, static_cast<int>(c->bond_labels.size())) : 0.0;
   if (st != AJF_OK && st != AJF_E_BUDGET) return st;
   ajf_plan_info i1{};
   const ajf_status st1 = plan_one(c, 1, opts, &i1);
   if (st1 == AJF_OK) {
     double slices = 1;
     for (int j : c->slice_noises) slices *= c->noises[j].nk;
-    if (!have2 || c->path.est_seconds * slices <= t2) {
+    if (!have2 || std::ldexp(c->path.est_seconds, static_cast<int>(c->bond_labels.size())) * slices <= t2) {
       if (info) *info = i1;
       return AJF_OK;
     }
@@ -1106,7 +1230,7 @@ ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out
   if (!c->planned || c->alg != alg) return fail(c, AJF_E_STATE, "no Alg. " + std::to_string(alg) + " plan");
   if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
   if (eps > 1.0) return fail(c, AJF_E_ARG, "eps > 1");
-  if (is_sliced(c)) return fail(c, AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
+  if (multi_run(c)) return fail(c, AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
   const Program& P = c->prog;
   if (P.arena_bytes > kStaticArenaBytes)
     return fail(c, AJF_E_NOMEM, "plan needs " + std::to_string(P.arena_bytes) + " bytes of device memory; the fixed " +
@@ -1161,11 +1285,16 @@ ajf_status ajf_alg1_traces(ajf_ctx* c, double* traces, int64_t count) {
     std::memcpy(traces, c->slice_traces.data(), 2 * static_cast<size_t>(real) * sizeof(double));
     return AJF_OK;
   }
-  CUDA_TRY(c, cudaSetDevice(c->device));
-  std::vector<double> padded(2 * static_cast<size_t>(c->prog.n_traces));
-  CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + c->prog.off_traces, padded.size() * sizeof(double),
-                              cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> padded;
+  if (bond_sliced(c)) {  // summed on the host over the bond slices
+    padded = c->bond_traces;
+  } else {
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    padded.resize(2 * static_cast<size_t>(c->prog.n_traces));
+    CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + c->prog.off_traces, padded.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
   // padded index: noise j's Kraus index shifted by the bits of the noises added after it
   const int m = static_cast<int>(c->in.noises.size());
   std::vector<int> shift(m, 0);
@@ -1192,7 +1321,7 @@ ajf_status ajf_launch(ajf_ctx* c, double* dev_result) {
   if (!c) return AJF_E_ARG;
   if (!c->planned || !c->uploaded || c->device < 0)
     return fail(c, AJF_E_STATE, "ajf_launch needs a plan and uploaded inputs on a device context");
-  if (is_sliced(c)) return fail(c, AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
+  if (multi_run(c)) return fail(c, AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
   CUDA_TRY(c, cudaSetDevice(c->device));
   ajf_status st = run_program(c);
   if (st != AJF_OK) return st;
@@ -1405,7 +1534,7 @@ ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double e
       return fail(ctxs[0], AJF_E_ARG, "contexts must share one device");
     if (!ctxs[i]->planned || ctxs[i]->alg != alg)
       return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
-    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
+    if (multi_run(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
     if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
   }
   // every context runs on its own stream so independent circuits overlap on the GPU
@@ -1443,7 +1572,7 @@ ajf_status ajf_fidelity_alg1_batch(ajf_ctx* const* ctxs, int n_ctx, double eps, 
     if (!ctxs[i]) return AJF_E_ARG;
     if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[0], AJF_E_ARG, "contexts on different devices");
     if (!ctxs[i]->planned || ctxs[i]->alg != 1) return fail(ctxs[i], AJF_E_STATE, "context without an Alg. I plan");
-    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
+    if (multi_run(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
     if (ctxs[i]->opts.precision != ctxs[0]->opts.precision) return fail(ctxs[0], AJF_E_ARG, "mixed precision");
   }
   // every context runs on its own stream so independent circuits overlap on the GPU
@@ -1706,7 +1835,7 @@ ajf_status ajf_fidelity_batch_persistent(ajf_ctx* const* ctxs, int n_ctx, int al
   for (int i = 0; i < n_ctx; ++i) {
     if (!ctxs[i]->planned || ctxs[i]->alg != alg)
       return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
-    if (is_sliced(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
+    if (multi_run(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
     (ctxs[i]->prog.persistent ? pers : rest).push_back(ctxs[i]);
   }
   CUDA_TRY(ctxs[0], cudaSetDevice(ctxs[0]->device));

@@ -65,7 +65,8 @@ struct LeafDev {
   int64_t src;            // complex offset of the source matrix in the input buffer
   int32_t kind, a, nk, kbits;
   int32_t bits;           // total tensor bits
-  int32_t pad;
+  uint16_t fix_mask;      // bond slicing: positions of sliced labels in the full leaf index
+  uint16_t fix_val;       // their values in this slice (bits under fix_mask)
 };
 
 // Final reduction: scalars, open tensor, result.

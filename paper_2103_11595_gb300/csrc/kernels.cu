@@ -96,13 +96,27 @@ __device__ __forceinline__ void leaf_value(const LeafDev& L, const double* __res
   }
 }
 
+// Index into the full (unsliced) leaf of element e of a leaf whose sliced labels are fixed:
+// e's bits fill the free positions from the lowest up, the sliced positions take fix_val.
+__device__ __forceinline__ int64_t leaf_full_index(const LeafDev& L, int64_t e) {
+  if (L.fix_mask == 0) return e;
+  int64_t full = L.fix_val;
+  int src = 0;
+  for (int p = 0; p < 16 && src < L.bits; ++p) {
+    if ((L.fix_mask >> p) & 1) continue;
+    full |= ((e >> src) & 1) << p;
+    ++src;
+  }
+  return full;
+}
+
 template <typename T>
 __global__ void k_leaf(const LeafDev* leaves, const double* __restrict__ in, T* __restrict__ arena) {
   const LeafDev L = leaves[blockIdx.x];
   const int64_t n = int64_t(1) << L.bits;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     double re, im;
-    leaf_value(L, in, e, re, im);
+    leaf_value(L, in, leaf_full_index(L, e), re, im);
     arena[L.off + e] = static_cast<T>(re);
     arena[L.off + L.plane + e] = static_cast<T>(im);
   }
@@ -728,7 +742,7 @@ __global__ void __launch_bounds__(256) k_persistent(const InterpJob* __restrict_
       const int64_t n = int64_t(1) << L.bits;
       for (int64_t e = first_local(base, tid, nt); e < n; e += nt) {
         double re, im;
-        leaf_value(L, in, e, re, im);
+        leaf_value(L, in, leaf_full_index(L, e), re, im);
         W[L.off - w0 + e] = re;
         W[L.off - w0 + L.plane + e] = im;
       }

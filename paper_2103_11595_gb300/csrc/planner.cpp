@@ -129,6 +129,125 @@ void evaluate_path(const Network& net, Path& path, const PlanParams& p) {
   path.est_seconds = secs;
 }
 
+// ------------------------------------------------------------------ bond slicing
+//
+// Slicing a closed label b writes the contraction as the sum of two contractions, one with b
+// fixed to 0 and one with b fixed to 1 in both tensors that carry it: the full contraction is a
+// sum over every label assignment, so fixing some labels and summing over their values is the
+// same sum in another order. s sliced labels give 2^s independent contractions whose tensors are
+// all at most 2^s times smaller.
+
+std::vector<int> choose_slice_labels(const Network& net, const Path& path, int count) {
+  const int L = static_cast<int>(net.leaf_labels.size());
+  std::vector<Labels> ts;
+  for (auto& l : net.leaf_labels) ts.push_back(sorted(l));
+  for (auto& st : path.steps) ts.push_back(sorted(st.out));
+  std::vector<char> open(net.n_labels, 0), cut(net.n_labels, 0);
+  for (int x : net.open_labels) open[x] = 1;
+  // leaves carrying each label, to keep every leaf at one label at least
+  std::vector<std::vector<int>> holders(net.n_labels);
+  for (int i = 0; i < L; ++i)
+    for (int x : ts[i]) holders[x].push_back(i);
+  std::vector<int> left(L);
+  for (int i = 0; i < L; ++i) left[i] = static_cast<int>(ts[i].size());
+  std::vector<int> chosen;
+  for (int round = 0; round < count; ++round) {
+    std::vector<int> rank(ts.size());
+    int w = 0;
+    for (size_t i = 0; i < ts.size(); ++i) {
+      int r = 0;
+      for (int x : ts[i]) r += cut[x] ? 0 : 1;
+      rank[i] = r;
+      w = std::max(w, r);
+    }
+    // score: tensors of the largest rank that carry the label, then the summed size of every
+    // tensor that carries it (the memory and work that halve). When the largest tensors carry
+    // no closed label (an Alg. I result made of open indices), the volume alone decides.
+    std::vector<double> in_widest(net.n_labels, 0), mass(net.n_labels, 0);
+    for (size_t i = 0; i < ts.size(); ++i)
+      for (int x : ts[i]) {
+        if (cut[x]) continue;
+        if (rank[i] == w) in_widest[x] += 1;
+        mass[x] += std::ldexp(1.0, rank[i]);
+      }
+    int best = -1;
+    for (int x = 0; x < net.n_labels; ++x) {
+      if (open[x] || cut[x] || mass[x] == 0) continue;
+      bool keeps = true;
+      for (int h : holders[x]) keeps = keeps && left[h] > 1;
+      if (!keeps) continue;
+      if (best < 0 || in_widest[x] > in_widest[best] || (in_widest[x] == in_widest[best] && mass[x] > mass[best]))
+        best = x;
+    }
+    if (best < 0) break;  // nothing left to slice
+    cut[best] = 1;
+    for (int h : holders[best]) --left[h];
+    chosen.push_back(best);
+  }
+  std::sort(chosen.begin(), chosen.end());
+  return chosen;
+}
+
+Network slice_network(const Network& net, const std::vector<int>& labels) {
+  Network out = net;
+  std::vector<char> cut(net.n_labels, 0);
+  for (int x : labels) cut[x] = 1;
+  for (size_t i = 0; i < out.leaf_labels.size(); ++i) {
+    const std::vector<int>& full = net.leaf_labels[i];
+    std::vector<int> kept;
+    uint32_t mask = 0;
+    for (size_t p = 0; p < full.size(); ++p) {
+      if (cut[full[p]]) mask |= 1u << p;
+      else kept.push_back(full[p]);
+    }
+    out.leaf_labels[i] = kept;
+    out.leaf_specs[i].fix_mask = mask;
+  }
+  return out;
+}
+
+Path restrict_path(const Network& sliced, const Path& path, const std::vector<int>& labels, const PlanParams& p) {
+  std::vector<char> cut;
+  for (int x : labels) {
+    if (x >= static_cast<int>(cut.size())) cut.resize(x + 1, 0);
+    cut[x] = 1;
+  }
+  auto is_cut = [&](int x) { return x < static_cast<int>(cut.size()) && cut[x]; };
+  const int L = static_cast<int>(sliced.leaf_labels.size());
+  // id[old] = new tensor id, or -1 for a scalar that is already among the final tensors
+  std::vector<int> id(L + path.steps.size(), -1);
+  for (int i = 0; i < L; ++i) id[i] = i;
+  Path r;
+  r.planner = path.planner;
+  int next = L;
+  for (size_t s = 0; s < path.steps.size(); ++s) {
+    const PathStep& st = path.steps[s];
+    const int a = id[st.a], b = id[st.b];
+    if (a < 0 || b < 0) {  // merging with a scalar: the scalar stays a final factor
+      id[L + s] = a < 0 ? b : a;
+      continue;
+    }
+    PathStep ns;
+    ns.a = a;
+    ns.b = b;
+    for (int x : st.out)
+      if (!is_cut(x)) ns.out.push_back(x);
+    r.steps.push_back(ns);
+    const int mine = next++;
+    if (ns.out.empty()) {
+      r.final_ids.push_back(mine);
+      id[L + s] = -1;
+    } else {
+      id[L + s] = mine;
+    }
+  }
+  for (int f : path.final_ids)
+    if (id[f] >= 0 && std::find(r.final_ids.begin(), r.final_ids.end(), id[f]) == r.final_ids.end())
+      r.final_ids.push_back(id[f]);
+  evaluate_path(sliced, r, p);
+  return r;
+}
+
 Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature) {
   Rng rng(seed);
   const int L = static_cast<int>(net.leaf_labels.size());

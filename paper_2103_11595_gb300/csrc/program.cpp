@@ -522,6 +522,8 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     d.nk = sp.nk;
     d.kbits = sp.kbits;
     d.bits = static_cast<int32_t>(labels[l].size());
+    d.fix_mask = static_cast<uint16_t>(sp.fix_mask);
+    d.fix_val = 0;
     P.leaves.push_back(d);
   }
   for (auto& d : P.steps) {
