@@ -286,6 +286,23 @@ ajf_status ajf_alg1_checkpoint(const ajf_ctx *ctx, ajf_alg1_state *state);
  * Errors: AJF_E_ARG (NULL, another plan or other values, fields out of range), AJF_E_STATE. */
 ajf_status ajf_alg1_restore(ajf_ctx *ctx, const ajf_alg1_state *state);
 
+/* Independent runs of one evaluation of the current plan: the Kraus-index slices of a sliced
+ * Alg. I plan (opts.alg1_slices), 2^n_sliced_bonds for a bond-sliced plan (opts.slice_bonds),
+ * otherwise 1. These are the units for sharding one evaluation across devices or processes.
+ * Errors: AJF_E_ARG (NULL), AJF_E_STATE (no plan). */
+ajf_status ajf_slice_count(const ajf_ctx *ctx, int64_t *n);
+
+/* Sharding one Alg. II evaluation (the paper has no counterpart; Sec. IV-B contracts the doubled
+ * network whole). Runs the bond slices [first, first + count) of the context's Alg. II plan
+ * (a plan without bond slicing has the one slice 0) and writes the sum of their scalars to
+ * *S_part, in FP64. The slices partition the contraction's sum over label values, so S_part over
+ * ranges that partition [0, ajf_slice_count) adds up to S, and F_J = S / 4^n: one FP64
+ * all-reduce of S_part across devices or processes completes the evaluation. count = 0 gives
+ * S_part = 0 without running anything. Synchronises the context's stream.
+ * Errors: AJF_E_ARG (NULL, range outside [0, ajf_slice_count)), AJF_E_STATE (no Alg. II plan,
+ * host-only context), AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT. */
+ajf_status ajf_alg2_slice_range(ajf_ctx *ctx, int64_t first, int64_t count, double *S_part);
+
 /* Alg. II (Sec. IV-B): F_J from the one doubled network. Same contract as ajf_fidelity_alg1,
  * requiring ajf_plan(ctx, 2, ...). */
 ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);

@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
             "ajf_alg1_restore": (I32, [P, ctypes.POINTER(Alg1State)]),
             "ajf_autotune_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32)]),
             "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
+            "ajf_slice_count": (I32, [P, ctypes.POINTER(I64)]),
+            "ajf_alg2_slice_range": (I32, [P, I64, I64, ctypes.POINTER(D)]),
             "ajf_alg1_traces": (I32, [P, P, I64]),
             "ajf_launch": (I32, [P, P]),
             "ajf_upload": (I32, [P]),
@@ -270,6 +272,19 @@ def ajf_planned_alg(ctx) -> int:
     a = ctypes.c_int()
     _check(ctx, lib().ajf_planned_alg(ctx, ctypes.byref(a)))
     return int(a.value)
+
+
+def ajf_slice_count(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, lib().ajf_slice_count(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def ajf_alg2_slice_range(ctx, first: int, count: int) -> float:
+    """Sum of the scalars of bond slices [first, first + count) of an Alg. II plan (FP64)."""
+    s = ctypes.c_double()
+    _check(ctx, lib().ajf_alg2_slice_range(ctx, int(first), int(count), ctypes.byref(s)))
+    return float(s.value)
 
 
 def ajf_fidelity_alg2(ctx, eps: float = -1.0) -> dict:

@@ -578,33 +578,27 @@ ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) { return run
 // carry them taking the assignment's bits (fix_val; only the leaf descriptors change between
 // runs, which also holds under CUDA-graph replay). Alg. II adds the runs' real scalars, Alg. I
 // the runs' complex traces before |t|^2 is formed: both are linear in the runs, F is not.
-// Sums are FP64 in run order (Neumaier-compensated for S).
-ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+// run_bonds runs assignments [first, first + count) (a plan without bond slicing has the one
+// assignment 0): Alg. II returns the Neumaier-compensated FP64 sum of the runs' scalars in
+// *S_out, Alg. I adds the runs' traces to bond_traces (padded order) in run order.
+ajf_status run_bonds(ajf_ctx* c, int alg, int64_t first, int64_t count, double* S_out) {
   const Program& P = c->prog;
-  const int nb = static_cast<int>(c->bond_labels.size());
   const size_t leaves_at = P.off_leaves - P.off_desc;
-  const int64_t runs = int64_t(1) << nb;
   std::vector<double> padded;
-  if (alg == 1) {
-    padded.assign(2 * static_cast<size_t>(P.n_traces), 0.0);
-    c->bond_traces.assign(padded.size(), 0.0);
-  }
+  if (alg == 1) padded.assign(2 * static_cast<size_t>(P.n_traces), 0.0);
   double S = 0, comp = 0;
-  auto add = [&](double x) {  // Neumaier summation
-    const double t = S + x;
-    comp += std::fabs(S) >= std::fabs(x) ? (S - t) + x : (x - t) + S;
-    S = t;
-  };
-  for (int64_t v = 0; v < runs; ++v) {
-    for (auto& bl : c->bond_leaves) {
-      uint16_t val = 0;
-      for (auto& pb : bl.bits)
-        if ((v >> pb.second) & 1) val = static_cast<uint16_t>(val | (1u << pb.first));
-      std::memcpy(c->desc_image.data() + leaves_at + bl.leaf * sizeof(LeafDev) + offsetof(LeafDev, fix_val), &val,
-                  sizeof(val));
+  for (int64_t v = first; v < first + count; ++v) {
+    if (!c->bond_leaves.empty()) {
+      for (auto& bl : c->bond_leaves) {
+        uint16_t val = 0;
+        for (auto& pb : bl.bits)
+          if ((v >> pb.second) & 1) val = static_cast<uint16_t>(val | (1u << pb.first));
+        std::memcpy(c->desc_image.data() + leaves_at + bl.leaf * sizeof(LeafDev) + offsetof(LeafDev, fix_val), &val,
+                    sizeof(val));
+      }
+      CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, c->desc_image.data() + leaves_at,
+                                  P.leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, c->stream));
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, c->desc_image.data() + leaves_at,
-                                P.leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, c->stream));
     ajf_status st = run_program(c);
     if (st != AJF_OK) return st;
     double res[3];
@@ -615,14 +609,35 @@ ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     st = check_status_words(c);
     if (st != AJF_OK) return st;
-    if (alg == 2) add(res[0]);
-    else
+    if (alg == 2) {  // Neumaier summation
+      const double t = S + res[0];
+      comp += std::fabs(S) >= std::fabs(res[0]) ? (S - t) + res[0] : (res[0] - t) + S;
+      S = t;
+    } else {
       for (size_t i = 0; i < padded.size(); ++i) c->bond_traces[i] += padded[i];
+    }
   }
-  if (alg == 1)
-    for (size_t i = 0; i < c->bond_traces.size(); i += 2)
-      add(c->bond_traces[i] * c->bond_traces[i] + c->bond_traces[i + 1] * c->bond_traces[i + 1]);
-  S += comp;
+  if (S_out) *S_out = S + comp;
+  return AJF_OK;
+}
+
+ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  const int nb = static_cast<int>(c->bond_labels.size());
+  if (alg == 1) c->bond_traces.assign(2 * static_cast<size_t>(c->prog.n_traces), 0.0);
+  double S = 0;
+  ajf_status st = run_bonds(c, alg, 0, int64_t(1) << nb, &S);
+  if (st != AJF_OK) return st;
+  if (alg == 1) {
+    double comp = 0;
+    S = 0;
+    for (size_t i = 0; i < c->bond_traces.size(); i += 2) {
+      const double x = c->bond_traces[i] * c->bond_traces[i] + c->bond_traces[i + 1] * c->bond_traces[i + 1];
+      const double t = S + x;
+      comp += S >= x ? (S - t) + x : (x - t) + S;
+      S = t;
+    }
+    S += comp;
+  }
   const int nsq = 2 * c->n;
   out->S = S;
   out->F = std::ldexp(S, -nsq);
@@ -1215,6 +1230,31 @@ ajf_status ajf_alg1_restore(ajf_ctx* c, const ajf_alg1_state* st) {
   c->slice_traces_valid = st->next_slice == 0;  // the traces of earlier slices are not in a checkpoint
   c->have_alg1 = false;
   return AJF_OK;
+}
+
+ajf_status ajf_slice_count(const ajf_ctx* c, int64_t* n) {
+  if (!c || !n) return AJF_E_ARG;
+  if (!c->planned) return AJF_E_STATE;
+  *n = is_sliced(c) ? slice_count(c) : (int64_t(1) << c->bond_labels.size());
+  return AJF_OK;
+}
+
+ajf_status ajf_alg2_slice_range(ajf_ctx* c, int64_t first, int64_t count, double* S_part) {
+  if (!c) return AJF_E_ARG;
+  if (!S_part) return fail(c, AJF_E_ARG, "S_part is NULL");
+  if (!c->planned || c->alg != 2) return fail(c, AJF_E_STATE, "needs an Alg. II plan");
+  if (c->device < 0) return fail(c, AJF_E_STATE, "host-only context (device -1) cannot run the contraction");
+  const int64_t n = int64_t(1) << c->bond_labels.size();
+  if (first < 0 || count < 0 || first > n || count > n - first)
+    return fail(c, AJF_E_ARG, "slice range outside [0, " + std::to_string(n) + ")");
+  *S_part = 0;
+  if (count == 0) return AJF_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (!c->uploaded) {
+    ajf_status st = do_upload(c);
+    if (st != AJF_OK) return st;
+  }
+  return run_bonds(c, 2, first, count, S_part);
 }
 
 ajf_status ajf_fidelity(ajf_ctx* c, double eps, ajf_result* out) {
