@@ -286,6 +286,31 @@ ajf_status ajf_alg1_checkpoint(const ajf_ctx *ctx, ajf_alg1_state *state);
  * Errors: AJF_E_ARG (NULL, another plan or other values, fields out of range), AJF_E_STATE. */
 ajf_status ajf_alg1_restore(ajf_ctx *ctx, const ajf_alg1_state *state);
 
+/* Host-side replay of the current plan's device program (no device needed; the paper has no
+ * counterpart). It stands in for a device memory checker, which this library cannot rely on.
+ * Every address a kernel of the program can form is a base plus distinct powers of two taken
+ * from the step's index maps: leaves, pairwise steps, operand gathers, GEMM operands, results,
+ * K-split workspaces, partial sums, scalar slots and the final pass. The check makes sure that
+ * each such address lies inside its buffer and the arena region that holds it. Replaying the
+ * launches in stream order, it also makes sure that:
+ *   - every buffer read was written by an earlier launch;
+ *   - no launch writes over a buffer that it, or a later launch, still reads;
+ *   - no two writes of one launch overlap.
+ * Errors: AJF_E_ARG (NULL), AJF_E_STATE (no plan, or a violation: the first is in
+ * ajf_last_error). */
+ajf_status ajf_check_plan(ajf_ctx *ctx);
+
+/* Self-test of ajf_check_plan (tests only; no paper counterpart): plant one mistake in a copy of
+ * the current plan's program and check it. mutation 1: a leaf past the end of the work region;
+ * 2: an index-map position beyond its operand's bits; 3: a step writing over its own input;
+ * 4: a step reading memory that no launch wrote; 5: two leaves in the same place; 6: a step of
+ * the first launch writing over a leaf that a later launch still reads (3, 5 and 6 move their
+ * buffer's readers along, so that only the overlap is wrong). The context's
+ * own program is not changed. Returns AJF_OK when the check reports the mistake (its message is
+ * in ajf_last_error), AJF_E_STATE when it does not, AJF_E_ARG for an unknown mutation or a plan
+ * without the needed step. */
+ajf_status ajf_selftest_check_plan(ajf_ctx *ctx, int mutation);
+
 /* Independent runs of one evaluation of the current plan: the Kraus-index slices of a sliced
  * Alg. I plan (opts.alg1_slices), 2^n_sliced_bonds for a bond-sliced plan (opts.slice_bonds),
  * otherwise 1. These are the units for sharding one evaluation across devices or processes.

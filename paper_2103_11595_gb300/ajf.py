@@ -117,6 +117,8 @@ def lib() -> ctypes.CDLL:
             "ajf_autotune_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32)]),
             "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
             "ajf_slice_count": (I32, [P, ctypes.POINTER(I64)]),
+            "ajf_check_plan": (I32, [P]),
+            "ajf_selftest_check_plan": (I32, [P, ctypes.c_int]),
             "ajf_alg2_slice_range": (I32, [P, I64, I64, ctypes.POINTER(D)]),
             "ajf_alg1_traces": (I32, [P, P, I64]),
             "ajf_launch": (I32, [P, P]),
@@ -272,6 +274,17 @@ def ajf_planned_alg(ctx) -> int:
     a = ctypes.c_int()
     _check(ctx, lib().ajf_planned_alg(ctx, ctypes.byref(a)))
     return int(a.value)
+
+
+def ajf_check_plan(ctx) -> None:
+    """Host-side replay of the plan's address arithmetic and buffer lifetimes; raises on a violation."""
+    _check(ctx, lib().ajf_check_plan(ctx))
+
+
+def ajf_selftest_check_plan(ctx, mutation: int) -> str:
+    """Plant mistake `mutation` in a copy of the plan; returns the check's report (raises if missed)."""
+    _check(ctx, lib().ajf_selftest_check_plan(ctx, int(mutation)))
+    return ajf_last_error(ctx)
 
 
 def ajf_slice_count(ctx) -> int:

@@ -1,6 +1,7 @@
 // C ABI of libajf (see include/ajf.h): context, input validation, planning, upload and the
 // executor that enqueues a lowered program on the context's stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstddef>
@@ -23,6 +24,16 @@
 using namespace ajf;
 
 namespace {
+
+// NVTX range for profilers (Nsight Systems / Compute): header-only NVTX3, inert when no tool is
+// attached. Ranges: plan, upload, program run (graph replay or enqueue), result read-back,
+// sliced evaluations and batches.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 struct GateData {
   int arity;
@@ -391,6 +402,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
 }
 
 ajf_status run_program(ajf_ctx* c) {
+  Range nvtx_range("ajf run program");
   if (c->opts.use_graph && !c->profiling) {
     if (!c->graph) {
       cudaGraph_t g = nullptr;
@@ -413,6 +425,7 @@ ajf_status run_program(ajf_ctx* c) {
 }
 
 ajf_status do_upload(ajf_ctx* c) {
+  Range nvtx_range("ajf upload");
   if (!c->planned) return fail(c, AJF_E_STATE, "ajf_upload: no plan");
   ajf_status st = ensure_arena(c);
   if (st != AJF_OK) return st;
@@ -461,6 +474,7 @@ bool multi_run(const ajf_ctx* c) { return is_sliced(c) || bond_sliced(c); }
 // Runs up to max_slices (<= 0: all) further slices from the context's progress (reset: from the
 // first); stops early once the partial F exceeds 1 - eps (eps >= 0).
 ajf_status run_slices(ajf_ctx* c, double eps, int64_t max_slices, bool reset, ajf_result* out) {
+  Range nvtx_range("ajf Alg. I Kraus slices");
   const Program& P = c->prog;
   const auto& nz = c->in.noises;
   const int m = static_cast<int>(nz.size());
@@ -622,6 +636,7 @@ ajf_status run_bonds(ajf_ctx* c, int alg, int64_t first, int64_t count, double* 
 }
 
 ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  Range nvtx_range("ajf bond slices");
   const int nb = static_cast<int>(c->bond_labels.size());
   if (alg == 1) c->bond_traces.assign(2 * static_cast<size_t>(c->prog.n_traces), 0.0);
   double S = 0;
@@ -672,6 +687,7 @@ uint64_t slice_signature(const ajf_ctx* c) {
 }
 
 ajf_status fidelity(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  Range nvtx_range("ajf fidelity");
   if (!c) return AJF_E_ARG;
   if (!out) return fail(c, AJF_E_ARG, "out is NULL");
   if (!c->planned || c->alg != alg) return fail(c, AJF_E_STATE, "no Alg. " + std::to_string(alg) + " plan");
@@ -848,6 +864,7 @@ ajf_status ajf_clear_noise(ajf_ctx* c) {
 namespace {
 
 ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_info* info) {
+  Range nvtx_range("ajf plan");
   if (!c) return AJF_E_ARG;
   if (!c->has_ideal) return fail(c, AJF_E_STATE, "ajf_plan before ajf_load_circuit");
   if (alg != 1 && alg != 2) return fail(c, AJF_E_ARG, "alg must be 0, 1 or 2");
@@ -1232,6 +1249,118 @@ ajf_status ajf_alg1_restore(ajf_ctx* c, const ajf_alg1_state* st) {
   return AJF_OK;
 }
 
+ajf_status ajf_check_plan(ajf_ctx* c) {
+  if (!c) return AJF_E_ARG;
+  if (!c->planned) return fail(c, AJF_E_STATE, "no plan");
+  const std::string why = check_program(c->prog);
+  if (!why.empty()) return fail(c, AJF_E_STATE, "plan check: " + why);
+  c->err.clear();
+  return AJF_OK;
+}
+
+ajf_status ajf_selftest_check_plan(ajf_ctx* c, int mutation) {
+  if (!c) return AJF_E_ARG;
+  if (!c->planned) return fail(c, AJF_E_STATE, "no plan");
+  Program P = c->prog;  // a copy: the context's program is not touched
+  auto first_step = [&](auto pred) -> StepDev* {
+    for (auto& ln : P.launches)
+      if (ln.kind == LK_SMALL || ln.kind == LK_SPLITK || ln.kind == LK_DOT)
+        for (int k = ln.first; k < ln.first + ln.count; ++k)
+          if (pred(P.steps[k])) return &P.steps[k];
+    return nullptr;
+  };
+  // Point the reads of the tensor at element offset `from` (plane `plane`, written before launch
+  // `first`) to `to`: launches from `first` on, until one writes over its old place.
+  auto redirect = [&](int64_t from, int64_t plane, size_t first, int64_t to) {
+    const int64_t lo = from, hi = from + 2 * plane;
+    auto hits = [&](int64_t o, int64_t p) { return o < hi && lo < o + 2 * p; };
+    for (size_t li = first; li < P.launches.size(); ++li) {
+      const Launch& ln = P.launches[li];
+      bool overwritten = false;
+      if (ln.kind == LK_SMALL || ln.kind == LK_SPLITK || ln.kind == LK_DOT) {
+        for (int k = ln.first; k < ln.first + ln.count; ++k) {
+          StepDev& d = P.steps[k];
+          if (d.a == from && d.pa == plane) d.a = to;
+          if (d.b == from && d.pb == plane) d.b = to;
+        }
+        for (int k = ln.first; k < ln.first + ln.count; ++k)
+          overwritten = overwritten || (P.steps[k].scalar_slot < 0 && hits(P.steps[k].c, P.steps[k].pc));
+      } else if (ln.kind == LK_PERM) {
+        for (int k = ln.first; k < ln.first + ln.count; ++k)
+          if (P.perms[k].src == from && P.perms[k].plane == plane) P.perms[k].src = to;
+      } else {
+        const int64_t c0 = ln.c_off / static_cast<int64_t>(P.elem);
+        overwritten = hits(c0, ln.M * ln.N / 2);
+      }
+      if (overwritten) return;
+    }
+    if (P.fin.open_off == from && P.fin.open_plane == plane) P.fin.open_off = to;
+  };
+  switch (mutation) {
+    case 1:  // a leaf placed past the end of the work region
+      if (P.leaves.empty()) return fail(c, AJF_E_ARG, "no leaves");
+      P.leaves[0].off = static_cast<int64_t>((P.off_work + P.work_bytes) / P.elem);
+      break;
+    case 2: {  // an index-map position beyond the operand's bits
+      StepDev* d = first_step([](const StepDev& x) { return x.rk > 0; });
+      if (!d) return fail(c, AJF_E_ARG, "no step with a contracted index");
+      int bits = 0;
+      while ((int64_t(1) << bits) < d->pa) ++bits;
+      d->ka.pos[0] = static_cast<int8_t>(bits);
+      break;
+    }
+    case 3: {  // a step writing over its own input (its readers follow it)
+      StepDev* d = first_step([](const StepDev& x) { return x.scalar_slot < 0 && x.pc <= x.pa; });
+      if (!d) return fail(c, AJF_E_ARG, "no step with a tensor output");
+      const size_t li = static_cast<size_t>(std::find_if(P.launches.begin(), P.launches.end(), [&](const Launch& l) {
+                          return (l.kind == LK_SMALL || l.kind == LK_SPLITK || l.kind == LK_DOT) && l.first <= d - P.steps.data() &&
+                                 d - P.steps.data() < l.first + l.count;
+                        }) - P.launches.begin());
+      redirect(d->c, d->pc, li + 1, d->a);
+      d->c = d->a;
+      break;
+    }
+    case 4: {  // a read of memory no launch wrote (the operand shifted by one element)
+      StepDev* d = first_step([](const StepDev&) { return true; });
+      if (!d) return fail(c, AJF_E_ARG, "no pairwise step");
+      d->a += 1;
+      break;
+    }
+    case 5: {  // two leaves of one size in the same place (the second one's readers follow it)
+      for (size_t j = 1; j < P.leaves.size(); ++j)
+        if (P.leaves[j].bits == P.leaves[0].bits) {
+          redirect(P.leaves[j].off, P.leaves[j].plane, 0, P.leaves[0].off);
+          P.leaves[j].off = P.leaves[0].off;
+          break;
+        }
+      break;
+    }
+    case 6: {  // a step of the first launch writing over a leaf that a later launch still reads
+      const Launch& l0 = P.launches.empty() ? Launch{} : P.launches[0];
+      if (P.launches.empty() || l0.kind != LK_SMALL) return fail(c, AJF_E_ARG, "first launch is not a small-step launch");
+      std::vector<char> early(P.leaves.size(), 0);  // leaves the first launch reads
+      for (int k = l0.first; k < l0.first + l0.count; ++k)
+        for (size_t l = 0; l < P.leaves.size(); ++l)
+          if (P.steps[k].a == P.leaves[l].off || P.steps[k].b == P.leaves[l].off) early[l] = 1;
+      StepDev* d = nullptr;
+      for (int k = l0.first; k < l0.first + l0.count && !d; ++k)
+        if (P.steps[k].scalar_slot < 0) d = &P.steps[k];
+      size_t x = 0;  // a leaf the first launch does not read, of another size than d's output
+      while (x < P.leaves.size() && d && (early[x] || P.leaves[x].plane == d->pc)) ++x;
+      if (!d || x == P.leaves.size()) return fail(c, AJF_E_ARG, "no step / late leaf to use");
+      redirect(d->c, d->pc, 1, P.leaves[x].off);
+      d->c = P.leaves[x].off;
+      break;
+    }
+    default:
+      return fail(c, AJF_E_ARG, "unknown mutation");
+  }
+  const std::string why = check_program(P);
+  if (why.empty()) return fail(c, AJF_E_STATE, "planted mistake " + std::to_string(mutation) + " was not caught");
+  c->err = "caught: " + why;
+  return AJF_OK;
+}
+
 ajf_status ajf_slice_count(const ajf_ctx* c, int64_t* n) {
   if (!c || !n) return AJF_E_ARG;
   if (!c->planned) return AJF_E_STATE;
@@ -1567,6 +1696,7 @@ ajf_status ajf_profile_read(ajf_ctx* c, ajf_kernel_stats* stats, int cap) {
 }
 
 ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out) {
+  Range nvtx_range("ajf batch");
   if (!ctxs || n_ctx < 1 || !out || (alg != 1 && alg != 2)) return AJF_E_ARG;
   for (int i = 0; i < n_ctx; ++i) {
     if (!ctxs[i]) return AJF_E_ARG;
@@ -1804,6 +1934,7 @@ ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_r
 extern "C" {
 
 ajf_status ajf_launch_persistent(ajf_ctx* const* ctxs, int n_ctx, double* dev_results) {
+  Range nvtx_range("ajf persistent launch");
   ajf_status st = check_batch(ctxs, n_ctx);
   if (st != AJF_OK) return st;
   for (int i = 0; i < n_ctx; ++i)

@@ -549,3 +549,249 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
 }
 
 }  // namespace ajf
+
+// ------------------------------------------------------------------ host-side replay check
+//
+// Every address a kernel of the program can form is a base offset plus a sum of distinct powers
+// of two taken from a BitMap, so the largest one is known without running anything. The check
+// replays the launches in stream order and tracks, for every buffer written, the last launch that
+// reads it, which is what a device memory checker would catch at run time: accesses outside a
+// buffer or the arena region it belongs to, buffers that no earlier launch wrote, and launches
+// that overwrite a buffer still to be read (or race with their own reads and writes).
+
+namespace ajf {
+namespace {
+
+struct Span {
+  size_t lo = 0, hi = 0;  // bytes [lo, hi) of the arena
+  bool operator==(const Span& o) const { return lo == o.lo && hi == o.hi; }
+};
+bool overlaps(const Span& x, const Span& y) { return x.lo < y.hi && y.lo < x.hi; }
+std::string span_str(const Span& s) { return "[" + std::to_string(s.lo) + ", " + std::to_string(s.hi) + ")"; }
+
+// Add the positions of `m` (those >= 0) to `used`; false if one repeats or is >= limit_bits.
+bool add_positions(const BitMap& m, int limit_bits, uint64_t& used) {
+  if (m.nbits < 0 || m.nbits > kMaxBits) return false;
+  for (int i = 0; i < m.nbits; ++i) {
+    const int p = m.pos[i];
+    if (p < 0) continue;
+    if (p >= limit_bits || ((used >> p) & 1)) return false;
+    used |= uint64_t(1) << p;
+  }
+  return true;
+}
+
+int log2_exact(int64_t x) {
+  if (x <= 0 || (x & (x - 1))) return -1;
+  int b = 0;
+  while ((int64_t(1) << b) < x) ++b;
+  return b;
+}
+
+}  // namespace
+
+std::string check_program(const Program& P) {
+  const size_t work_lo = P.off_work, work_hi = P.off_work + P.work_bytes;
+  if (P.arena_bytes != work_hi) return "arena size differs from the end of its work region";
+  const int64_t inputs_complex = static_cast<int64_t>(P.input_bytes / 16);
+  auto tensor = [&](int64_t off_el, int64_t plane) {
+    return Span{static_cast<size_t>(off_el) * P.elem, static_cast<size_t>(off_el + 2 * plane) * P.elem};
+  };
+  auto in_work = [&](const Span& s) { return s.lo >= work_lo && s.hi <= work_hi && s.lo < s.hi; };
+
+  // launch units: 0 = leaves, 1.. = P.launches, last = the final FP64 pass
+  struct Write {
+    Span s;
+    int unit;
+    int last_read;
+  };
+  std::vector<Write> writes;
+  std::vector<std::vector<Span>> unit_reads(P.launches.size() + 2), unit_writes(P.launches.size() + 2);
+
+  // ---- leaves
+  for (size_t l = 0; l < P.leaves.size(); ++l) {
+    const LeafDev& L = P.leaves[l];
+    const std::string who = "leaf " + std::to_string(l);
+    if (L.bits < 0 || L.plane != (int64_t(1) << L.bits)) return who + ": plane is not 2^bits";
+    const int full_bits = L.bits + __builtin_popcount(L.fix_mask);
+    const int op_bits = L.kind == LEAF_KRAUS_OPEN ? 2 * L.a + L.kbits : (L.kind == LEAF_IDENTITY ? 2 : 2 * L.a);
+    if (full_bits != op_bits || full_bits > 16 || (L.fix_val & ~L.fix_mask)) return who + ": sliced bits do not fit";
+    int64_t need = 0;  // complex input entries read
+    const int64_t dim = int64_t(1) << L.a;
+    switch (L.kind) {
+      case LEAF_GATE: case LEAF_GATE_CONJ: case LEAF_GATE_DAG: case LEAF_GATE_TRANS: need = dim * dim; break;
+      case LEAF_KRAUS_OPEN: need = int64_t(L.nk) * dim * dim; break;
+      case LEAF_SUPEROP: {
+        const int64_t nd = int64_t(1) << (L.a / 2);
+        need = int64_t(L.nk) * nd * nd;
+        break;
+      }
+      default: need = 0;
+    }
+    if (L.src < 0 || L.src + need > inputs_complex) return who + ": reads past the packed inputs";
+    const Span s = tensor(L.off, L.plane);
+    if (!in_work(s)) return who + ": " + span_str(s) + " is outside the work region";
+    unit_writes[0].push_back(s);
+  }
+
+  // ---- steps, gathers and GEMMs
+  std::vector<char> slot_used(static_cast<size_t>(std::max(1, P.n_scalars)), 0);
+  std::vector<Span> partial_spans;
+  for (size_t li = 0; li < P.launches.size(); ++li) {
+    const Launch& ln = P.launches[li];
+    const int u = static_cast<int>(li) + 1;
+    const std::string who = "launch " + std::to_string(li);
+    auto& R = unit_reads[u];
+    auto& W = unit_writes[u];
+    if (ln.kind == LK_SMALL || ln.kind == LK_SPLITK || ln.kind == LK_DOT) {
+      if (ln.first < 0 || ln.count < 0 || ln.first + ln.count > static_cast<int>(P.steps.size()))
+        return who + ": step range";
+      for (int k = ln.first; k < ln.first + ln.count; ++k) {
+        const StepDev& d = P.steps[k];
+        const std::string ws = who + " step " + std::to_string(k);
+        const int ba = log2_exact(d.pa), bb = log2_exact(d.pb);
+        if (ba < 0 || bb < 0) return ws + ": operand planes are not powers of two";
+        if (d.oa.nbits != d.rc || d.ob.nbits != d.rc || d.ka.nbits != d.rk || d.kb.nbits != d.rk)
+          return ws + ": map sizes differ from the step's ranks";
+        uint64_t ua = 0, ub = 0;
+        if (!add_positions(d.oa, ba, ua) || !add_positions(d.ka, ba, ua)) return ws + ": A addresses repeat or overflow";
+        if (!add_positions(d.ob, bb, ub) || !add_positions(d.kb, bb, ub)) return ws + ": B addresses repeat or overflow";
+        const Span sa = tensor(d.a, d.pa), sb = tensor(d.b, d.pb);
+        if (!in_work(sa) || !in_work(sb)) return ws + ": an operand lies outside the work region";
+        R.push_back(sa);
+        R.push_back(sb);
+        if (d.scalar_slot >= 0) {
+          if (d.scalar_slot >= P.n_scalars || slot_used[d.scalar_slot]) return ws + ": scalar slot reused or out of range";
+          slot_used[d.scalar_slot] = 1;
+          if (d.rc != 0) return ws + ": a scalar step has output bits";
+        } else {
+          if (d.pc != (int64_t(1) << d.rc)) return ws + ": output plane is not 2^rc";
+          const Span sc = tensor(d.c, d.pc);
+          if (!in_work(sc)) return ws + ": output " + span_str(sc) + " lies outside the work region";
+          W.push_back(sc);
+        }
+        if (ln.kind == LK_DOT) {
+          if (d.ntl < 0 || d.ntl > 10 || d.ntl > d.rk) return ws + ": dot tile bits";
+          uint32_t ta = 0, tb = 0;
+          for (int q = 0; q < d.ntl; ++q) {
+            if (d.tl[q] < 0 || d.tl[q] >= d.rk || d.tlb[q] < 0 || d.tlb[q] >= d.rk) return ws + ": dot tile bit range";
+            ta |= 1u << d.tl[q];
+            tb |= 1u << d.tlb[q];
+          }
+          if (__builtin_popcount(ta) != d.ntl || ta != tb) return ws + ": dot tile bits repeat";
+        }
+        if (ln.kind == LK_SPLITK || ln.kind == LK_DOT) {
+          const int64_t n = (ln.kind == LK_DOT ? 1 : (int64_t(1) << d.rc)) * d.nsplit;
+          if (d.nsplit < 1 || d.poff < 0 || d.poff + n > static_cast<int64_t>(P.partial_count))
+            return ws + ": partial sums past their region";
+          const Span sp{static_cast<size_t>(d.poff), static_cast<size_t>(d.poff + n)};
+          for (auto& o : partial_spans)
+            if (overlaps(o, sp)) return ws + ": partial sums shared with another step";
+          partial_spans.push_back(sp);
+        }
+      }
+    } else if (ln.kind == LK_PERM) {
+      if (ln.count != 2 || ln.first < 0 || ln.first + 2 > static_cast<int>(P.perms.size())) return who + ": gather range";
+      for (int k = ln.first; k < ln.first + 2; ++k) {
+        const PermDev& g = P.perms[k];
+        const std::string ws = who + " gather " + std::to_string(k);
+        const int bp = log2_exact(g.plane);
+        if (bp < 0 || g.rows.nbits != g.rbits || g.cols.nbits != g.kbits) return ws + ": map sizes";
+        uint64_t used = 0;
+        if (!add_positions(g.rows, bp, used) || !add_positions(g.cols, bp, used))
+          return ws + ": source addresses repeat or overflow";
+        const Span src = tensor(g.src, g.plane);
+        if (!in_work(src)) return ws + ": source outside the work region";
+        R.push_back(src);
+        const size_t rows = size_t(1) << (g.rbits + (g.embed ? 1 : 0)), cols = size_t(1) << (g.kbits + 1);
+        const size_t bytes = rows * cols * mode_bytes(g.mode);
+        for (int t = 0; t < mode_terms(g.mode); ++t) {
+          const Span d{static_cast<size_t>(g.dst[t]), static_cast<size_t>(g.dst[t]) + bytes};
+          if (!in_work(d)) return ws + ": operand term " + std::to_string(t) + " outside the work region";
+          W.push_back(d);
+        }
+      }
+    } else if (ln.kind == LK_GEMM_TC || ln.kind == LK_GEMM_SIMT) {
+      if (li == 0 || P.launches[li - 1].kind != LK_PERM) return who + ": GEMM without its gather";
+      const Launch& lp = P.launches[li - 1];
+      const PermDev& px = P.perms[lp.first];
+      const size_t eb = mode_bytes(px.mode);
+      const int terms = ln.kind == LK_GEMM_TC ? ln.npass : 1;
+      if (terms < 1 || terms > 3 || terms != mode_terms(px.mode)) return who + ": operand terms";
+      if (log2_exact(ln.M) < 0 || log2_exact(ln.N) < 0 || log2_exact(ln.K) < 0) return who + ": GEMM shape";
+      for (int t = 0; t < terms; ++t) {
+        const Span a{static_cast<size_t>(ln.a_off[t]), static_cast<size_t>(ln.a_off[t]) + size_t(ln.M) * size_t(ln.K) * eb};
+        const Span b{static_cast<size_t>(ln.b_off[t]), static_cast<size_t>(ln.b_off[t]) + size_t(ln.N) * size_t(ln.K) * eb};
+        if (!in_work(a) || !in_work(b)) return who + ": operand outside the work region";
+        R.push_back(a);
+        R.push_back(b);
+      }
+      const Span c{static_cast<size_t>(ln.c_off), static_cast<size_t>(ln.c_off) + size_t(ln.M) * size_t(ln.N) * 8};
+      if (!in_work(c)) return who + ": result outside the work region";
+      W.push_back(c);
+      if (ln.ksplit > 1) {
+        const Span w{static_cast<size_t>(ln.ws_off),
+                     static_cast<size_t>(ln.ws_off) + size_t(ln.ksplit) * size_t(ln.M) * size_t(ln.N) * 8};
+        if (!in_work(w)) return who + ": K-split workspace outside the work region";
+        W.push_back(w);  // written by the GEMM and read back by the split sum of the same launch
+      }
+    } else {
+      return who + ": unknown launch kind";
+    }
+  }
+
+  // ---- final pass
+  const int uf = static_cast<int>(P.launches.size()) + 1;
+  const FinalDev& f = P.fin;
+  if (f.n_scalars != P.n_scalars) return "final pass: scalar count";
+  for (int i = 0; i < P.n_scalars; ++i)
+    if (!slot_used[i]) return "final pass: scalar slot " + std::to_string(i) + " is never written";
+  if (f.open_off >= 0) {
+    const int bo = log2_exact(f.open_plane);
+    uint64_t used = 0;
+    if (bo < 0 || f.open_map.nbits != f.open_bits || bo != f.open_bits || !add_positions(f.open_map, bo, used))
+      return "final pass: open-tensor addresses";
+    const Span so = tensor(f.open_off, f.open_plane);
+    if (!in_work(so)) return "final pass: open tensor outside the work region";
+    unit_reads[uf].push_back(so);
+  } else if (f.open_bits != 0) {
+    return "final pass: open bits without an open tensor";
+  }
+  if ((int64_t(1) << f.open_bits) != P.n_traces) return "final pass: trace count";
+
+  // ---- replay: every read finds the most recent exact write before it; no write overlaps a
+  // buffer that a later (or the same) launch still reads, nor another write of its launch
+  for (int u = 0; u <= uf; ++u) {
+    for (const Span& r : unit_reads[u]) {
+      int hit = -1;
+      for (int w = static_cast<int>(writes.size()) - 1; w >= 0; --w)
+        if (writes[w].unit < u && writes[w].s == r) {
+          hit = w;
+          break;
+        }
+      if (hit < 0) return "unit " + std::to_string(u) + " reads " + span_str(r) + " that no earlier launch wrote";
+      writes[hit].last_read = std::max(writes[hit].last_read, u);
+    }
+    for (const Span& w : unit_writes[u]) writes.push_back({w, u, -1});
+  }
+  // last_read is final now; check the hazards
+  for (size_t i = 0; i < writes.size(); ++i) {
+    const Write& w = writes[i];
+    for (const Span& r : unit_reads[w.unit])
+      if (overlaps(w.s, r)) return "unit " + std::to_string(w.unit) + " writes " + span_str(w.s) + " over its own input";
+    for (size_t j = 0; j < writes.size(); ++j) {
+      if (j == i) continue;
+      const Write& v = writes[j];
+      if (!overlaps(w.s, v.s)) continue;
+      if (v.unit == w.unit)
+        return "unit " + std::to_string(w.unit) + " writes overlapping buffers " + span_str(w.s) + " and " +
+               span_str(v.s);
+      if (v.unit < w.unit && v.last_read >= w.unit)
+        return "unit " + std::to_string(w.unit) + " overwrites " + span_str(v.s) + " (written by unit " +
+               std::to_string(v.unit) + ") before unit " + std::to_string(v.last_read) + " reads it";
+    }
+  }
+  return "";
+}
+
+}  // namespace ajf

@@ -1,6 +1,7 @@
 // A lowered contraction: descriptor arrays, the launch sequence and the arena layout.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "ajf_internal.h"
@@ -67,5 +68,10 @@ struct Program {
 // (LK_SPLITK), so that one thread block of the persistent kernel can run the whole program.
 Program lower(const Network& net, const Path& path, int precision, size_t inputs_complex, bool tc_ok,
               bool persistent = false);
+
+// Host-side replay of a lowered program's address arithmetic and buffer lifetimes (no device
+// needed): "" if every access stays inside its buffer and region and no launch overwrites a buffer
+// still to be read; otherwise the first violation.
+std::string check_program(const Program& P);
 
 }  // namespace ajf
