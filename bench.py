@@ -212,6 +212,9 @@ def main():
                     help="small-network workloads: keep 256 threads per persistent block")
     ap.add_argument("--no-simplified", action="store_true",
                     help="skip the run with SWAP elimination and local optimisations")
+    ap.add_argument("--no-sliced", action="store_true",
+                    help="skip the bond-sliced evaluations (AJF_SLICE_AUTO under one eighth of the arena)")
+    ap.add_argument("--sliced-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--instances", type=int, default=N_INSTANCES,
                     help="mid-config seeds per step (small values for profiler captures)")
@@ -393,6 +396,39 @@ def main():
         for c in sctx:
             c.close()
 
+    # ---- the same evaluations bond-sliced (AJF_SLICE_AUTO) to fit one eighth of their unsliced
+    # arenas: 2^s contractions of a smaller network per evaluation, summed in FP64
+    sliced = None
+    if not args.no_sliced:
+        for c in ctxs:
+            c.close()
+        ctxs = []
+        lctx, linfos = [], []
+        for inst, s, inf in zip(insts, streams, infos):
+            c = ajf.Context(dev, s.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            linfos.append(ajf.ajf_plan(c.handle, 2, precision=args.precision, trials=args.trials, use_graph=True,
+                                       slice_bonds="auto", mem_budget_bytes=inf["arena_bytes"] / 8))
+            lctx.append(c)
+        for c in lctx:  # warm-up: upload and graph capture
+            ajf.ajf_fidelity(c.handle)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.sliced_steps)):
+            F_sl = np.array([ajf.ajf_fidelity(c.handle)["F"] for c in lctx])
+        l_s = max_over_ranks(time.perf_counter() - t0, world)
+        sliced = {"value": n_inst * max(1, args.sliced_steps) * world / l_s, "unit": "evals/s",
+                  "sliced_bonds": [int(i["n_sliced_bonds"]) for i in linfos],
+                  "arena_bytes_max": float(max(i["arena_bytes"] for i in linfos)),
+                  "arena_bytes_max_unsliced": float(max(i["arena_bytes"] for i in infos)),
+                  "flops_per_step": float(sum(i["flops"] for i in linfos)),
+                  "max_abs_dF_vs_unsliced": float(np.max(np.abs(F_sl - F_fast))),
+                  "note": "host wall clock; instances one after another, each slice's result read back "
+                          "before the next run (ajf_fidelity on a bond-sliced plan)"}
+        for c in lctx:
+            c.close()
+
     # ---- end to end through the C ABI from host arrays
     for c in ctxs:
         c.close()
@@ -444,7 +480,7 @@ def main():
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,
             "flops_per_step": flops_per_step,
             "F_J": [float(x) for x in F_fast],
-            "roofline": roof, "kernel_classes": classes, "plain": plain, "simplified": simplified, "e2e": e2e,
+            "roofline": roof, "kernel_classes": classes, "plain": plain, "simplified": simplified, "sliced": sliced, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
