@@ -428,9 +428,12 @@ ajf_status ajf_selftest_convert(int device, const float *in, double *out, int64_
  * program is enqueued on that context's own stream (give each context its own stream for the
  * circuits to overlap on the GPU), then all results are read back; out[i] receives context i's.
  * Contexts may differ in circuit size and precision. Sec. IV-A notes that the traces -- and so
- * the circuits -- are independent.
+ * the circuits -- are independent. A bond-sliced context (opts.slice_bonds) enqueues all its
+ * runs on its stream at once when their staging fits 256 MiB of pinned memory (else it runs
+ * chunk by chunk after the others are enqueued); Kraus-sliced Alg. I plans are refused.
  * Errors: AJF_E_ARG (n_ctx < 1, NULL entries, bad alg, contexts on different devices),
- * AJF_E_STATE (a context without a plan for `alg`), plus those of ajf_fidelity_alg1/alg2. */
+ * AJF_E_STATE (a context without a plan for `alg`, an alg1_slices plan), plus those of
+ * ajf_fidelity_alg1/alg2. */
 ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out);
 
 /* Persistent execution of many small networks in ONE kernel launch (no paper counterpart; the

@@ -592,17 +592,33 @@ ajf_status fidelity_sliced(ajf_ctx* c, double eps, ajf_result* out) { return run
 // carry them taking the assignment's bits (fix_val; only the leaf descriptors change between
 // runs, which also holds under CUDA-graph replay). Alg. II adds the runs' real scalars, Alg. I
 // the runs' complex traces before |t|^2 is formed: both are linear in the runs, F is not.
-// run_bonds runs assignments [first, first + count) (a plan without bond slicing has the one
-// assignment 0): Alg. II returns the Neumaier-compensated FP64 sum of the runs' scalars in
-// *S_out, Alg. I adds the runs' traces to bond_traces (padded order) in run order.
-ajf_status run_bonds(ajf_ctx* c, int alg, int64_t first, int64_t count, double* S_out) {
+// Bond-sliced runs: each run's leaf descriptors are staged in a pinned slot and its result (and
+// Alg. I traces) read back into the same slot asynchronously, so runs are enqueued back to back
+// with one synchronisation per chunk of runs.
+struct BondLayout {
+  size_t lb = 0, tr_bytes = 0, per_run = 0;
+  int64_t chunk = 1;
+};
+
+BondLayout bond_layout(const ajf_ctx* c, int alg, int64_t count) {
+  auto a16 = [](size_t x) { return (x + 15) / 16 * 16; };
+  BondLayout L;
+  L.lb = c->bond_leaves.empty() ? 0 : a16(c->prog.leaves.size() * sizeof(LeafDev));
+  L.tr_bytes = alg == 1 ? 2 * static_cast<size_t>(c->prog.n_traces) * sizeof(double) : 0;
+  L.per_run = L.lb + 32 + a16(L.tr_bytes);
+  L.chunk = std::max<int64_t>(1, std::min<int64_t>(count, static_cast<int64_t>((size_t(256) << 20) / L.per_run)));
+  return L;
+}
+
+// Stage and enqueue runs [v0, v0 + n) (n <= L.chunk) into pinned slots 0..n-1.
+ajf_status enqueue_bond_runs(ajf_ctx* c, int alg, int64_t v0, int64_t n, const BondLayout& L) {
   const Program& P = c->prog;
   const size_t leaves_at = P.off_leaves - P.off_desc;
-  std::vector<double> padded;
-  if (alg == 1) padded.assign(2 * static_cast<size_t>(P.n_traces), 0.0);
-  double S = 0, comp = 0;
-  for (int64_t v = first; v < first + count; ++v) {
-    if (!c->bond_leaves.empty()) {
+  const size_t leaves_bytes = P.leaves.size() * sizeof(LeafDev);
+  for (int64_t r = 0; r < n; ++r) {
+    char* slot = c->pinned + static_cast<size_t>(r) * L.per_run;
+    const int64_t v = v0 + r;
+    if (L.lb) {
       for (auto& bl : c->bond_leaves) {
         uint16_t val = 0;
         for (auto& pb : bl.bits)
@@ -610,38 +626,63 @@ ajf_status run_bonds(ajf_ctx* c, int alg, int64_t first, int64_t count, double* 
         std::memcpy(c->desc_image.data() + leaves_at + bl.leaf * sizeof(LeafDev) + offsetof(LeafDev, fix_val), &val,
                     sizeof(val));
       }
-      CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, c->desc_image.data() + leaves_at,
-                                  P.leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, c->stream));
+      std::memcpy(slot, c->desc_image.data() + leaves_at, leaves_bytes);
+      CUDA_TRY(c, cudaMemcpyAsync(c->arena + P.off_leaves, slot, leaves_bytes, cudaMemcpyHostToDevice, c->stream));
     }
     ajf_status st = run_program(c);
     if (st != AJF_OK) return st;
-    double res[3];
-    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + P.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(slot + L.lb, c->arena + P.off_result, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
     if (alg == 1)
-      CUDA_TRY(c, cudaMemcpyAsync(padded.data(), c->arena + P.off_traces, padded.size() * sizeof(double),
-                                  cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(slot + L.lb + 32, c->arena + P.off_traces, L.tr_bytes, cudaMemcpyDeviceToHost,
+                                  c->stream));
+  }
+  return AJF_OK;
+}
+
+// After the stream has drained: add the n slots' results in run order (Alg. II: Neumaier sum of
+// the scalars into S/comp; Alg. I: traces into bond_traces).
+void collect_bond_runs(ajf_ctx* c, int alg, int64_t n, const BondLayout& L, double& S, double& comp) {
+  for (int64_t r = 0; r < n; ++r) {
+    const char* slot = c->pinned + static_cast<size_t>(r) * L.per_run;
+    if (alg == 2) {
+      double x;
+      std::memcpy(&x, slot + L.lb, sizeof(x));
+      const double t = S + x;
+      comp += std::fabs(S) >= std::fabs(x) ? (S - t) + x : (x - t) + S;
+      S = t;
+    } else {
+      const double* tr = reinterpret_cast<const double*>(slot + L.lb + 32);
+      for (size_t i = 0; i < c->bond_traces.size(); ++i) c->bond_traces[i] += tr[i];
+    }
+  }
+}
+
+// run_bonds runs assignments [first, first + count) (a plan without bond slicing has the one
+// assignment 0): Alg. II returns the Neumaier-compensated FP64 sum of the runs' scalars in
+// *S_out, Alg. I adds the runs' traces to bond_traces (padded order) in run order.
+ajf_status run_bonds(ajf_ctx* c, int alg, int64_t first, int64_t count, double* S_out) {
+  const BondLayout L = bond_layout(c, alg, count);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the staging buffer may still feed an upload
+  ajf_status st = ensure_pinned(c, L.per_run * static_cast<size_t>(L.chunk));
+  if (st != AJF_OK) return st;
+  double S = 0, comp = 0;
+  for (int64_t v0 = first; v0 < first + count; v0 += L.chunk) {
+    const int64_t n = std::min(L.chunk, first + count - v0);
+    st = enqueue_bond_runs(c, alg, v0, n, L);
+    if (st != AJF_OK) return st;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     st = check_status_words(c);
     if (st != AJF_OK) return st;
-    if (alg == 2) {  // Neumaier summation
-      const double t = S + res[0];
-      comp += std::fabs(S) >= std::fabs(res[0]) ? (S - t) + res[0] : (res[0] - t) + S;
-      S = t;
-    } else {
-      for (size_t i = 0; i < padded.size(); ++i) c->bond_traces[i] += padded[i];
-    }
+    collect_bond_runs(c, alg, n, L, S, comp);
   }
   if (S_out) *S_out = S + comp;
   return AJF_OK;
 }
 
-ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
-  Range nvtx_range("ajf bond slices");
-  const int nb = static_cast<int>(c->bond_labels.size());
-  if (alg == 1) c->bond_traces.assign(2 * static_cast<size_t>(c->prog.n_traces), 0.0);
-  double S = 0;
-  ajf_status st = run_bonds(c, alg, 0, int64_t(1) << nb, &S);
-  if (st != AJF_OK) return st;
+// The result of a whole bond-sliced evaluation: S from the Alg. II sum, or from the summed
+// Alg. I traces (|t|^2 is formed only after the sum over slices).
+void finish_bonds(ajf_ctx* c, int alg, double S, double eps, ajf_result* out) {
   if (alg == 1) {
     double comp = 0;
     S = 0;
@@ -661,6 +702,16 @@ ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
   out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
   out->reserved = 0;
   if (alg == 1) c->have_alg1 = true;
+}
+
+ajf_status fidelity_bonds(ajf_ctx* c, int alg, double eps, ajf_result* out) {
+  Range nvtx_range("ajf bond slices");
+  const int nb = static_cast<int>(c->bond_labels.size());
+  if (alg == 1) c->bond_traces.assign(2 * static_cast<size_t>(c->prog.n_traces), 0.0);
+  double S = 0;
+  ajf_status st = run_bonds(c, alg, 0, int64_t(1) << nb, &S);
+  if (st != AJF_OK) return st;
+  finish_bonds(c, alg, S, eps, out);
   return AJF_OK;
 }
 
@@ -1704,10 +1755,13 @@ ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double e
       return fail(ctxs[0], AJF_E_ARG, "contexts must share one device");
     if (!ctxs[i]->planned || ctxs[i]->alg != alg)
       return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
-    if (multi_run(ctxs[i])) return fail(ctxs[i], AJF_E_STATE, "a sliced plan runs through ajf_fidelity_alg1/2 / ajf_fidelity only");
+    if (is_sliced(ctxs[i]))
+      return fail(ctxs[i], AJF_E_STATE, "a sliced Alg. I plan runs through ajf_fidelity_alg1 / ajf_fidelity only");
     if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
   }
-  // every context runs on its own stream so independent circuits overlap on the GPU
+  // every context runs on its own stream so independent circuits overlap on the GPU; a
+  // bond-sliced context enqueues all its runs at once when they fit one staging chunk
+  std::vector<char> bonds_pending(n_ctx, 0);
   for (int i = 0; i < n_ctx; ++i) {
     ajf_ctx* c = ctxs[i];
     CUDA_TRY(c, cudaSetDevice(c->device));
@@ -1715,11 +1769,40 @@ ajf_status ajf_fidelity_batch(ajf_ctx* const* ctxs, int n_ctx, int alg, double e
       ajf_status st = do_upload(c);
       if (st != AJF_OK) return st;
     }
+    if (bond_sliced(c)) {
+      const int64_t runs = int64_t(1) << c->bond_labels.size();
+      const BondLayout L = bond_layout(c, alg, runs);
+      if (L.chunk < runs) continue;  // run in the second pass, chunk by chunk
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      ajf_status st = ensure_pinned(c, L.per_run * static_cast<size_t>(runs));
+      if (st == AJF_OK) st = enqueue_bond_runs(c, alg, 0, runs, L);
+      if (st != AJF_OK) return st;
+      bonds_pending[i] = 1;
+      continue;
+    }
     ajf_status st = run_program(c);
     if (st != AJF_OK) return st;
   }
   for (int i = 0; i < n_ctx; ++i) {
     ajf_ctx* c = ctxs[i];
+    if (bond_sliced(c)) {
+      ajf_status st;
+      if (bonds_pending[i]) {
+        const int64_t runs = int64_t(1) << c->bond_labels.size();
+        const BondLayout L = bond_layout(c, alg, runs);
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        st = check_status_words(c);
+        if (st != AJF_OK) return st;
+        if (alg == 1) c->bond_traces.assign(2 * static_cast<size_t>(c->prog.n_traces), 0.0);
+        double S = 0, comp = 0;
+        collect_bond_runs(c, alg, runs, L, S, comp);
+        finish_bonds(c, alg, S + comp, eps, &out[i]);
+      } else {
+        st = fidelity_bonds(c, alg, eps, &out[i]);
+        if (st != AJF_OK) return st;
+      }
+      continue;
+    }
     double res[3];
     CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -178,9 +178,39 @@ def test_single_run_paths_reject_sliced_plans(gpu):
         with pytest.raises(ajf.AjfError) as e:
             ajf.ajf_fidelity_noalloc(c.handle, 2)
         assert e.value.status == ajf.AJF_E_STATE
+        ajf.ajf_upload(c.handle)
         with pytest.raises(ajf.AjfError) as e:
-            ajf.ajf_fidelity_batch([c.handle], 2)
-        assert e.value.status == ajf.AJF_E_STATE
+            ajf.ajf_launch(c.handle, 0)
+        assert e.value.status == ajf.AJF_E_STATE and "sliced" in str(e.value)
         r = ajf.ajf_fidelity_alg2(c.handle)
     from oracle import dense
     assert abs(r["F"] - dense.fidelity(inst)["F"]) <= 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("alg", [1, 2])
+def test_batch_of_sliced_and_unsliced_contexts(gpu, alg):
+    """ajf_fidelity_batch over contexts on their own streams: bond-sliced ones (1-3 labels) enqueue
+    all their runs at once next to unsliced ones; every F_J (and Alg. I trace) against the oracle."""
+    import torch
+    from oracle import dense
+    insts = [W.random_small(s, n=3 + s % 3, n_gates=14, n_noises=2 + s % 2, two_qubit_noise=(s % 2 == 0))
+             for s in range(4)]
+    streams = [torch.cuda.Stream() for _ in insts]
+    ctxs = [ajf.Context(0, st.cuda_stream) for st in streams]
+    try:
+        for k, (c, inst) in enumerate(zip(ctxs, insts)):
+            ajf.load_instance(c.handle, inst)
+            ajf.ajf_plan(c.handle, alg, trials=4, slice_bonds=k % 4)
+        for _ in range(2):  # the second call replays graphs and reuses the staging buffers
+            rs = ajf.ajf_fidelity_batch([c.handle for c in ctxs], alg)
+            for r, inst, c in zip(rs, insts, ctxs):
+                ref = dense.fidelity(inst)
+                assert abs(r["F"] - ref["F"]) <= 1e-12
+                assert abs(r["one_minus_F"] - ref["one_minus_F"]) <= 1e-12
+                if alg == 1:
+                    t = ajf.ajf_alg1_traces(c.handle, inst.n_combinations())
+                    np.testing.assert_allclose(t, ref["traces"], atol=1e-12 * 2 ** inst.n)
+    finally:
+        for c in ctxs:
+            c.close()
