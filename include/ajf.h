@@ -289,7 +289,8 @@ ajf_status ajf_alg1_restore(ajf_ctx *ctx, const ajf_alg1_state *state);
 /* Host-side replay of the current plan's device program (no device needed; the paper has no
  * counterpart). It stands in for a device memory checker, which this library cannot rely on.
  * Every address a kernel of the program can form is a base plus distinct powers of two taken
- * from the step's index maps: leaves, pairwise steps, operand gathers, GEMM operands, results,
+ * from the step's index maps (which must address every bit of their operand, or elements would
+ * be skipped): leaves, pairwise steps, operand gathers, GEMM operands, results,
  * K-split workspaces, partial sums, scalar slots and the final pass. The check makes sure that
  * each such address lies inside its buffer and the arena region that holds it. Replaying the
  * launches in stream order, it also makes sure that:
@@ -305,7 +306,8 @@ ajf_status ajf_check_plan(ajf_ctx *ctx);
  * 2: an index-map position beyond its operand's bits; 3: a step writing over its own input;
  * 4: a step reading memory that no launch wrote; 5: two leaves in the same place; 6: a step of
  * the first launch writing over a leaf that a later launch still reads (3, 5 and 6 move their
- * buffer's readers along, so that only the overlap is wrong). The context's
+ * buffer's readers along, so that only the overlap is wrong); 7: an operand bit that no index
+ * map addresses (elements that would be skipped). The context's
  * own program is not changed. Returns AJF_OK when the check reports the mistake (its message is
  * in ajf_last_error), AJF_E_STATE when it does not, AJF_E_ARG for an unknown mutation or a plan
  * without the needed step. */

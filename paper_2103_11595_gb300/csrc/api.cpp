@@ -1403,6 +1403,20 @@ ajf_status ajf_selftest_check_plan(ajf_ctx* c, int mutation) {
       d->c = P.leaves[x].off;
       break;
     }
+    case 7: {  // an operand bit that no map addresses (an output bit dropped from A's map)
+      StepDev* d = first_step([](const StepDev& x) {
+        for (int i = 0; i < x.oa.nbits; ++i)
+          if (x.oa.pos[i] >= 0) return true;
+        return false;
+      });
+      if (!d) return fail(c, AJF_E_ARG, "no step with an output bit of A");
+      for (int i = 0; i < d->oa.nbits; ++i)
+        if (d->oa.pos[i] >= 0) {
+          d->oa.pos[i] = -1;
+          break;
+        }
+      break;
+    }
     default:
       return fail(c, AJF_E_ARG, "unknown mutation");
   }

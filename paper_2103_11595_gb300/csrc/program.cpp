@@ -659,6 +659,9 @@ std::string check_program(const Program& P) {
         uint64_t ua = 0, ub = 0;
         if (!add_positions(d.oa, ba, ua) || !add_positions(d.ka, ba, ua)) return ws + ": A addresses repeat or overflow";
         if (!add_positions(d.ob, bb, ub) || !add_positions(d.kb, bb, ub)) return ws + ": B addresses repeat or overflow";
+        // every operand bit is an output or a contracted bit: otherwise elements would be skipped
+        if (ua != (ba == 64 ? ~0ull : (uint64_t(1) << ba) - 1) || ub != (bb == 64 ? ~0ull : (uint64_t(1) << bb) - 1))
+          return ws + ": an operand bit is not addressed";
         const Span sa = tensor(d.a, d.pa), sb = tensor(d.b, d.pb);
         if (!in_work(sa) || !in_work(sb)) return ws + ": an operand lies outside the work region";
         R.push_back(sa);
@@ -703,6 +706,7 @@ std::string check_program(const Program& P) {
         uint64_t used = 0;
         if (!add_positions(g.rows, bp, used) || !add_positions(g.cols, bp, used))
           return ws + ": source addresses repeat or overflow";
+        if (used != (uint64_t(1) << bp) - 1) return ws + ": a source bit is not addressed";
         const Span src = tensor(g.src, g.plane);
         if (!in_work(src)) return ws + ": source outside the work region";
         R.push_back(src);
@@ -752,7 +756,8 @@ std::string check_program(const Program& P) {
   if (f.open_off >= 0) {
     const int bo = log2_exact(f.open_plane);
     uint64_t used = 0;
-    if (bo < 0 || f.open_map.nbits != f.open_bits || bo != f.open_bits || !add_positions(f.open_map, bo, used))
+    if (bo < 0 || f.open_map.nbits != f.open_bits || bo != f.open_bits || !add_positions(f.open_map, bo, used) ||
+        used != (uint64_t(1) << bo) - 1)
       return "final pass: open-tensor addresses";
     const Span so = tensor(f.open_off, f.open_plane);
     if (!in_work(so)) return "final pass: open tensor outside the work region";

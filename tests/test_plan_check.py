@@ -3,7 +3,8 @@
 A device memory checker is not available to this library, so every lowered program is replayed
 on the host instead. Every address a kernel can form is a base offset plus distinct powers of
 two from the step's index maps, so the largest is known. The replay checks:
-  - every access lies inside its buffer and arena region;
+  - every access lies inside its buffer and arena region, and every operand bit is addressed
+    (else elements would be skipped);
   - every read finds the launch that wrote it;
   - no launch writes over a buffer that it, or a later launch, still reads;
   - no two writes of one launch overlap.
@@ -67,7 +68,8 @@ def test_persistent_sliced_and_simplified_plans():
 
 
 RULES = {1: "outside the work region", 2: "addresses repeat or overflow", 3: "over its own input",
-         4: "that no earlier launch wrote", 5: "writes overlapping buffers", 6: "before unit"}
+         4: "that no earlier launch wrote", 5: "writes overlapping buffers", 6: "before unit",
+         7: "bit is not addressed"}
 
 
 @pytest.mark.parametrize("mutation", sorted(RULES))
