@@ -313,7 +313,8 @@ ajf_status ajf_check_plan(ajf_ctx *ctx);
  * without the needed step. */
 ajf_status ajf_selftest_check_plan(ajf_ctx *ctx, int mutation);
 
-/* Independent runs of one evaluation of the current plan: the Kraus-index slices of a sliced
+/* Independent runs of one evaluation of the current plan (Sec. IV-A remarks that the traces are
+ * independent; bond slices have no paper counterpart): the Kraus-index slices of a sliced
  * Alg. I plan (opts.alg1_slices), 2^n_sliced_bonds for a bond-sliced plan (opts.slice_bonds),
  * otherwise 1. These are the units for sharding one evaluation across devices or processes.
  * Errors: AJF_E_ARG (NULL), AJF_E_STATE (no plan). */
