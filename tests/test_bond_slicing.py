@@ -90,6 +90,42 @@ def test_leaves_keep_a_label():
         assert p["width"] >= max(1, open_bits)
 
 
+def _sliced_sum(tensors, loops, cut):
+    """Sum over every assignment of the labels in `cut` of the contraction with those labels fixed
+    in every tensor that carries them (the oracle's own networks and contraction)."""
+    from oracle import network
+    total = 0
+    for v in range(2 ** len(cut)):
+        fixed = {x: (v >> j) & 1 for j, x in enumerate(cut)}
+        ts = [(arr[tuple(fixed[x] if x in fixed else slice(None) for x in ls)], [x for x in ls if x not in fixed])
+              for arr, ls in tensors]
+        total += network.contract(ts, loops, order="greedy")[0]
+    return total
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_slicing_identity_on_the_oracle_networks(seed):
+    """The identity bond slicing rests on, checked with the oracle's networks and no library code:
+    fixing s labels in both tensors that carry them and adding the 2^s contractions gives the full
+    contraction (the doubled network's S of Sec. IV-B and one Alg. I trace of Sec. IV-A)."""
+    from oracle import dense, network
+    inst = W.random_small(seed, n=3 + seed, n_gates=14, n_noises=3, two_qubit_noise=True)
+    rng = np.random.default_rng(seed)
+    tensors, loops = network.alg2_network(inst)
+    labels = sorted({x for _, ls in tensors for x in ls})
+    full = network.contract(tensors, loops, order="greedy")[0]
+    assert abs(full.real - dense.fidelity(inst)["S"]) <= 1e-10
+    for s in (1, 2, 4):
+        cut = [int(x) for x in rng.choice(labels, s, replace=False)]
+        assert abs(_sliced_sum(tensors, loops, cut) - full) <= 1e-12 * abs(full)
+    choice = [int(rng.integers(len(nz.kraus))) for nz in inst.noises]
+    tensors, loops = network.alg1_network(inst, choice)
+    labels = sorted({x for _, ls in tensors for x in ls})
+    t = network.contract(tensors, loops, order="greedy")[0]
+    cut = [int(x) for x in rng.choice(labels, 3, replace=False)]
+    assert abs(_sliced_sum(tensors, loops, cut) - t) <= 1e-12 * max(1.0, abs(t))
+
+
 # --------------------------------------------------------------------------- GPU
 
 
