@@ -293,7 +293,8 @@ ajf_status ajf_alg1_restore(ajf_ctx *ctx, const ajf_alg1_state *state);
  * be skipped): leaves, pairwise steps, operand gathers, GEMM operands, results,
  * K-split workspaces, partial sums, scalar slots and the final pass. The check makes sure that
  * each such address lies inside its buffer and the arena region that holds it. Replaying the
- * launches in stream order, it also makes sure that:
+ * launches in stream order (each GEMM's shape must be that of the two gathers feeding it), it
+ * also makes sure that:
  *   - every buffer read was written by an earlier launch;
  *   - no launch writes over a buffer that it, or a later launch, still reads;
  *   - no two writes of one launch overlap.
@@ -307,7 +308,8 @@ ajf_status ajf_check_plan(ajf_ctx *ctx);
  * 4: a step reading memory that no launch wrote; 5: two leaves in the same place; 6: a step of
  * the first launch writing over a leaf that a later launch still reads (3, 5 and 6 move their
  * buffer's readers along, so that only the overlap is wrong); 7: an operand bit that no index
- * map addresses (elements that would be skipped). The context's
+ * map addresses (elements that would be skipped); 8: a GEMM whose K differs from its gathers'.
+ * The context's
  * own program is not changed. Returns AJF_OK when the check reports the mistake (its message is
  * in ajf_last_error), AJF_E_STATE when it does not, AJF_E_ARG for an unknown mutation or a plan
  * without the needed step. */

@@ -1417,6 +1417,14 @@ ajf_status ajf_selftest_check_plan(ajf_ctx* c, int mutation) {
         }
       break;
     }
+    case 8: {  // a GEMM whose K is twice its gathers' (it would read past their operand terms)
+      Launch* g = nullptr;
+      for (auto& ln : P.launches)
+        if (!g && (ln.kind == LK_GEMM_TC || ln.kind == LK_GEMM_SIMT)) g = &ln;
+      if (!g) return fail(c, AJF_E_ARG, "no GEMM launch");
+      g->K *= 2;
+      break;
+    }
     default:
       return fail(c, AJF_E_ARG, "unknown mutation");
   }

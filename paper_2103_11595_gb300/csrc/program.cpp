@@ -722,6 +722,11 @@ std::string check_program(const Program& P) {
       if (li == 0 || P.launches[li - 1].kind != LK_PERM) return who + ": GEMM without its gather";
       const Launch& lp = P.launches[li - 1];
       const PermDev& px = P.perms[lp.first];
+      const PermDev& py = P.perms[lp.first + 1];
+      // the GEMM's shape is the gathers': X' = 2M x 2K (embedded), Y' = N x 2K, one K
+      if (px.embed != 1 || py.embed != 0 || px.kbits != py.kbits || px.mode != py.mode ||
+          ln.M != (int64_t(2) << px.rbits) || ln.N != (int64_t(1) << py.rbits) || ln.K != (int64_t(2) << px.kbits))
+        return who + ": GEMM shape differs from its gathers";
       const size_t eb = mode_bytes(px.mode);
       const int terms = ln.kind == LK_GEMM_TC ? ln.npass : 1;
       if (terms < 1 || terms > 3 || terms != mode_terms(px.mode)) return who + ": operand terms";

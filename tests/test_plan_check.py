@@ -69,15 +69,17 @@ def test_persistent_sliced_and_simplified_plans():
 
 RULES = {1: "outside the work region", 2: "addresses repeat or overflow", 3: "over its own input",
          4: "that no earlier launch wrote", 5: "writes overlapping buffers", 6: "before unit",
-         7: "bit is not addressed"}
+         7: "bit is not addressed", 8: "GEMM shape differs from its gathers"}
 
 
 @pytest.mark.parametrize("mutation", sorted(RULES))
 def test_planted_mistakes_are_reported(mutation):
     """Each mistake is planted in a copy of the program; the check must report it, by the rule
     meant for it (3, 5 and 6 move their buffer's readers along, so that only the overlap is wrong)."""
-    for inst, alg, precision in ((W.tiny(0), 2, "f64"), (W.tiny(3), 1, "f64"), (W.mid(0), 2, "bf16x6"),
-                                 (W.batching_circuit(2), 1, "bf16x6")):
+    cases = ((W.tiny(0), 2, "f64"), (W.tiny(3), 1, "f64"), (W.mid(0), 2, "bf16x6"), (W.batching_circuit(2), 1, "bf16x6"))
+    if mutation == 8:  # needs a GEMM: the networks with tensor-core steps
+        cases = ((W.mid(0), 2, "bf16x6"), (W.mid(1), 2, "f64"), (W.mid(2), 1, "tf32x3"))
+    for inst, alg, precision in cases:
         with ajf.Context(-1) as c:
             ajf.load_instance(c.handle, inst)
             ajf.ajf_plan(c.handle, alg, trials=4, precision=precision)
