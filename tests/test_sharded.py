@@ -68,6 +68,13 @@ def test_two_gloo_ranks_all_reduce_the_partial_sums():
 def test_slice_counts_of_plans():
     with ajf.Context(-1) as c:
         ajf.load_instance(c.handle, W.tiny(0))      # 2 depolarising noises, 4 Kraus operators each
+        with pytest.raises(ajf.AjfError) as e:           # no plan yet
+            ajf.ajf_slice_count(c.handle)
+        assert e.value.status == ajf.AJF_E_STATE
+        ajf.ajf_plan(c.handle, 1, trials=2)
+        with pytest.raises(ajf.AjfError) as e:           # an Alg. I plan has no Alg. II slices
+            ajf.ajf_alg2_slice_range(c.handle, 0, 1)
+        assert e.value.status == ajf.AJF_E_STATE and "Alg. II" in str(e.value)
         ajf.ajf_plan(c.handle, 2, trials=2)
         assert ajf.ajf_slice_count(c.handle) == 1
         ajf.ajf_plan(c.handle, 2, trials=2, slice_bonds=3)
