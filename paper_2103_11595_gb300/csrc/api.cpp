@@ -2007,7 +2007,7 @@ ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_r
   cudaStream_t s0 = lead->stream;
   for (int i = 1; i < n_ctx; ++i) {
     if (ctxs[i]->stream == s0) continue;
-    cudaEvent_t ev;
+    cudaEvent_t ev = nullptr;
     if ((st = sync_event(ctxs[i], &ev)) != AJF_OK) return st;
     CUDA_TRY(ctxs[i], cudaEventRecord(ev, ctxs[i]->stream));
     CUDA_TRY(lead, cudaStreamWaitEvent(s0, ev, 0));
@@ -2024,7 +2024,7 @@ ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_r
                                             lead->pers_smem, lead->pers_threads, s0);
     if (e != cudaSuccess) return cuda_fail(lead, e, "persistent kernel");
   }
-  cudaEvent_t ev0;
+  cudaEvent_t ev0 = nullptr;
   if ((st = sync_event(lead, &ev0)) != AJF_OK) return st;
   CUDA_TRY(lead, cudaEventRecord(ev0, s0));
   for (int i = 1; i < n_ctx; ++i)
