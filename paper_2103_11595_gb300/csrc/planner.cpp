@@ -66,17 +66,6 @@ Labels sym_diff(const Labels& a, const Labels& b, int* shared) {
   return out;
 }
 
-int count_shared(const Labels& a, const Labels& b) {
-  size_t i = 0, j = 0;
-  int sh = 0;
-  while (i < a.size() && j < b.size()) {
-    if (a[i] < b[j]) ++i;
-    else if (b[j] < a[i]) ++j;
-    else { ++sh; ++i; ++j; }
-  }
-  return sh;
-}
-
 // Merge whatever is left when no two tensors share a label: tensors with open labels are joined
 // by outer products (smallest first); scalars stay separate and are multiplied at the end.
 void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& path) {
