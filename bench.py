@@ -45,7 +45,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     def __init__(self, index: int):
         self.index = index
@@ -59,7 +59,7 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -118,8 +118,7 @@ def shard_seeds(rank: int, n_inst: int, first: int = 0) -> list:
 # averaged over the GEMM launches of one step of the mid workload (seeds 0-9, bf16x6), from one
 # ncu capture per seed (each seed alone: the whole step holds ~8.5 GB on the device). The figures
 # belong to the GEMM kernel's source as hashed below; a changed kernel reports traffic null until
-# it is captured again (the capture commands are in profiles/k_gemm_tc_mid_bf16x6.md). The GEMM's
-# device code is all in the two files hashed.
+# it is captured again. The GEMM's device code is all in the two files hashed.
 TC_TRAFFIC = {"sha256": "d263bc17a857c51c61bcff373003d40c0641888f20279b700d35e3204ccd3b39",
               "precision": "bf16x6", "bytes_per_launch": 52191041.9, "launches": 233}
 TC_SOURCES = ("paper_2103_11595_gb300/csrc/tc_gemm.cu", "paper_2103_11595_gb300/csrc/fp_bits.h")
@@ -150,7 +149,7 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def oracle_sample(min_s: float = 10.0):
+def oracle_sample(min_s: float = 10.0, threads: str = "default"):
     """Oracle O2 (Alg. II network, min-fill order, numpy tensordot, complex128) on the mid seeds in
     order (0, 1, 2, ...) until at least `min_s` seconds of CPU work are done (a bounded sample of
     the workload: each evaluation takes about 1-10 s)."""
@@ -165,9 +164,35 @@ def oracle_sample(min_s: float = 10.0):
         if time.perf_counter() - t0 >= min_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+    cores = 1 if threads == "1" else os.cpu_count()
+    blas = "one BLAS thread" if threads == "1" else f"default BLAS threads ({cores})"
+    return {"value": done / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} evaluation(s) of mid seeds 0..{done - 1} (Alg. II, oracle/network.py, min-fill "
-                      f"order, numpy complex128 tensordot, default BLAS threads) in {dt:.1f} s"}
+                      f"order, numpy complex128 tensordot, {blas}) in {dt:.1f} s"}
+
+
+_SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                      "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
+
+
+def oracle_sample_single_thread(min_s: float = 10.0):
+    """The same sample with one BLAS thread, in a fresh interpreter (the thread count of numpy's
+    BLAS is fixed when it loads)."""
+    env = dict(os.environ, **{k: "1" for k in _SINGLE_THREAD_ENV})
+    code = ("import json, bench; print(json.dumps(bench.oracle_sample(%r, threads='1')))" % float(min_s))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=20 * min_s + 120)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # a missing figure must not sink the bench line
+        return {"value": None, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+def cpu_baselines(min_s: float = 10.0):
+    """The oracle on all host cores (numpy's default BLAS threads) and on one thread."""
+    cpu = oracle_sample(min_s)
+    cpu["single_thread"] = oracle_sample_single_thread(min_s)
+    return cpu
 
 
 def run_reference(args, world, rank):
@@ -222,6 +247,12 @@ def main():
                     help="first mid-config seed (per-seed profiler captures)")
     ap.add_argument("--persistent-flops", type=float, default=2e6,
                     help="batching workload: networks up to this many flops run in the persistent kernel")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="mid workload: skip the batching-workload block of the line")
+    ap.add_argument("--no-oracle-parity", action="store_true",
+                    help="batching workload: skip the |dF| check against the CPU oracle")
+    ap.add_argument("--oracle-parity-s", type=float, default=20.0,
+                    help="batching workload: seconds of oracle work for the |dF| check")
     ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "batching", "precision"],
                     help="mid: the headline workload; tiny / batching: the small-network workloads "
                          "run through the persistent kernel")
@@ -356,7 +387,7 @@ def main():
     if (dom == "gemm_tc" and TC_TRAFFIC["sha256"] == tc_source_sha256() and args.precision == TC_TRAFFIC["precision"]
             and n_inst == N_INSTANCES and args.first_seed == 0 and d["launches"] == TC_TRAFFIC["launches"] * world):
         traffic = TC_TRAFFIC["bytes_per_launch"]
-        roof["traffic_src"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_gemm_tc_mid_bf16x6.md"
+        roof["traffic_src"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per GEMM launch of one step"
     roof.update({"kernel_class": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
                  "launches_per_step": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                  "share_of_step": d["ms"] / max(1e-9, sum(v["ms"] for v in classes.values()))})
@@ -367,10 +398,11 @@ def main():
         for c in ctxs:
             c.close()
         pctx, pinfos = make_contexts("f64")
-        p_ms = timed_steps(pctx, 1, 1)
+        p_ms = timed_steps(pctx, args.steps, args.warmup)
         F_plain = out[:, 1].cpu().numpy().copy()
         p_s = max_over_ranks(p_ms / 1e3, world)
-        plain = {"value": n_inst * world / p_s, "unit": "evals/s", "dtype": "c128",
+        plain = {"value": n_inst * args.steps * world / p_s, "unit": "evals/s", "dtype": "c128",
+                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": p_s * 1e3 / args.steps,
                  "max_abs_dF_fast_vs_plain": float(np.max(np.abs(F_fast - F_plain))),
                  "max_rel_d_one_minus_F": float(np.max(np.abs((1 - F_fast) - (1 - F_plain)) / np.abs(1 - F_plain)))}
         for c in pctx:
@@ -462,7 +494,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample()
+        cpu = cpu_baselines()
+
+    # the batching workload (Alg. I over 64 circuits) as a block of the same line
+    batching = None
+    if not args.no_batching:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.workload = "batching"
+        bargs.no_cpu_baseline = True
+        batching = small_networks_line(bargs, world, rank, local)
+        if rank == 0:
+            batching = {k: batching[k] for k in ("value", "unit", "ms_per_step", "us_per_eval", "traces_per_s",
+                                                  "e2e", "default_path", "oracle_parity", "roofline", "config",
+                                                  "gpu_launches", "clocks", "dtype")}
 
     if rank == 0:
         line = {
@@ -480,7 +524,8 @@ def main():
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,
             "flops_per_step": flops_per_step,
             "F_J": [float(x) for x in F_fast],
-            "roofline": roof, "kernel_classes": classes, "plain": plain, "simplified": simplified, "sliced": sliced, "e2e": e2e,
+            "roofline": roof, "kernel_classes": classes, "plain": plain, "simplified": simplified, "sliced": sliced,
+            "batching": batching, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
@@ -495,8 +540,38 @@ BATCHING = ("batching: 64 circuits, n~U{8..20}, 50-300 gates (U3 + NN-CX bricks)
 
 
 def run_small_networks(args, world, rank, local):
+    line = small_networks_line(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+def oracle_parity(jobs, F_dev, budget_s: float):
+    """|dF| of the device results against the oracle's F_J (Alg. II network, min-fill order), on
+    the jobs taken smallest n first until `budget_s` seconds of oracle work are spent."""
+    import numpy as np
+    from oracle import network
+    order = sorted(range(len(jobs)), key=lambda j: (jobs[j][0].n, len(jobs[j][0].ideal)))
+    t0 = time.perf_counter()
+    dF, rel, checked = [], [], []
+    for j in order:
+        if time.perf_counter() - t0 >= budget_s:
+            break
+        r = network.alg2_fidelity(jobs[j][0], order="minfill")
+        dF.append(abs(float(F_dev[j]) - r["F"]))
+        rel.append(abs((1 - float(F_dev[j])) - r["one_minus_F"]) / r["one_minus_F"])
+        checked.append(j)
+    return {"checked": len(checked), "of": len(jobs), "max_abs_dF": float(np.max(dF)) if dF else None,
+            "max_rel_err_one_minus_F": float(np.max(rel)) if rel else None,
+            "max_n": int(max(jobs[j][0].n for j in checked)) if checked else None,
+            "seconds": time.perf_counter() - t0,
+            "how": "oracle/network.py Alg. II (min-fill, complex128) on the circuits taken smallest n first"}
+
+
+def small_networks_line(args, world, rank, local):
     """Small-network workloads: all networks of a step in one persistent-kernel launch (tiny), or
-    the small ones in one persistent launch and the large ones on their own streams (batching)."""
+    the small ones in one persistent launch and the large ones on their own streams (batching).
+    Returns the bench line (rank 0) without printing it."""
     import numpy as np
     import torch
 
@@ -605,7 +680,7 @@ def run_small_networks(args, world, rank, local):
                 pers_threads[alg] = ajf.ajf_autotune_persistent([pers[i].handle for i in groups[alg]], reps=5)
         torch.cuda.synchronize()
 
-    # a tiny step takes well under a millisecond: time enough steps for the clock sampler (200 ms)
+    # a tiny step takes well under a millisecond: time enough steps for the clock sampler
     if args.workload == "tiny":
         args.steps = max(args.steps, 2000)
     with ClockSampler(dev) as clk:
@@ -636,6 +711,11 @@ def run_small_networks(args, world, rank, local):
             "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s); the kernel is latency-bound at these sizes",
             "launches_per_step": pst["launches"], "avg_launch_ms": pst["ms"] / max(1, pst["launches"]),
             "hbm_bytes_per_launch_alg": pst["bytes"] / max(1, pst["launches"])}
+
+    # device results in job order (rows of `out` follow the persistent groups by alg, then big)
+    F_ord = np.empty(n_jobs)
+    for j, ((inst, alg), (kind, idx)) in enumerate(zip(jobs, order)):
+        F_ord[j] = F_dev[pers_rows[alg] + groups[alg].index(idx)] if kind == "p" else F_dev[big_rows[idx]]
 
     # the default path on the same jobs (per-context CUDA graphs, one stream per context)
     default = None
@@ -673,13 +753,6 @@ def run_small_networks(args, world, rank, local):
             e1.synchronize()
         d_ms = e0.elapsed_time(e1)
         F_def = dout[:, 1].cpu().numpy()
-        # rows of `out` follow (persistent groups by alg, then big); map them back to job order
-        F_ord = np.empty(n_jobs)
-        for j, ((inst, alg), (kind, idx)) in enumerate(zip(jobs, order)):
-            if kind == "p":
-                F_ord[j] = F_dev[pers_rows[alg] + groups[alg].index(idx)]
-            else:
-                F_ord[j] = F_dev[big_rows[idx]]
         default = {"value": n_jobs / (d_ms / 1e3), "unit": "evals/s", "dtype": "f64",
                    "path": "default lowering, one CUDA graph per network, one stream per network",
                    "max_abs_dF_vs_persistent_run": float(np.max(np.abs(F_ord - F_def)))}
@@ -730,8 +803,13 @@ def run_small_networks(args, world, rank, local):
         cpu = {"value": done / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the first {done} evaluations of the step, {how}, in {dt:.1f} s"}
 
+    parity = None
+    if rank == 0 and args.workload == "batching" and not args.no_oracle_parity:
+        parity = oracle_parity(jobs, F_ord, args.oracle_parity_s)
+
     for c in pers + big:
         c.close()
+    line = None
     if rank == 0:
         n_traces = sum(i.n_combinations() for i, a in jobs if a == 1)
         line = {
@@ -747,12 +825,12 @@ def run_small_networks(args, world, rank, local):
                        "parallelism": f"{world} independent ranks (weak scaling)"},
             "traces_per_s": n_traces * args.steps * world / total_s,
             "roofline": roof, "default_path": default, "e2e": e2e, "cpu_baseline": cpu,
+            "oracle_parity": parity,
             "gpu_launches": (len(groups) + sum(i["n_launches"] for i, (k, _) in zip(infos, order) if k == "b"))
                             * args.steps,
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
-    barrier(world)
+    return line
 
 
 PRECISION = ("precision: 4x5 grid, depth-4 brickwork of Haar SU(4), depolarising p~U[1e-4,1e-3] on both "

@@ -166,7 +166,10 @@ typedef struct ajf_result {
 /* Create a context on CUDA device `device` (device = -1: a host-only context that validates and
  * plans but cannot run; useful without a GPU). `cuda_stream` is a cudaStream_t that the library
  * borrows (never destroys); NULL makes the library create and own a non-blocking stream.
- * Errors: AJF_E_ARG (out == NULL), AJF_E_CUDA (bad device). */
+ * A device context also looks up the fixed 64 MiB arena of ajf_fidelity_noalloc, which makes the
+ * device reserve it (once per process and device) if it has not already.
+ * Errors: AJF_E_ARG (out == NULL), AJF_E_CUDA (bad device, or the fixed arena cannot be
+ * reserved). */
 ajf_status ajf_create(ajf_ctx **out, int device, void *cuda_stream);
 
 /* Release everything the context owns (device memory it allocated, graphs, its own stream).
@@ -333,6 +336,29 @@ ajf_status ajf_slice_count(const ajf_ctx *ctx, int64_t *n);
  * host-only context), AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT. */
 ajf_status ajf_alg2_slice_range(ajf_ctx *ctx, int64_t first, int64_t count, double *S_part);
 
+/* The units that one evaluation of the current plan shards into, and how a rank runs a block of
+ * them (the paper has no counterpart; Sec. IV-A notes the independence of Alg. I's traces):
+ *   AJF_UNITS_KRAUS_SLICES: the Kraus-index slices of a sliced Alg. I plan (opts.alg1_slices); a
+ *     block runs through ajf_alg1_restore (next_slice = first, S = 0) and ajf_alg1_continue, and
+ *     its S is that block's sum of |t_i|^2;
+ *   AJF_UNITS_BOND_SLICES: the 2^n_sliced_bonds bond slices of an Alg. II plan (1 when unsliced);
+ *     a block runs through ajf_alg2_slice_range;
+ *   AJF_UNITS_WHOLE: one unit, the whole evaluation (an Alg. I plan without Kraus slicing, bond
+ *     sliced or not: its per-trace sums of slices are not additive in S, so it does not shard);
+ *     the rank that holds it runs ajf_fidelity.
+ * *kind and *n_units are written; every rank holding the same plan gets the same answer, so the
+ * ranks agree on the split without communicating. Errors: AJF_E_ARG (NULL), AJF_E_STATE (no plan). */
+enum { AJF_UNITS_WHOLE = 0, AJF_UNITS_KRAUS_SLICES = 1, AJF_UNITS_BOND_SLICES = 2 };
+ajf_status ajf_shard_units(const ajf_ctx *ctx, int32_t *kind, int64_t *n_units);
+
+/* Completes an evaluation from its sum S = sum_i |tr(U^dagger E_i)|^2 (Sec. III, "Ease of
+ * calculation": F_J = S / d^2 with d = 2^n_qubits), e.g. after an all-reduce of the ranks' partial
+ * sums: F = S / 4^n and 1 - F = (4^n - S) / 4^n in FP64 (exact scaling by a power of two; the
+ * subtraction is the one rounding), equivalent per Definition 1 (F > 1 - eps; -1 when eps < 0),
+ * traces_done copied. Needs no context and no device.
+ * Errors: AJF_E_ARG (out NULL, n_qubits not in [1, 62], S negative or not finite, eps > 1). */
+ajf_status ajf_fidelity_from_sum(int n_qubits, double S, double eps, int64_t traces_done, ajf_result *out);
+
 /* Alg. II (Sec. IV-B): F_J from the one doubled network. Same contract as ajf_fidelity_alg1,
  * requiring ajf_plan(ctx, 2, ...). */
 ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);
@@ -348,8 +374,10 @@ ajf_status ajf_fidelity_alg2(ajf_ctx *ctx, double eps, ajf_result *out);
  * from the context's host memory and the result is read back synchronously. The context's own
  * arena, CUDA graph and Alg. I trace buffer are not touched (ajf_alg1_traces still returns the
  * last ajf_fidelity_alg1 result).
- * The first call on a device looks up the arena's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture on the device.
+ * The arena's device address is looked up (cudaGetSymbolAddress, with the device current) by
+ * ajf_create for every device context, which is also when the GPU reserves the array, so a
+ * reservation failure surfaces there and this call itself performs no set-up. A context created
+ * before a cudaDeviceReset keeps the old address: create a new context after a reset.
  * All calls on a device share the one arena and it keeps the last call's contents (the call
  * rewrites everything it reads, and zeroes its status words first). Calls whose device work
  * overlaps -- from different threads or different streams of one device -- race on the arena

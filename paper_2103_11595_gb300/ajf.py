@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libajf.so")
 AJF_OK, AJF_E_ARG, AJF_E_NOT_UNITARY, AJF_E_NOT_TP, AJF_E_STATE = 0, 1, 2, 3, 4
 AJF_E_BUDGET, AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT, AJF_E_UNSUPPORTED = 5, 6, 7, 8, 9
 AJF_IDEAL, AJF_IMPL = 0, 1
+AJF_UNITS_WHOLE, AJF_UNITS_KRAUS_SLICES, AJF_UNITS_BOND_SLICES = 0, 1, 2
 AJF_PLANNER_AUTO, AJF_PLANNER_GREEDY, AJF_PLANNER_MINFILL, AJF_PLANNER_LEARNED = 0, 1, 2, 3
 AJF_PREC_F64, AJF_PREC_F32, AJF_PREC_TF32, AJF_PREC_TF32X3, AJF_PREC_BF16X3, AJF_PREC_BF16X6 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"f64": AJF_PREC_F64, "f32": AJF_PREC_F32, "tf32": AJF_PREC_TF32, "tf32x3": AJF_PREC_TF32X3,
@@ -117,6 +118,8 @@ def lib() -> ctypes.CDLL:
             "ajf_autotune_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32)]),
             "ajf_planned_alg": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
             "ajf_slice_count": (I32, [P, ctypes.POINTER(I64)]),
+            "ajf_shard_units": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
+            "ajf_fidelity_from_sum": (I32, [ctypes.c_int, D, D, I64, ctypes.POINTER(Result)]),
             "ajf_check_plan": (I32, [P]),
             "ajf_selftest_check_plan": (I32, [P, ctypes.c_int]),
             "ajf_alg2_slice_range": (I32, [P, I64, I64, ctypes.POINTER(D)]),
@@ -291,6 +294,23 @@ def ajf_slice_count(ctx) -> int:
     n = ctypes.c_int64()
     _check(ctx, lib().ajf_slice_count(ctx, ctypes.byref(n)))
     return int(n.value)
+
+
+def ajf_shard_units(ctx) -> tuple:
+    """(kind, n_units): how one evaluation of the plan splits into independent units
+    (AJF_UNITS_WHOLE, AJF_UNITS_KRAUS_SLICES or AJF_UNITS_BOND_SLICES)."""
+    k, n = ctypes.c_int32(), ctypes.c_int64()
+    _check(ctx, lib().ajf_shard_units(ctx, ctypes.byref(k), ctypes.byref(n)))
+    return int(k.value), int(n.value)
+
+
+def ajf_fidelity_from_sum(n_qubits: int, S: float, eps: float = -1.0, traces_done: int = 0) -> dict:
+    """F, 1 - F and the decision from S = sum |tr|^2 (no context, no device)."""
+    r = Result()
+    st = lib().ajf_fidelity_from_sum(int(n_qubits), float(S), float(eps), int(traces_done), ctypes.byref(r))
+    if st != AJF_OK:
+        raise AjfError(st, "ajf_fidelity_from_sum: bad arguments")
+    return r.as_dict()
 
 
 def ajf_alg2_slice_range(ctx, first: int, count: int) -> float:

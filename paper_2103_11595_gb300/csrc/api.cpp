@@ -107,10 +107,17 @@ struct ajf_ctx {
   std::vector<int64_t> prog_key;
   bool prog_valid = false;
   int64_t prog_gen = 0;  // bumped whenever a new program is lowered
-  // tensor-core GEMM launches prepared on the host for (program, arena); index = launch index
-  std::vector<ajf::TcPrepared> tc_prep;
-  int64_t tc_prep_gen = -1;
-  char* tc_prep_arena = nullptr;
+  // tensor-core GEMM launches prepared on the host for (program, arena); index = launch index.
+  // One set for the context's own arena, one for the fixed arena of ajf_fidelity_noalloc, so
+  // that alternating the two paths re-encodes nothing.
+  struct TcPrepSet {
+    std::vector<ajf::TcPrepared> prep;
+    int64_t gen = -1;
+    char* arena = nullptr;
+  };
+  TcPrepSet tc_own, tc_static;
+  // device address of the fixed arena of ajf_fidelity_noalloc, resolved by ajf_create
+  char* static_arena = nullptr;
   // profiling
   struct ProfRec {
     cudaEvent_t a, b;
@@ -326,9 +333,10 @@ void drain_profile(ajf_ctx* c) {
 }
 
 // Enqueue the device program: leaves, contraction launches, FP64 final reduction.
-ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
+ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = nullptr) {
   const Program& P = c->prog;
   char* base = c->arena;
+  if (!tc) tc = &c->tc_own;
   void* arena = base;
   const bool f64 = P.f64;
   cudaError_t e;
@@ -345,21 +353,21 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
   int* status = reinterpret_cast<int*>(base + P.off_status);
   // tensor-core GEMM set-up (tensor maps, tiling) is done on the host once per program and arena,
   // outside the timed launches
-  if (c->tc_prep_gen != c->prog_gen || c->tc_prep_arena != base || c->tc_prep.size() != P.launches.size()) {
-    c->tc_prep.assign(P.launches.size(), TcPrepared{});
+  if (tc->gen != c->prog_gen || tc->arena != base || tc->prep.size() != P.launches.size()) {
+    tc->prep.assign(P.launches.size(), TcPrepared{});
     for (size_t i = 0; i < P.launches.size(); ++i) {
       const Launch& ln = P.launches[i];
       if (ln.kind != LK_GEMM_TC) continue;
-      e = tc_gemm_prepare(&c->tc_prep[i], base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<double*>(base + ln.c_off),
+      e = tc_gemm_prepare(&tc->prep[i], base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<double*>(base + ln.c_off),
                           ln.M, ln.N, ln.K, ln.tc_kind, reinterpret_cast<double*>(base + ln.ws_off), ln.ksplit, status,
                           kTcWaitNs, 0);
       if (e != cudaSuccess) {
-        c->tc_prep_gen = -1;
+        tc->gen = -1;
         return cuda_fail(c, e, "tensor-core GEMM set-up");
       }
     }
-    c->tc_prep_gen = c->prog_gen;
-    c->tc_prep_arena = base;
+    tc->gen = c->prog_gen;
+    tc->arena = base;
   }
   for (size_t li = 0; li < P.launches.size(); ++li) {
     const Launch& ln = P.launches[li];
@@ -383,7 +391,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s) {
                              s);
         break;
       case LK_GEMM_TC:
-        e = tc_gemm_run(c->tc_prep[li], s);
+        e = tc_gemm_run(tc->prep[li], s);
         break;
       default:
         e = cudaErrorInvalidValue;
@@ -793,6 +801,17 @@ ajf_status ajf_create(ajf_ctx** out, int device, void* cuda_stream) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return AJF_E_CUDA;
   c->tc_device = prop.major >= 10;
   if (set_kernel_smem_limits() != cudaSuccess) return AJF_E_CUDA;
+  // The fixed arena of ajf_fidelity_noalloc: its module is loaded (and the array reserved) here,
+  // at set-up, so that the no-allocation call itself never triggers the reservation. Looked up
+  // for every context, so a context created after a device reset sees the current address.
+  {
+    void* sa = nullptr;
+    if (static_arena_address(device, &sa) != cudaSuccess) {
+      cudaGetLastError();
+      return AJF_E_CUDA;
+    }
+    c->static_arena = static_cast<char*>(sa);
+  }
   if (cuda_stream) {
     c->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -1459,6 +1478,35 @@ ajf_status ajf_alg2_slice_range(ajf_ctx* c, int64_t first, int64_t count, double
   return run_bonds(c, 2, first, count, S_part);
 }
 
+ajf_status ajf_shard_units(const ajf_ctx* c, int32_t* kind, int64_t* n_units) {
+  if (!c || !kind || !n_units) return AJF_E_ARG;
+  if (!c->planned) return AJF_E_STATE;
+  if (c->alg == 1 && is_sliced(c)) {
+    *kind = AJF_UNITS_KRAUS_SLICES;
+    *n_units = slice_count(c);
+  } else if (c->alg == 2) {
+    *kind = AJF_UNITS_BOND_SLICES;
+    *n_units = int64_t(1) << c->bond_labels.size();
+  } else {
+    *kind = AJF_UNITS_WHOLE;
+    *n_units = 1;
+  }
+  return AJF_OK;
+}
+
+ajf_status ajf_fidelity_from_sum(int n_qubits, double S, double eps, int64_t traces_done, ajf_result* out) {
+  if (!out || n_qubits < 1 || n_qubits > 62 || !std::isfinite(S) || S < 0 || eps > 1.0 || std::isnan(eps))
+    return AJF_E_ARG;
+  const int nsq = 2 * n_qubits;
+  out->S = S;
+  out->F = std::ldexp(S, -nsq);
+  out->one_minus_F = std::ldexp(std::ldexp(1.0, nsq) - S, -nsq);
+  out->traces_done = traces_done;
+  out->equivalent = eps < 0 ? -1 : (out->F > 1.0 - eps ? 1 : 0);
+  out->reserved = 0;
+  return AJF_OK;
+}
+
 ajf_status ajf_fidelity(ajf_ctx* c, double eps, ajf_result* out) {
   if (!c) return AJF_E_ARG;
   if (!c->planned) return fail(c, AJF_E_STATE, "no plan");
@@ -1477,14 +1525,13 @@ ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out
   if (P.arena_bytes > kStaticArenaBytes)
     return fail(c, AJF_E_NOMEM, "plan needs " + std::to_string(P.arena_bytes) + " bytes of device memory; the fixed " +
                                     "arena of ajf_fidelity_noalloc holds " + std::to_string(kStaticArenaBytes) + " bytes");
+  if (!c->static_arena) return fail(c, AJF_E_STATE, "the fixed arena was not resolved when the context was created");
   CUDA_TRY(c, cudaSetDevice(c->device));
-  void* sa = nullptr;
-  CUDA_TRY(c, static_arena_address(c->device, &sa));
   // Run the same device program with the fixed arena as its base; the context's own arena, its
-  // CUDA graph and its profiling state are left untouched.
+  // CUDA graph, its prepared tensor-core launches and its profiling state are left untouched.
   char* const own_arena = c->arena;
   const bool own_profiling = c->profiling;
-  c->arena = static_cast<char*>(sa);
+  c->arena = c->static_arena;
   c->profiling = false;
   ajf_status st = AJF_OK;
   double res[3] = {0, 0, 0};
@@ -1495,7 +1542,7 @@ ajf_status ajf_fidelity_noalloc(ajf_ctx* c, int alg, double eps, ajf_result* out
     e = cudaMemcpyAsync(c->arena + P.off_inputs, c->in.packed.data(), P.input_bytes, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->arena + P.off_status, 0, 16 * sizeof(int32_t), c->stream);
   if (e != cudaSuccess) st = cuda_fail(c, e, "ajf_fidelity_noalloc upload");
-  if (st == AJF_OK) st = enqueue_program(c, c->stream);
+  if (st == AJF_OK) st = enqueue_program(c, c->stream, &c->tc_static);
   if (st == AJF_OK) {
     e = cudaMemcpyAsync(res, c->arena + P.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)

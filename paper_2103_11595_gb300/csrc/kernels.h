@@ -9,7 +9,7 @@ namespace ajf {
 cudaError_t set_kernel_smem_limits();
 
 // Fixed device arena (static_arena.cu) for evaluations that allocate nothing: its size, and its
-// device address on `device`, which must be the current device (looked up once per device).
+// device address on `device`, which must be the current device (cudaErrorInvalidDevice otherwise).
 constexpr size_t kStaticArenaBytes = size_t(64) << 20;
 cudaError_t static_arena_address(int device, void** ptr);
 size_t step_table_bytes(const StepDev& st);

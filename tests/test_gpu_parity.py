@@ -290,9 +290,7 @@ def test_batching_circuit_alg1(precision):
     assert info["n_tc_gemms"] > 0
     err = abs(r["F"] - r64["F"])
     print(f"{precision}: |dF| = {err:.3e}")
-    # the TF32 split keeps 22 of the 24 FP32 mantissa bits; its bound on this Alg. I circuit is
-    # looser than the six-product bf16 split's
-    assert err <= (1e-6 if precision == "bf16x6" else 3e-6)
+    assert err <= TOL[precision]
     for choice in ([0] * 6, [1, 0, 2, 0, 0, 3]):
         idx = 0
         for c in choice:
@@ -337,3 +335,41 @@ def test_replan_same_structure_new_values(use_graph):
             assert info["plan_cached"] == (1 if k > 0 else 0)
             r = ajf.ajf_fidelity_alg2(c.handle)
             assert abs(r["F"] - dense.fidelity(inst)["F"]) <= 1e-12
+
+
+# --------------------------------------------------------------------------- reduced precision vs the oracle
+
+_ORACLE_F = {}
+
+
+def _oracle_alg2(key, make):
+    """The oracle's F_J and 1 - F_J (doubled network, min-fill order, complex128), once per input."""
+    if key not in _ORACLE_F:
+        _ORACLE_F[key] = network.alg2_fidelity(make(), order="minfill")
+    return _ORACLE_F[key]
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "tf32x3"])
+@pytest.mark.parametrize("seed", [4, 10, 29, 36])
+def test_batching_alg1_tensor_cores_vs_oracle(seed, precision):
+    """Batching workload circuits with n <= 16 (6 depolarising noises, 4096 traces): Alg. I on the
+    tensor cores against the oracle's F_J directly (Sec. III: F_J = sum |tr|^2 / d^2), within the
+    FP32-accumulated tolerance, and 1 - F_J to 1e-3 relative."""
+    inst = W.batching_circuit(seed)
+    assert inst.n <= 16
+    ref = _oracle_alg2(("batch", seed), lambda: W.batching_circuit(seed))
+    r, _, info = run(inst, 1, precision, trials=8)
+    assert info["n_tc_gemms"] > 0
+    print(f"seed {seed} {precision}: |dF| = {abs(r['F'] - ref['F']):.3e}")
+    check(r, ref, TOL[precision])
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_mid_bench_seeds_bf16x6_vs_oracle(seed):
+    """Every instance the bench times (mid workload, seeds 0-9, Alg. II, bf16x6, the bench's 32
+    planner restarts) against the oracle's own network contraction."""
+    ref = _oracle_alg2(("mid", seed), lambda: W.mid(seed))
+    r, _, info = run(W.mid(seed), 2, "bf16x6", trials=32)
+    assert info["n_tc_gemms"] > 0
+    print(f"mid seed {seed}: |dF| = {abs(r['F'] - ref['F']):.3e}")
+    check(r, ref, TOL["bf16x6"])

@@ -295,3 +295,126 @@ def test_gate_qubit_order_matters():
     impl = [W.Gate((0,), W.H), W.Gate((1, 0), W.CX), W.Gate((1,), W.T)]
     inst = W.Instance(2, ideal, [], impl=impl)
     assert _all_forms(inst) == pytest.approx(1 / 16, abs=1e-14)
+
+
+# --------------------------------------------------------------------------- one-operation wires
+
+
+def _count_self_traces(monkeypatch):
+    """Wrap the oracle's self-trace so a test can assert that a repeated label was really summed."""
+    calls = {"n": 0}
+    real = network._self_trace
+
+    def counting(arr, labels):
+        calls["n"] += len(labels) - len(set(labels))
+        return real(arr, labels)
+
+    monkeypatch.setattr(network, "_self_trace", counting)
+    return calls
+
+
+def _random_kraus(rng, a, weights):
+    """A Kraus set of unequal, non-symmetric operators: sqrt(w) times Haar unitaries."""
+    return np.stack([W.haar_unitary(rng, 2 ** a) * math.sqrt(w) for w in weights])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_noise_on_gate_free_qubit(seed, monkeypatch):
+    """A noise on a qubit that no gate touches: its wire holds one operation, whose output closes
+    onto its own input, so each term is tr(K_k) (Sec. IV, the trace closes every wire). With the
+    gates cancelling on the other qubits, F_J = sum_k |tr K_k|^2 / 4 (a single noise anywhere)."""
+    rng = np.random.default_rng(40 + seed)
+    gates = [W.Gate((0,), W.haar_unitary(rng, 2)) for _ in range(3)]
+    kr = _random_kraus(rng, 1, (0.5, 0.3, 0.2))
+    inst = W.Instance(2, gates, [W.Noise(1, (1,), kr)])
+    expect = sum(abs(np.trace(K)) ** 2 for K in kr) / 4
+    calls = _count_self_traces(monkeypatch)
+    assert _all_forms(inst) == pytest.approx(expect, abs=1e-13)
+    assert calls["n"] > 0
+
+
+@pytest.mark.parametrize("busy", [False, True])
+def test_two_qubit_noise_on_idle_wires(busy, monkeypatch):
+    """A 2-qubit noise whose two wires (or one of them, `busy`) carry no other operation: one
+    tensor closes onto itself on both label pairs (or on one, a partial trace). F_J must be the
+    single-noise closed form sum_k |tr K_k|^2 / 16 for a non-symmetric Kraus set, so pairing an
+    output with the wrong input, or a missing sum, fails."""
+    rng = np.random.default_rng(7)
+    kr = _random_kraus(rng, 2, (0.6, 0.4))
+    gates = [W.Gate((0,), W.haar_unitary(rng, 2)), W.Gate((0,), W.haar_unitary(rng, 2))]
+    if busy:
+        gates.append(W.Gate((1,), W.haar_unitary(rng, 2)))
+        nz = W.Noise(2, (1, 2), kr)
+    else:
+        nz = W.Noise(1, (1, 2), kr)
+    inst = W.Instance(3, gates, [nz])
+    expect = sum(abs(np.trace(K)) ** 2 for K in kr) / 16
+    calls = _count_self_traces(monkeypatch)
+    assert _all_forms(inst) == pytest.approx(expect, abs=1e-13)
+    assert calls["n"] > 0
+
+
+def test_one_operation_implementation_wire(monkeypatch):
+    """Problem 1 allows an implementation that differs from U. Here the ideal circuit leaves
+    qubit 1 idle and the implementation puts one gate G there: that wire is G alone, closed onto
+    itself (tr G in Alg. I; tr G and tr G^* on q, q' in Alg. II), so
+    F_J = |tr G|^2 / 4 * (1 - 3p/4) with a depolarising noise on qubit 0."""
+    rng = np.random.default_rng(3)
+    u = W.haar_unitary(rng, 2)
+    g = W.haar_unitary(rng, 2)
+    p = 0.2
+    ideal = [W.Gate((0,), u)]
+    impl = [W.Gate((0,), u), W.Gate((1,), g)]
+    inst = W.Instance(2, ideal, [W.Noise(0, (0,), W.depolarising(p))], impl=impl)
+    expect = abs(np.trace(g)) ** 2 / 4 * (1 - 0.75 * p)
+    calls = _count_self_traces(monkeypatch)
+    assert _all_forms(inst) == pytest.approx(expect, abs=1e-13)
+    assert calls["n"] > 0
+
+
+def _wrong_pair_self_trace(arr, labels):
+    """Planted mistake: with two repeated labels, trace each first occurrence against the OTHER
+    label's second occurrence."""
+    pos = {}
+    for i, x in enumerate(labels):
+        pos.setdefault(x, []).append(i)
+    dups = [v for v in pos.values() if len(v) == 2]
+    if len(dups) < 2:
+        return network._real_self_trace(arr, labels)
+    (i1, j1), (i2, j2) = dups[0], dups[1]
+    pairs = [(i1, j2), (i2, j1)]
+    keep = [k for k in range(len(labels)) if k not in (i1, j1, i2, j2)]
+    letters = "abcdefghijklmnopqrstuvwxyz"
+    sub = [letters[k] for k in range(len(labels))]
+    for a, b in pairs:
+        sub[b] = sub[a]
+    out = "".join(sub[k] for k in keep)
+    return np.einsum("".join(sub) + "->" + out, arr), [labels[k] for k in keep]
+
+
+def _no_sum_self_trace(arr, labels):
+    """Planted mistake: keep only the diagonal element 0 of a repeated label instead of summing."""
+    seen = {}
+    for i, x in enumerate(labels):
+        if x in seen:
+            j0 = seen[x]
+            idx = [slice(None)] * arr.ndim
+            idx[j0] = 0
+            idx[i] = 0
+            return _no_sum_self_trace(arr[tuple(idx)], [y for k, y in enumerate(labels) if k not in (j0, i)])
+        seen[x] = i
+    return arr, labels
+
+
+@pytest.mark.parametrize("mistake", [_wrong_pair_self_trace, _no_sum_self_trace], ids=["wrong_pair", "no_sum"])
+def test_planted_mistake_self_trace(mistake, monkeypatch):
+    """A self-trace that pairs the wrong axes or drops the sum must fail the idle-wire pin."""
+    rng = np.random.default_rng(7)
+    kr = _random_kraus(rng, 2, (0.6, 0.4))
+    gates = [W.Gate((0,), W.haar_unitary(rng, 2)), W.Gate((0,), W.haar_unitary(rng, 2))]
+    inst = W.Instance(3, gates, [W.Noise(1, (1, 2), kr)])
+    expect = sum(abs(np.trace(K)) ** 2 for K in kr) / 16
+    assert network.alg1_fidelity(inst)["F"] == pytest.approx(expect, abs=1e-13)
+    monkeypatch.setattr(network, "_real_self_trace", network._self_trace, raising=False)
+    monkeypatch.setattr(network, "_self_trace", mistake)
+    assert network.alg1_fidelity(inst)["F"] != pytest.approx(expect, abs=1e-6)

@@ -87,6 +87,78 @@ def test_slice_counts_of_plans():
         assert e.value.status == ajf.AJF_E_STATE
 
 
+def test_shard_units_of_plans():
+    """ajf_shard_units: Kraus slices for a sliced Alg. I plan, bond slices for Alg. II, and the
+    whole evaluation as one unit for an Alg. I plan without Kraus slices (bond sliced or not)."""
+    with ajf.Context(-1) as c:
+        ajf.load_instance(c.handle, W.tiny(0))
+        ajf.ajf_plan(c.handle, 1, trials=2)
+        assert ajf.ajf_shard_units(c.handle) == (ajf.AJF_UNITS_WHOLE, 1)
+        ajf.ajf_plan(c.handle, 1, trials=2, slice_bonds=2)
+        assert ajf.ajf_shard_units(c.handle) == (ajf.AJF_UNITS_WHOLE, 1)
+        ajf.ajf_plan(c.handle, 1, trials=2, alg1_slices=2)
+        assert ajf.ajf_shard_units(c.handle) == (ajf.AJF_UNITS_KRAUS_SLICES, 16)
+        ajf.ajf_plan(c.handle, 2, trials=2, slice_bonds=3)
+        assert ajf.ajf_shard_units(c.handle) == (ajf.AJF_UNITS_BOND_SLICES, 8)
+        ajf.ajf_plan(c.handle, 2, trials=2)
+        assert ajf.ajf_shard_units(c.handle) == (ajf.AJF_UNITS_BOND_SLICES, 1)
+        # every rank derives the same split: the whole Alg. I evaluation lands on rank 0 alone
+        ajf.ajf_plan(c.handle, 1, trials=2, slice_bonds=2)
+        assert [sharded.rank_work(c.handle, r, 3) for r in range(3)] == [(0, 0, 1), (0, 1, 0), (0, 1, 0)]
+
+
+def test_fidelity_from_sum():
+    """F = S / 4^n and 1 - F = (4^n - S) / 4^n in FP64, Definition 1's decision, argument checks."""
+    r = ajf.ajf_fidelity_from_sum(2, 15.5, eps=0.05, traces_done=7)
+    assert r["F"] == 15.5 / 16 and r["one_minus_F"] == 0.5 / 16 and r["S"] == 15.5
+    assert r["equivalent"] == 1 and r["traces_done"] == 7
+    assert ajf.ajf_fidelity_from_sum(2, 15.0, eps=0.05)["equivalent"] == 0
+    assert ajf.ajf_fidelity_from_sum(2, 15.0)["equivalent"] == -1
+    # 1 - F keeps the digits that S / 4^n rounds away near F = 1
+    n = 20
+    S = 4.0 ** n - 3.0
+    assert ajf.ajf_fidelity_from_sum(n, S)["one_minus_F"] == 3.0 / 4.0 ** n
+    for bad in ((0, 1.0), (63, 1.0), (2, -1.0), (2, float("nan")), (2, float("inf"))):
+        with pytest.raises(ajf.AjfError):
+            ajf.ajf_fidelity_from_sum(*bad)
+    with pytest.raises(ajf.AjfError):
+        ajf.ajf_fidelity_from_sum(2, 1.0, eps=1.5)
+
+
+def _whole_unit_rank(rank, world, port, out):
+    """A rank holding an Alg. I plan without Kraus slices (host-only context): it must reach the
+    all-reduce whatever its block is, with the device run replaced by an exact stand-in S."""
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    with ajf.Context(-1) as c:
+        ajf.load_instance(c.handle, W.tiny(0))
+        ajf.ajf_plan(c.handle, 1, trials=2)
+        kind, first, count = sharded.rank_work(c.handle, rank, world)
+        ajf.ajf_fidelity = lambda h, eps=-1.0: {"S": 60.0}   # stand-in for the device evaluation
+        res = sharded.sharded_fidelity(c.handle, 3, rank, world)
+    out.put((rank, (kind, first, count), res))
+    dist.destroy_process_group()
+
+
+def test_unsliced_alg1_plan_over_two_gloo_ranks():
+    """An Alg. I plan without Kraus slices is one unit: rank 0 runs it, rank 1 contributes 0, and
+    both ranks return the same F (no rank stops short of the all-reduce)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_whole_unit_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == (ajf.AJF_UNITS_WHOLE, 0, 1) and res[1][1] == (ajf.AJF_UNITS_WHOLE, 1, 0)
+    for _, _, r in res:
+        assert r["S"] == 60.0 and r["F"] == 60.0 / 64 and r["one_minus_F"] == 4.0 / 64
+
+
 # --------------------------------------------------------------------------- GPU
 
 
@@ -107,9 +179,7 @@ def _sharded(inst, alg, world, precision="f64", **plan):
             ajf.load_instance(c.handle, inst)
             ajf.ajf_plan(c.handle, alg, trials=4, precision=precision, **plan)
             parts.append(sharded.partial_S(c.handle, r, world))
-    total = sum(parts)
-    d2 = 4.0 ** inst.n
-    return {"S": total, "F": total / d2, "one_minus_F": (d2 - total) / d2}
+    return ajf.ajf_fidelity_from_sum(inst.n, sum(parts))
 
 
 @pytest.mark.gpu
@@ -142,6 +212,19 @@ def test_alg1_kraus_slices_sharded(gpu, world):
     ref = dense.fidelity(inst)
     r = _sharded(inst, 1, world, alg1_slices=2)
     assert abs(r["F"] - ref["F"]) <= 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("slice_bonds", [0, 2])
+def test_alg1_whole_unit_sharded(gpu, slice_bonds):
+    """An Alg. I plan without Kraus slices (unsliced, or bond sliced) over two ranks: rank 0 runs
+    the whole evaluation, rank 1 contributes 0, and F_J equals the oracle's."""
+    from oracle import dense
+    inst = W.random_small(8, n=4, n_gates=14, n_noises=3)
+    ref = dense.fidelity(inst)
+    r = _sharded(inst, 1, 2, slice_bonds=slice_bonds)
+    assert abs(r["F"] - ref["F"]) <= 1e-12
+    assert abs(r["one_minus_F"] - ref["one_minus_F"]) <= 1e-12
 
 
 @pytest.mark.gpu
