@@ -446,11 +446,23 @@ ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
 ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t N, int64_t K, const void *A,
                              const void *B, double *C);
 
+/* Self-test of one real product through the path's own operand preparation and tensor-core GEMM
+ * (no paper counterpart; used by the test suite): C[M][N] = A[M][K] . B[N][K]^T for FP64 A and B
+ * (row-major, host memory), on device `device`, in precision mode `precision` (AJF_PREC_TF32,
+ * _TF32X3, _BF16X3 or _BF16X6). A and B enter as complex tensors with zero imaginary part; the
+ * gather splits them into the mode's operand terms (the leading term quantised per row and
+ * K block) and the GEMM forms the product as it does in a contraction step. M, N, K: powers of
+ * two with M >= 16, N >= 16, K >= 8. C receives M * N doubles. The call allocates and frees its
+ * own device memory and synchronises the device.
+ * Errors: AJF_E_ARG, AJF_E_UNSUPPORTED (shape), AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT. */
+ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t N, int64_t K, const double *A,
+                                   const double *B, double *C);
+
 /* Self-test of the FP32 -> FP64 conversion that the tensor-core GEMM epilogue runs on the integer
  * pipe (no paper counterpart; used by the test suite). On device `device`, for each of the n
  * floats x of `in`, out receives the double x * s, where s = 1 + q * 2^-46 with
- * q = round((scale - 1) * 2^46) -- the form in which the epilogue applies its de-biasing factor;
- * |scale - 1| must be below 2^-10. Normal x: within 2 units in the last place of the exact
+ * q = round((scale - 1) * 2^46); |scale - 1| must be below 2^-10 (the GEMM epilogue uses
+ * scale = 1, an exact conversion). Normal x: within 2 units in the last place of the exact
  * product; zero keeps its sign; subnormal, infinite and NaN x as the hardware x * s.
  * in and out are host memory; the call allocates and frees its own device memory and
  * synchronises the device. Errors: AJF_E_ARG (NULL pointer, n < 0, scale), AJF_E_NOMEM,

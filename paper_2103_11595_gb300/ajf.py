@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
             "ajf_selftest_convert": (I32, [ctypes.c_int, P, P, I64, D]),
+            "ajf_selftest_split_gemm": (I32, [ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_selftest_wait_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
             "ajf_learned_param_count": (I32, []),
             "ajf_set_learned_model": (I32, [P, P, I32]),
@@ -364,6 +365,19 @@ def ajf_selftest_gemm(device: int, kind: int, A: np.ndarray, B: np.ndarray, M: i
     st = lib().ajf_selftest_gemm(device, kind, npass, M, N, K, _ptr(A), _ptr(B), _ptr(C))
     if st != AJF_OK:
         raise AjfError(st, "ajf_selftest_gemm failed")
+    return C
+
+
+def ajf_selftest_split_gemm(device: int, precision: str, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """A @ B.T (FP64 in, FP64 out) through the path's operand split and tensor-core GEMM."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    (M, K), (N, K2) = A.shape, B.shape
+    assert K == K2
+    C = np.empty((M, N), dtype=np.float64)
+    st = lib().ajf_selftest_split_gemm(device, PRECISIONS[precision], M, N, K, _ptr(A), _ptr(B), _ptr(C))
+    if st != AJF_OK:
+        raise AjfError(st, "ajf_selftest_split_gemm failed")
     return C
 
 

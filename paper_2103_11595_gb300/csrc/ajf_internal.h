@@ -106,6 +106,11 @@ void evaluate_path(const Network& net, Path& path, const PlanParams& p);
 Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature);
 Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed);
 Path plan_learned(const Network& net, const PlanParams& p, uint64_t seed, bool* used);
+// Subtree reconfiguration: every merge's subtree, cut at up to 8 inputs, is replaced by the
+// cheapest binary tree over those inputs (dynamic programming over subsets, evaluate_path's cost
+// model) when that is cheaper; `passes` sweeps over the forest. The result computes the same
+// tensors at the roots.
+Path reconfigure_path(const Network& net, const Path& path, const PlanParams& p, int passes);
 // Bond slicing. choose_slice_labels: `count` closed labels to fix, picked greedily on `path` so
 // that the widest tensors shrink first (labels whose removal would leave a leaf without labels
 // are never picked). slice_network: the network with those labels removed from its leaves

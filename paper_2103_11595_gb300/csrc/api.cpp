@@ -10,6 +10,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <memory>
 #include <mutex>
 #include <map>
@@ -144,6 +145,37 @@ struct ajf_ctx {
 };
 
 namespace {
+
+// Process-wide cache of planned paths, keyed by the structural plan key (bounded, oldest out).
+struct SharedPaths {
+  std::mutex m;
+  std::map<std::vector<int64_t>, Path> paths;
+  std::deque<std::vector<int64_t>> order;
+};
+constexpr size_t kSharedPathsMax = 512;
+SharedPaths& shared_paths() {
+  static SharedPaths sp;
+  return sp;
+}
+bool shared_path_lookup(const std::vector<int64_t>& key, Path* out) {
+  SharedPaths& sp = shared_paths();
+  std::lock_guard<std::mutex> lock(sp.m);
+  auto it = sp.paths.find(key);
+  if (it == sp.paths.end()) return false;
+  *out = it->second;
+  return true;
+}
+void shared_path_store(const std::vector<int64_t>& key, const Path& path) {
+  SharedPaths& sp = shared_paths();
+  std::lock_guard<std::mutex> lock(sp.m);
+  if (sp.paths.count(key)) return;
+  sp.paths.emplace(key, path);
+  sp.order.push_back(key);
+  while (sp.order.size() > kSharedPathsMax) {
+    sp.paths.erase(sp.order.front());
+    sp.order.pop_front();
+  }
+}
 
 ajf_status fail(ajf_ctx* c, ajf_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -1066,7 +1098,14 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     try {
       if (!cached) {
         c->path_valid = false;
-        c->path_full = plan_path(full, pp);
+        // process-wide cache: every context planning the same structure with the same options
+        // gets the same path (the planners are deterministic given their seed); learned plans
+        // depend on the context's model and are not shared
+        const bool shared = o.planner != AJF_PLANNER_LEARNED;
+        if (!shared || !shared_path_lookup(key, &c->path_full)) {
+          c->path_full = plan_path(full, pp);
+          if (shared) shared_path_store(key, c->path_full);
+        }
         c->plan_key = key;
         c->path_valid = true;
       }
@@ -1653,6 +1692,100 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
   if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
   if (st == AJF_OK && (cudaMemcpy(C, d + off_c, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
                        cudaMemcpy(&status, d + off_s, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && status != 0) st = AJF_E_TIMEOUT;
+  cudaFree(d);
+  return st;
+}
+
+ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t N, int64_t K, const double* A,
+                                   const double* B, double* C) {
+  if (!A || !B || !C) return AJF_E_ARG;
+  int mode = 0, terms = 0;
+  switch (precision) {
+    case AJF_PREC_TF32: mode = OPM_TF32; terms = 1; break;
+    case AJF_PREC_TF32X3: mode = OPM_TF32X2; terms = 2; break;
+    case AJF_PREC_BF16X3: mode = OPM_BF16X2; terms = 2; break;
+    case AJF_PREC_BF16X6: mode = OPM_BF16X3; terms = 3; break;
+    default: return AJF_E_ARG;
+  }
+  auto log2i = [](int64_t x) {
+    int b = 0;
+    while ((int64_t(1) << b) < x) ++b;
+    return (int64_t(1) << b) == x ? b : -1;
+  };
+  const int mb = log2i(M), nb = log2i(N), kb = log2i(K);
+  if (mb < 4 || nb < 4 || kb < 3 || mb + kb > 30 || nb + kb > 30) return AJF_E_UNSUPPORTED;
+  const int kind = mode >= OPM_BF16X2 ? 1 : 0;
+  const int64_t Mt = 2 * M, Kt = 2 * K;
+  if (!tc_gemm_supported(Mt, N, Kt, kind)) return AJF_E_UNSUPPORTED;
+  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
+  const size_t eb = kind == 1 ? 2 : 4;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  // device layout: A and B as planar complex FP64 (imaginary planes zero), operand terms, C,
+  // K-split workspace, status word
+  const size_t a_src = 0, b_src = al(2 * size_t(M) * K * 8);
+  const size_t x0 = b_src + al(2 * size_t(N) * K * 8);
+  const size_t xbytes = al(size_t(Mt) * Kt * eb), ybytes = al(size_t(N) * Kt * eb);
+  const size_t y0 = x0 + terms * xbytes;
+  const size_t c_off = y0 + terms * ybytes;
+  const int ksplit = tc_gemm_splits(Mt, N, Kt, kind);
+  const size_t cbytes = al(size_t(Mt) * N * 8);
+  const size_t w_off = c_off + cbytes, s_off = w_off + (ksplit > 1 ? ksplit * cbytes : 0);
+  const size_t p_off = s_off + 256, total = p_off + al(2 * sizeof(PermDev));
+  char* d = nullptr;
+  if (cudaMalloc(&d, total) != cudaSuccess) return AJF_E_NOMEM;
+  std::vector<PermDev> pd(2);
+  std::memset(pd.data(), 0, 2 * sizeof(PermDev));
+  for (int side = 0; side < 2; ++side) {
+    PermDev& q = pd[side];
+    const int rb = side == 0 ? mb : nb;
+    q.src = static_cast<int64_t>((side == 0 ? a_src : b_src) / 8);
+    q.plane = (int64_t(1) << rb) * K;
+    q.rows.nbits = rb;
+    for (int i = 0; i < rb; ++i) q.rows.pos[i] = static_cast<int8_t>(kb + i);
+    q.cols.nbits = kb;
+    for (int i = 0; i < kb; ++i) q.cols.pos[i] = static_cast<int8_t>(i);
+    q.rbits = rb;
+    q.kbits = kb;
+    q.embed = side == 0 ? 1 : 0;
+    q.rows_fast = 0;
+    q.mode = mode;
+    for (int t = 0; t < 3; ++t)
+      q.dst[t] = static_cast<int64_t>((side == 0 ? x0 + t * xbytes : y0 + t * ybytes));
+  }
+  ajf_status st = AJF_OK;
+  std::vector<double> planar(2 * size_t(std::max(M, N)) * K, 0.0);
+  auto upload = [&](const double* src, int64_t rows, size_t off) {
+    std::fill(planar.begin(), planar.end(), 0.0);
+    std::memcpy(planar.data(), src, size_t(rows) * K * sizeof(double));
+    return cudaMemcpy(d + off, planar.data(), 2 * size_t(rows) * K * sizeof(double), cudaMemcpyHostToDevice);
+  };
+  if (upload(A, M, a_src) != cudaSuccess || upload(B, N, b_src) != cudaSuccess ||
+      cudaMemcpy(d + p_off, pd.data(), 2 * sizeof(PermDev), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d + s_off, 0, 256) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK) {
+    const int64_t tiles = std::max<int64_t>(int64_t(1) << std::max(0, mb + kb - 10), int64_t(1) << std::max(0, nb + kb - 10));
+    const size_t smem = std::max(perm_table_bytes(pd[0]), perm_table_bytes(pd[1]));
+    if (launch_perm(reinterpret_cast<const PermDev*>(d + p_off), 2, static_cast<int>(std::min<int64_t>(tiles, 2048)),
+                    smem, d, d, false, 0) != cudaSuccess)
+      st = AJF_E_CUDA;
+  }
+  int64_t ao[6] = {0, 0, 0, 0, 0, 0}, bo[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = 0; t < terms; ++t) {
+    ao[t] = static_cast<int64_t>(x0 + t * xbytes);
+    bo[t] = static_cast<int64_t>(y0 + t * ybytes);
+  }
+  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, terms, reinterpret_cast<double*>(d + c_off), Mt, N, Kt, kind,
+                                     reinterpret_cast<double*>(d + w_off), ksplit, reinterpret_cast<int*>(d + s_off),
+                                     0) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
+  int status = 0;
+  // the first M rows of C' = [[A, 0], [0, A]] [B | 0]^T hold A . B^T
+  if (st == AJF_OK && (cudaMemcpy(C, d + c_off, size_t(M) * N * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(&status, d + s_off, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
     st = AJF_E_CUDA;
   if (st == AJF_OK && status != 0) st = AJF_E_TIMEOUT;
   cudaFree(d);

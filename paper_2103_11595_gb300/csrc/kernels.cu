@@ -431,8 +431,33 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Two consecutive operand elements (idx even) with one vector store per split term.
-__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, double v0, double v1) {
+// Split operand modes make their leading term a fixed-point number: an integer multiple of
+// q = 2^qexp with |x_0 / q| <= 2^kLeadBits, q fixed per operand row and 128-byte K block (64 bf16
+// or 32 TF32 elements). Then every product of leading terms within one K block is a multiple of
+// q_a q_b below 2^(2 kLeadBits) q_a q_b, and their block sum -- 64 products of at most 2^16, or 32
+// of at most 2^18 -- stays below 2^24 q_a q_b, so the tensor core's FP32 accumulation of the leading
+// product is exact (it truncates nothing). The remainder x - x_0 (exact in FP32, |.| <= q/2) is
+// split into the correction terms in floating point as usual.
+__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_TF32X2 || mode >= OPM_BF16X2; }
+__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_TF32X2 ? 9 : 8; }
+
+// qexp for a row block whose largest magnitude is m: q = 2^(floor(log2 m) + 1 - lead bits), so
+// that m / q < 2^lead bits; clamped to the normal FP32 range (zero blocks take the floor).
+__device__ __forceinline__ int quantum_exp(float m, int lead) {
+  const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xFFu) - 127;  // floor(log2 m), m normal
+  const int qe = e + 1 - lead;
+  return qe < -126 ? -126 : qe;
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float(static_cast<uint32_t>(127 + e) << 23); }
+
+// Leading term of x: rint(x / q) q, exact (power-of-two scalings of a float with |x / q| < 2^9).
+__device__ __forceinline__ float lead_term(float x, int qexp) { return rintf(x * pow2f(-qexp)) * pow2f(qexp); }
+
+// Two consecutive operand elements (idx even, same row and K block) with one vector store per
+// split term. qexp: the block's quantum (split modes only).
+__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, double v0, double v1,
+                                               int qexp) {
   switch (p.mode) {
     case OPM_F64:
       *reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx) = make_double2(v0, v1);
@@ -447,7 +472,7 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
       break;
     case OPM_TF32X2: {
       const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
-      const float h0 = to_tf32(x0), h1 = to_tf32(x1);
+      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(h0, h1);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[1]) + idx) =
           make_float2(to_tf32(x0 - h0), to_tf32(x1 - h1));
@@ -455,21 +480,21 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
     }
     case OPM_BF16X2: {
       const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
-      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-      const float2 hf = __bfloat1622float2(h);
-      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
+      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) =
+          __floats2bfloat162_rn(h0, h1);
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) =
-          __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+          __floats2bfloat162_rn(x0 - h0, x1 - h1);
       break;
     }
     default: {  // OPM_BF16X3
       const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
-      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-      const float2 hf = __bfloat1622float2(h);
-      const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
+      const float r0 = x0 - h0, r1 = x1 - h1;
       const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
       const float2 mf = __bfloat1622float2(m);
-      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) =
+          __floats2bfloat162_rn(h0, h1);
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) = m;
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[2]) + idx) =
           __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
@@ -478,15 +503,18 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
   }
 }
 
-// Tile of 32 rows x 32 k per iteration, 256 threads. The source offsets of the tile's rows and
-// columns are computed once per tile; loads run with lanes along whichever index is contiguous in
-// the source, stores with lanes along k and two elements per vector store.
+// Tile of 32 rows x TK k per iteration, 256 threads; TK = 32, or for bf16 split modes 64 = one
+// 128-byte K block of the operand (the leading-term quantum is fixed per row and block). The
+// source offsets of the tile's rows and columns are computed once per tile; loads run with lanes
+// along whichever index is contiguous in the source, stores with lanes along k and two elements
+// per vector store.
 template <typename T>
 __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
                                               char* __restrict__ base) {
   extern __shared__ int64_t tab[];
-  __shared__ T tre[32][33], tim[32][33];
-  __shared__ int64_t roff[32], koff[32];
+  __shared__ T tre[32][65], tim[32][65];
+  __shared__ int64_t roff[32], koff[64];
+  __shared__ int qre[32], qim[32];
   const PermDev& p = perms[blockIdx.y];
   const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
   int64_t* t_r = tab;
@@ -494,53 +522,87 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   build_table(p.rows, t_r);
   build_table(p.cols, t_k);
   __syncthreads();
+  const bool split = split_mode(p.mode);
+  const int lead = lead_bits(p.mode);
+  // K block of the GEMM in complex k: 64 bf16 or 32 TF32 elements of one plane; with K below
+  // that, one block holds both planes of the row (Re and -Im, or Im and Re, or Re and Im)
+  const int W = (p.mode >= OPM_BF16X2) ? 64 : 32;
   const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
-  const int TK = p.kbits >= 5 ? 32 : (1 << p.kbits);
+  const int TK = p.kbits >= 6 && W == 64 ? 64 : (p.kbits >= 5 ? 32 : (1 << p.kbits));
+  const bool joint = (int64_t(1) << p.kbits) < W;  // the quantum spans both planes
+  const int KW = TK > 32 ? 64 : 32;                // k extent of the thread mapping
   const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
   const int64_t ntr = R / TR, ntk = K / TK;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const T* src = arena + p.src;
   const int64_t ld = 2 * K;
   for (int64_t tile = blockIdx.x; tile < ntr * ntk; tile += gridDim.x) {
     const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
-    if (threadIdx.x < 32) roff[tx] = tx < TR ? lookup(t_r, c_r, r0 + tx) : 0;
-    else if (threadIdx.x < 64) koff[tx] = tx < TK ? lookup(t_k, c_k, k0 + tx) : 0;
+    if (threadIdx.x < 32) roff[threadIdx.x] = threadIdx.x < TR ? lookup(t_r, c_r, r0 + threadIdx.x) : 0;
+    else if (threadIdx.x < 96) koff[threadIdx.x - 32] = threadIdx.x - 32 < TK ? lookup(t_k, c_k, k0 + threadIdx.x - 32) : 0;
     __syncthreads();
-    // the four loads (x 2 planes) of a thread are issued before its shared-memory stores
-    T vr[4], vi[4];
+    // all loads (x 2 planes) of a thread are issued before its shared-memory stores
+    T vr[8], vi[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = ty + 8 * q;
-      const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
-      if (rr < TR && kk < TK) {
-        const int64_t off = roff[rr] + koff[kk];
-        vr[q] = src[off];
-        vi[q] = src[p.plane + off];
+    for (int q = 0; q < 8; ++q) {
+      if (q < KW / 8) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
+        if (rr < TR && kk < TK) {
+          const int64_t off = roff[rr] + koff[kk];
+          vr[q] = src[off];
+          vi[q] = src[p.plane + off];
+        }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = ty + 8 * q;
-      const int rr = p.rows_fast ? tx : i, kk = p.rows_fast ? i : tx;
-      if (rr < TR && kk < TK) {
-        tre[rr][kk] = vr[q];
-        tim[rr][kk] = vi[q];
+    for (int q = 0; q < 8; ++q) {
+      if (q < KW / 8) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
+        if (rr < TR && kk < TK) {
+          tre[rr][kk] = vr[q];
+          tim[rr][kk] = vi[q];
+        }
       }
     }
     __syncthreads();
+    if (split) {
+      // per row: the largest |Re| and |Im| of the tile's k range (as the FP32 values that are
+      // split), one warp per four rows
+      const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+      for (int i = wp; i < TR; i += 8) {
+        float mr = 0.f, mi = 0.f;
+        for (int k = ln; k < TK; k += 32) {
+          mr = fmaxf(mr, fabsf(static_cast<float>(tre[i][k])));
+          mi = fmaxf(mi, fabsf(static_cast<float>(tim[i][k])));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+          mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+        }
+        if (ln == 0) {
+          if (joint) mr = mi = fmaxf(mr, mi);
+          qre[i] = quantum_exp(mr, lead);
+          qim[i] = quantum_exp(mi, lead);
+        }
+      }
+      __syncthreads();
+    }
     const int pairs = TK >> 1;
     for (int w = threadIdx.x; w < TR * pairs; w += blockDim.x) {
       const int i = w / pairs, j = 2 * (w % pairs);
       const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+      const int qr = split ? qre[i] : 0, qi = split ? qim[i] : 0;
       const int64_t r = r0 + i, k = k0 + j;
       if (p.embed) {
-        store_operand2(p, base, r * ld + k, re0, re1);             // (s=0, t=0):  Re
-        store_operand2(p, base, r * ld + K + k, -im0, -im1);       // (s=0, t=1): -Im
-        store_operand2(p, base, (R + r) * ld + k, im0, im1);       // (s=1, t=0):  Im
-        store_operand2(p, base, (R + r) * ld + K + k, re0, re1);   // (s=1, t=1):  Re
+        store_operand2(p, base, r * ld + k, re0, re1, qr);             // (s=0, t=0):  Re
+        store_operand2(p, base, r * ld + K + k, -im0, -im1, qi);       // (s=0, t=1): -Im
+        store_operand2(p, base, (R + r) * ld + k, im0, im1, qi);       // (s=1, t=0):  Im
+        store_operand2(p, base, (R + r) * ld + K + k, re0, re1, qr);   // (s=1, t=1):  Re
       } else {
-        store_operand2(p, base, r * ld + k, re0, re1);
-        store_operand2(p, base, r * ld + K + k, im0, im1);
+        store_operand2(p, base, r * ld + k, re0, re1, qr);
+        store_operand2(p, base, r * ld + K + k, im0, im1, qi);
       }
     }
     __syncthreads();

@@ -19,7 +19,10 @@
 // sum_s max(8 cmacs_s / peak_flops, bytes_s / peak_bw).
 #include <algorithm>
 #include <array>
+#include <bitset>
 #include <chrono>
+#include <functional>
+#include <limits>
 #include <unordered_set>
 #include <cmath>
 #include <cstring>
@@ -442,6 +445,210 @@ Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed) {
   return path;
 }
 
+// ---------------------------------------------------------------- subtree reconfiguration
+//
+// A path is a forest of binary merge trees. For a merge node v, cut its subtree at a frontier of
+// up to kReconfInputs tensors (expanding the largest internal tensor first); every binary tree
+// over those inputs computes the same tensor, out(v). Dynamic programming over subsets of the
+// frontier finds the tree of least estimated time (the cost model of evaluate_path): the labels of
+// the tensor made from a subset S are those of S's inputs that also occur in the rest of the
+// frontier or in out(v). If it beats the current subtree, it replaces it. All merge nodes are
+// visited, a few passes over the forest.
+namespace {
+
+constexpr int kReconfInputs = 8;
+constexpr size_t kReconfCandidates = 64;  // candidate paths that get reconfigured (the best by estimate)
+constexpr int kReconfPasses = 4;
+constexpr int kReconfLabels = 512;
+using LSet = std::bitset<kReconfLabels>;
+
+double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
+  const double c = std::ldexp(1.0, runion);
+  const double bytes = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * p.elem_bytes;
+  return std::max(8.0 * c / p.peak_flops, bytes / p.peak_bw) + 2e-6;
+}
+
+struct Forest {
+  int L = 0;
+  std::vector<int> ca, cb;            // children (-1 for leaves)
+  std::vector<Labels> lab;            // sorted labels of every node
+  std::vector<int> roots;
+};
+
+Forest to_forest(const Network& net, const Path& path) {
+  Forest f;
+  f.L = static_cast<int>(net.leaf_labels.size());
+  for (int i = 0; i < f.L; ++i) {
+    f.ca.push_back(-1);
+    f.cb.push_back(-1);
+    f.lab.push_back(sorted(net.leaf_labels[i]));
+  }
+  for (auto& st : path.steps) {
+    f.ca.push_back(st.a);
+    f.cb.push_back(st.b);
+    f.lab.push_back(sorted(st.out));
+  }
+  f.roots = path.final_ids;
+  return f;
+}
+
+Path from_forest(const Forest& f) {
+  Path out;
+  std::vector<int> id(f.ca.size(), -1);
+  for (int i = 0; i < f.L; ++i) id[i] = i;
+  // post-order, iterative
+  for (int r : f.roots) {
+    std::vector<std::pair<int, bool>> stack{{r, false}};
+    while (!stack.empty()) {
+      auto [v, expanded] = stack.back();
+      stack.pop_back();
+      if (id[v] >= 0) continue;
+      if (!expanded) {
+        stack.push_back({v, true});
+        stack.push_back({f.cb[v], false});
+        stack.push_back({f.ca[v], false});
+      } else {
+        PathStep st;
+        st.a = id[f.ca[v]];
+        st.b = id[f.cb[v]];
+        st.out = f.lab[v];
+        id[v] = f.L + static_cast<int>(out.steps.size());
+        out.steps.push_back(st);
+      }
+    }
+    out.final_ids.push_back(id[r]);
+  }
+  return out;
+}
+
+// One reconfiguration of the subtree at merge node v; true if it was replaced by a cheaper one.
+bool reconfigure_node(Forest& f, int v, const PlanParams& p) {
+  // frontier: expand the internal node with the most labels until kReconfInputs inputs
+  std::vector<int> front{f.ca[v], f.cb[v]};
+  std::vector<int> inner{v};
+  while (static_cast<int>(front.size()) < kReconfInputs) {
+    int best = -1;
+    for (int i = 0; i < static_cast<int>(front.size()); ++i)
+      if (f.ca[front[i]] >= 0 && (best < 0 || f.lab[front[i]].size() > f.lab[front[best]].size())) best = i;
+    if (best < 0) break;
+    const int u = front[best];
+    inner.push_back(u);
+    front[best] = f.ca[u];
+    front.push_back(f.cb[u]);
+  }
+  const int k = static_cast<int>(front.size());
+  if (k < 3) return false;
+  // current cost of the subtree between v and the frontier; every tree over k inputs has k - 1
+  // merges, so only the work part can improve: skip subtrees with under a microsecond of it
+  double cur = 0;
+  for (int u : inner) {
+    int sh = 0;
+    const int ru = static_cast<int>(sym_diff(f.lab[f.ca[u]], f.lab[f.cb[u]], &sh).size()) + sh;
+    cur += step_seconds(static_cast<int>(f.lab[f.ca[u]].size()), static_cast<int>(f.lab[f.cb[u]].size()), ru,
+                        static_cast<int>(f.lab[u].size()), p);
+  }
+  if (cur - 2e-6 * static_cast<double>(inner.size()) < 1e-6) return false;
+  // local label numbering
+  std::unordered_map<int, int> local;
+  auto loc = [&](int x) {
+    auto it = local.find(x);
+    if (it != local.end()) return it->second;
+    const int n = static_cast<int>(local.size());
+    local.emplace(x, n);
+    return n;
+  };
+  std::vector<LSet> in(k);
+  for (int i = 0; i < k; ++i)
+    for (int x : f.lab[front[i]]) {
+      const int l = loc(x);
+      if (l >= kReconfLabels) return false;
+      in[i].set(l);
+    }
+  LSet ext;
+  for (int x : f.lab[v]) {
+    auto it = local.find(x);
+    if (it != local.end()) ext.set(it->second);
+  }
+  const int full = (1 << k) - 1;
+  std::vector<LSet> uni(1 << k);
+  for (int s = 1; s <= full; ++s) {
+    const int low = s & -s;
+    uni[s] = uni[s ^ low] | in[__builtin_ctz(low)];
+  }
+  std::vector<int> rank(1 << k);
+  std::vector<LSet> tl(1 << k);
+  for (int s = 1; s <= full; ++s) {
+    tl[s] = uni[s] & (uni[full ^ s] | ext);
+    rank[s] = static_cast<int>(tl[s].count());
+  }
+  std::vector<double> cost(1 << k, 0.0);
+  std::vector<int> split(1 << k, 0);
+  for (int s = 1; s <= full; ++s) {
+    if ((s & (s - 1)) == 0) continue;  // single input
+    const int low = s & -s;
+    double best = std::numeric_limits<double>::infinity();
+    int bsplit = 0;
+    // s1 contains the lowest input of s; s2 = s ^ s1 nonempty
+    for (int s1 = (s - 1) & s; s1 > 0; s1 = (s1 - 1) & s) {
+      if (!(s1 & low)) continue;
+      const int s2 = s ^ s1;
+      const int ru = static_cast<int>((tl[s1] | tl[s2]).count());
+      const double c = cost[s1] + cost[s2] + step_seconds(rank[s1], rank[s2], ru, rank[s], p);
+      if (c < best) {
+        best = c;
+        bsplit = s1;
+      }
+    }
+    cost[s] = best;
+    split[s] = bsplit;
+  }
+  if (!(cost[full] < cur * (1.0 - 1e-9))) return false;
+  // rebuild: the node for subset s (inputs are frontier nodes, v is the root)
+  std::vector<int> label_of(local.size());
+  for (auto& kv : local) label_of[kv.second] = kv.first;
+  std::function<int(int)> build = [&](int s) -> int {
+    if ((s & (s - 1)) == 0) return front[__builtin_ctz(s)];
+    const int a = build(split[s]), b = build(s ^ split[s]);
+    if (s == full) {
+      f.ca[v] = a;
+      f.cb[v] = b;
+      return v;
+    }
+    Labels lb;
+    for (size_t i = 0; i < label_of.size(); ++i)
+      if (tl[s].test(i)) lb.push_back(label_of[i]);
+    std::sort(lb.begin(), lb.end());
+    f.ca.push_back(a);
+    f.cb.push_back(b);
+    f.lab.push_back(lb);
+    return static_cast<int>(f.ca.size()) - 1;
+  };
+  build(full);
+  return true;
+}
+
+}  // namespace
+
+Path reconfigure_path(const Network& net, const Path& path, const PlanParams& p, int passes) {
+  Forest f = to_forest(net, path);
+  for (int pass = 0; pass < passes; ++pass) {
+    bool changed = false;
+    // visit merge nodes reachable from the roots, largest tensors first
+    Path cur = from_forest(f);
+    Forest g = to_forest(net, cur);
+    std::vector<int> order;
+    for (int v = g.L; v < static_cast<int>(g.ca.size()); ++v) order.push_back(v);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return g.lab[x].size() > g.lab[y].size(); });
+    for (int v : order) changed |= reconfigure_node(g, v, p);
+    f = std::move(g);
+    if (!changed) break;
+  }
+  Path out = from_forest(f);
+  out.planner = path.planner;
+  evaluate_path(net, out, p);
+  return out;
+}
+
 Path plan_path(const Network& net, const PlanParams& p) {
   const int trials = std::max(1, p.trials);
   Path best;
@@ -458,25 +665,35 @@ Path plan_path(const Network& net, const PlanParams& p) {
     empty.planner = p.planner;
     return empty;
   }
+  std::vector<Path> cands;
   if (p.planner == AJF_PLANNER_LEARNED) {
     bool used = false;
     PlanParams q = p;
     for (int t = 0; t < trials; ++t) {
       q.learned_noise = t == 0 ? 0.0 : 0.25;
-      consider(plan_learned(net, q, p.seed * 1000003ull + static_cast<uint64_t>(t), &used));
+      cands.push_back(plan_learned(net, q, p.seed * 1000003ull + static_cast<uint64_t>(t), &used));
       if (!used) break;  // no model: plan_learned returned the greedy path
     }
     // the greedy planner judges: keep the learned path only if it is no worse
-    consider(plan_greedy(net, p, p.seed, 0.0));
-    return best;
+    cands.push_back(plan_greedy(net, p, p.seed, 0.0));
+  } else {
+    // restarts of both planners
+    const bool do_greedy = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_GREEDY;
+    const bool do_minfill = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_MINFILL;
+    for (int t = 0; t < trials; ++t) {
+      const uint64_t s = p.seed * 1000003ull + static_cast<uint64_t>(t);
+      if (do_greedy) cands.push_back(plan_greedy(net, p, s, t == 0 ? 0.0 : (t % 3 == 1 ? 0.5 : 1.0)));
+      if (do_minfill) cands.push_back(plan_minfill(net, p, s));
+    }
   }
-  const bool do_greedy = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_GREEDY;
-  const bool do_minfill = p.planner == AJF_PLANNER_AUTO || p.planner == AJF_PLANNER_MINFILL;
-  for (int t = 0; t < trials; ++t) {
-    const uint64_t s = p.seed * 1000003ull + static_cast<uint64_t>(t);
-    if (do_greedy) consider(plan_greedy(net, p, s, t == 0 ? 0.0 : (t % 3 == 1 ? 0.5 : 1.0)));
-    if (do_minfill) consider(plan_minfill(net, p, s));
-  }
+  // the best candidates are improved by subtree reconfiguration (the cheapest order of every
+  // small subtree); the best path by estimated time is kept
+  std::stable_sort(cands.begin(), cands.end(), [](const Path& x, const Path& y) {
+    return x.est_seconds < y.est_seconds || (x.est_seconds == y.est_seconds && x.cmacs < y.cmacs);
+  });
+  const size_t top = std::min<size_t>(cands.size(), kReconfCandidates);
+  for (size_t i = 0; i < top; ++i) consider(reconfigure_path(net, cands[i], p, kReconfPasses));
+  for (auto& c : cands) consider(std::move(c));
   return best;
 }
 

@@ -4,21 +4,27 @@
 //   C[M][N] (FP64, row-major) = sum_{i + j < T} A_i[M][K] . B_j[N][K]^T
 //
 // A_t and B_t (t < T) are the terms of a split operand -- x = x_0 + x_1 (+ x_2) -- stored
-// K-contiguous (K-major) in TF32 (FP32 containers, pre-rounded) or bf16. T = 1 is a plain
-// one-pass product; T = 2 is the three-product split (hi.hi + hi.lo + lo.hi); T = 3 the
-// six-product split. The complex contraction step arrives here as one real GEMM (the caller
-// embedded the complex operand as [[Re,-Im],[Im,Re]]).
+// K-contiguous (K-major) in TF32 (FP32 containers) or bf16. T = 1 is a plain one-pass product;
+// T = 2 is the three-product split (x_0.y_0 + x_0.y_1 + x_1.y_0); T = 3 the six-product split.
+// The complex contraction step arrives here as one real GEMM (the caller embedded the complex
+// operand as [[Re,-Im],[Im,Re]]).
 //
-// Accuracy. The tensor core's FP32 accumulation truncates toward zero. Measured on GB300 with
+// Accuracy. The tensor core's FP32 accumulation truncates toward zero: measured on GB300 with
 // positive operands, a TMEM accumulation over K drifts by about -(K/8) * 2^-24 relative, far above
-// round-to-nearest FP32. Two measures keep the GEMM at FP32 accuracy:
-//  * promotion: every 128-byte K block is accumulated into a fresh TMEM partial (the block's small
-//    correction products first, while the partial is small, then the four leading-term
-//    instructions), and the epilogue warps add the partials into FP32 registers with
-//    round-to-nearest, so the drift no longer grows with K;
-//  * de-biasing: truncation toward zero shrinks every partial by a factor (1 - e) whatever its sign,
-//    with a mean e per promoted block that was calibrated on GB300 (kBlockBias below), so the
-//    epilogue multiplies the result by (1 + e) once when it stores it.
+// round-to-nearest FP32, and a drift of that kind compounds over the dozens of GEMMs of one
+// contraction. The kernel removes the drift by construction instead of correcting it:
+//  * exact leading product: the operand preparation (k_perm) makes every leading term x_0 an
+//    integer multiple of a power of two q fixed per row and 128-byte K block, with |x_0 / q| <= 2^8
+//    (bf16) or 2^9 (TF32). Within one K block every product x_0 y_0 is then a multiple of q_x q_y of
+//    magnitude <= 2^16 (2^18) q_x q_y, and the block's sum of 64 (32) of them stays below 2^24 q_x q_y:
+//    the TMEM accumulation of the leading product loses no bit at all;
+//  * two partials per K block: the leading product goes into its own fresh TMEM partial P0 (exact),
+//    the correction products (about 2^-8 of it) into a second fresh partial P1, whose truncation
+//    is relative to |P1| and so at most ~2^-31 of the result per instruction;
+//  * promotion: eight epilogue warps add P0 + P1 of every K block into FP32 registers with
+//    round-to-nearest (unbiased), at most kMaxBlocksPerSplit blocks per register sum; longer
+//    contractions are split over K and the FP64 partial tiles summed in a fixed order.
+// No calibrated correction factor is involved; the result is stored as FP32 -> FP64 exactly.
 //
 // Kernel structure (persistent: one CTA per SM walks the 128 x BN output tiles in a grouped
 // raster order; 320 threads; the slot and TMEM-buffer rings continue from tile to tile so the
@@ -27,16 +33,17 @@
 //                    the B tile (BN rows x 128 B), 128-byte swizzle, into a ring of slots
 //                    (mbarrier expect-tx / complete-tx);
 //   warp 1         : allocates TMEM; lane 0 issues tcgen05.mma (M=128, N=BN, 32 B of K each) into
-//                    a ring of TMEM partial buffers and tcgen05.commit to release slots and hand
-//                    partials to the epilogue;
+//                    a ring of TMEM buffers (two partials of BN columns each) and tcgen05.commit
+//                    to release slots and hand partials to the epilogue;
 //   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
 //                    the BN columns of its rows: tcgen05.ld, FP32 round-to-nearest accumulation in
-//                    registers, de-biased FP64 store of the tile (rows < M, columns < N).
+//                    registers, FP64 store of the tile (rows < M, columns < N).
 // Work items are (tile, K split) pairs. GEMMs with fewer tiles than SMs, or with more than
 // kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP64 partial
 // tile to a workspace and k_split_sum adds the splits in a fixed order (deterministic).
 // Every wait is bounded by the global timer (2 s); on expiry the kernel records a status code,
-// stops issuing work, releases TMEM and returns, so the host sees AJF_E_TIMEOUT instead of a hang.
+// stops issuing work, waits (bounded again) for the TMA loads and MMAs it already issued,
+// releases TMEM and returns, so the host sees AJF_E_TIMEOUT instead of a hang.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -68,17 +75,6 @@ constexpr int64_t kPlanSMs = 152;
 constexpr int kMaxTerms = 3;
 constexpr uint32_t kSmemBudget = 192 * 1024;
 constexpr unsigned long long kWaitNs = kTcWaitNs;
-// Mean relative shrink of a promoted K block with all four leading-term instructions (K = 64 bf16
-// or 32 TF32 elements), fitted on GB300 so that F_J of held-out circuits matches the FP64 path
-// (Alg. II of the n = 16 line workload, seeds 100-105, and Alg. I of the batching workload, seeds
-// 1000-1007; the tests and bench use other seeds). Recompute with
-// paper_2103_11595_gb300/calibrate_tc_bias.py. A block whose K holds fewer instructions (K = 16
-// or 32 bf16, 8 or 16 TF32; the rest of the 128-byte row is zero-filled) truncates fewer times at
-// full magnitude: the i-th of n accumulating instructions truncates at about i/n of the block's
-// magnitude, so the shrink scales as (n + 1) / 5 of the four-instruction value.
-// Fitted values: TF32 8.69e-8 +- 0.51e-8, bf16 7.02e-8 +- 0.60e-8 (spread across circuits).
-constexpr double kBlockBiasTF32 = 8.69e-8;
-constexpr double kBlockBiasBF16 = 7.02e-8;
 
 struct TcParams {
   CUtensorMap amap[kMaxTerms];
@@ -86,9 +82,6 @@ struct TcParams {
   double* C;
   int* status;
   int64_t M, N;
-  double scale;                      // de-biasing factor applied at the store
-  int64_t scale_q;                   // the same factor as 1 + scale_q * 2^-46 (integer-pipe store)
-  int32_t scale_int;                 // 1: the store converts on the integer pipe (|scale - 1| < 2^-10)
   int32_t terms, kblocks, ntn, slots, bufs;
   int32_t mtn;                       // tiles along M
   int32_t group;                     // M tiles per raster group (L2 reuse of B tiles)
@@ -203,7 +196,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 template <int BN, bool kBF16>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
-  static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "tile width");
+  static_assert(BN == 32 || BN == 64 || BN == 128, "tile width");
   constexpr int COLS = BN / 2;                       // columns per epilogue thread (one TMEM lane = one row)
   constexpr int CH = COLS < 16 ? COLS : 16;          // columns per drain chunk
   constexpr uint32_t a_bytes = kBM * kRowBytes, b_bytes = BN * kRowBytes;
@@ -211,14 +204,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = p.slots, T = p.terms, NB = p.bufs;
-  const uint32_t ncols = static_cast<uint32_t>(NB * BN) < 32u ? 32u : static_cast<uint32_t>(NB * BN);
+  // TMEM: NB buffers of two partials (P0: leading product, P1: corrections), BN columns each
+  const uint32_t ncols = static_cast<uint32_t>(2 * NB * BN) < 32u ? 32u : static_cast<uint32_t>(2 * NB * BN);
   uint8_t* bars = smem + S * p.slot_bytes;
   const uint32_t full0 = smem_u32(bars);
   const uint32_t empty0 = full0 + 8 * kMaxSlots;
   const uint32_t accf0 = empty0 + 8 * kMaxSlots;  // partial buffer b ready (MMA -> epilogue)
   const uint32_t acce0 = accf0 + 8 * kMaxBufs;    // partial buffer b drained (epilogue -> MMA)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 16 * kMaxBufs);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 4);
+  const uint32_t drain0 = acce0 + 8 * kMaxBufs;   // MMAs issued before an abort have completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 12);
   // persistent tile loop: tile = blockIdx.x, blockIdx.x + gridDim.x, ...; every role walks the
   // same tiles, and its ring positions (slots, TMEM buffers) continue across tiles
   // grouped raster: `group` M tiles sweep the N tiles together, so concurrently running CTAs
@@ -248,6 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       mbar_init(accf0 + 8 * b, 1);
       mbar_init(acce0 + 8 * b, kEpiWarps);
     }
+    mbar_init(drain0, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -266,7 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     // ---- TMA producer: one slot per (K block, term) holds that term's A and B tiles. A block's
     // terms are loaded highest first, the order in which the MMA issuer frees their slots.
     int slot = 0;
-    uint32_t phase = 0;  // position in the slot ring, continued across tiles
+    uint32_t phase = 0;   // position in the slot ring, continued across tiles
+    uint32_t issued = 0;  // slots loaded so far (the last min(issued, S) may still be in flight)
     bool ok = !p.stall_loads;
     for (uint32_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
       int32_t m0, n0;
@@ -285,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           mbar_expect_tx(full0 + 8 * slot, a_bytes + b_bytes);
           tma_load_2d(sa, &p.amap[t], kx, m0, full0 + 8 * slot);
           tma_load_2d(sa + a_bytes, &p.bmap[t], kx, n0, full0 + 8 * slot);
+          ++issued;
           if (++slot == S) {
             slot = 0;
             phase ^= 1u;
@@ -292,9 +290,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         }
       }
     }
+    if (!ok && issued > 0) {
+      // abort: before the CTA releases its shared memory, let the loads already issued land (the
+      // last min(issued, S) slots; earlier ones were consumed), each wait bounded again
+      const uint32_t first = issued > static_cast<uint32_t>(S) ? issued - S : 0u;
+      for (uint32_t i = first; i < issued; ++i) {
+        const uint32_t sl = i % static_cast<uint32_t>(S), ph = (i / static_cast<uint32_t>(S)) & 1u;
+        mbar_wait(full0 + 8 * sl, ph, p.wait_ns, p.status, 15);
+      }
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     bool ok = true;
+    bool any = false;  // MMAs issued (an abort waits for them before TMEM is released)
     int buf = 0, slot = 0;
     uint32_t bphase = 0, phase = 0;  // ring positions, continued across tiles
     for (uint32_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
@@ -339,11 +347,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         const uint64_t ad0 = smem_desc(base + st0 * p.slot_bytes), bd0 = smem_desc(base + st0 * p.slot_bytes + a_bytes);
         const uint64_t ad1 = smem_desc(base + st1 * p.slot_bytes), bd1 = smem_desc(base + st1 * p.slot_bytes + a_bytes);
         const uint64_t ad2 = smem_desc(base + st2 * p.slot_bytes), bd2 = smem_desc(base + st2 * p.slot_bytes + a_bytes);
-        const uint32_t dst = tmem + static_cast<uint32_t>(b * BN);
+        const uint32_t dst0 = tmem + static_cast<uint32_t>(2 * b * BN);  // P0: the leading product alone
+        const uint32_t dst1 = dst0 + static_cast<uint32_t>(BN);          // P1: the correction products
         uint32_t acc = 0;
         // one product A_i . B_j over the block: 4 instructions, 32 bytes of K each (+2 in the
         // descriptor's 16-byte address field)
-        auto product = [&](uint64_t ad, uint64_t bd) {
+        auto product = [&](uint32_t dst, uint64_t ad, uint64_t bd) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             mma<kBF16>(dst, ad + 2 * kk, bd + 2 * kk, p.idesc, acc);
@@ -356,31 +365,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           return w;
         };
         // all of the block's terms are resident before its first MMA (a failed wait then leaves
-        // nothing in flight); correction products (i + j >= 1) go first, smallest first, the
-        // leading product last, and a term's slot is released (commit: freed once the MMAs issued
-        // so far complete) right after its last use
+        // nothing of this block in flight); the correction products go into P1 smallest first, the
+        // leading product into P0, and a term's slot is released (commit: freed once the MMAs
+        // issued so far complete) right after its last use
         const bool got = (T < 3 || arrived(st2, ph2)) && (T < 2 || arrived(st1, ph1)) && arrived(st0, ph0);
         if (!got) {
           ok = false;
           break;
         }
+        any = true;
         if (T == 3) {
-          product(ad0, bd2);
-          product(ad1, bd1);
-          product(ad2, bd0);
+          product(dst1, ad0, bd2);
+          product(dst1, ad1, bd1);
+          product(dst1, ad2, bd0);
           mma_commit(empty0 + 8 * st2);
         }
         if (T >= 2) {
-          product(ad0, bd1);
-          product(ad1, bd0);
+          product(dst1, ad0, bd1);
+          product(dst1, ad1, bd0);
           mma_commit(empty0 + 8 * st1);
         }
-        product(ad0, bd0);
+        acc = 0;
+        product(dst0, ad0, bd0);
         mma_commit(empty0 + 8 * st0);
         mma_commit(accf0 + 8 * b);
       }
     }
-    if (!ok) *abort_flag = 1;
+    if (!ok) {
+      *abort_flag = 1;
+      if (any) {
+        // abort: wait (bounded) until every MMA issued so far has completed, so that none is
+        // still writing TMEM or reading shared memory when they are released
+        mma_commit(drain0);
+        mbar_wait(drain0, 0u, p.wait_ns, p.status, 16);
+      }
+    }
   } else if (warp >= kEpiWarp0) {
     // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP64 per tile
     const int q = warp & 3, h = (warp - kEpiWarp0) >> 2;
@@ -415,37 +434,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t col = static_cast<uint32_t>(b * BN + h * COLS);
+        const uint32_t col = static_cast<uint32_t>(2 * b * BN + h * COLS);
 #pragma unroll
         for (int c0 = 0; c0 < COLS; c0 += CH) {
-          uint32_t r[CH];
+          uint32_t r0[CH], r1[CH];
 #pragma unroll
-          for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + c0 + c1, r + c1);
+          for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + c0 + c1, r0 + c1);
+          if (T > 1) {
+#pragma unroll
+            for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + BN + c0 + c1, r1 + c1);
+          }
           tmem_wait_ld();
+          if (T > 1) {
 #pragma unroll
-          for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+            for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r0[j]);
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(acce0 + 8 * b);
       }
       if (!ok) break;
-      // the MMA warp is already filling the next buffers while this tile is written
-      // FP32 -> scaled FP64 on the integer pipe: at GB300's FP64 rate a hardware conversion and
-      // multiply per element would cost about 8 us per 128 x 128 tile
+      // the MMA warp is already filling the next buffers while this tile is written; FP32 -> FP64
+      // is exact and runs on the integer pipe (GB300's FP64 rate would make a hardware conversion
+      // per element a visible cost of the store)
       if (mine) {
         double2* dstp = reinterpret_cast<double2*>(dbase + row * p.N + col0);
-        if (p.scale_int) {
 #pragma unroll
-          for (int j = 0; j < COLS / 2; ++j)
-            dstp[j] = make_double2(f32_to_f64_scaled(acc[2 * j], p.scale_q, p.scale),
-                                   f32_to_f64_scaled(acc[2 * j + 1], p.scale_q, p.scale));
-        } else {
-#pragma unroll
-          for (int j = 0; j < COLS / 2; ++j)
-            dstp[j] = make_double2(static_cast<double>(acc[2 * j]) * p.scale,
-                                   static_cast<double>(acc[2 * j + 1]) * p.scale);
-        }
+        for (int j = 0; j < COLS / 2; ++j)
+          dstp[j] = make_double2(f32_to_f64_scaled(acc[2 * j], 0, 1.0), f32_to_f64_scaled(acc[2 * j + 1], 0, 1.0));
       }
     }
     if (!ok) *abort_flag = 1;
@@ -454,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   // __syncthreads (bar.sync, the aligned form) must be executed by all threads of a warp
   // together; warps 0 and 1 get here diverged (lane 0 ran the producer / MMA loop, lanes 1-31 came
   // straight through), so they reconverge first. The barrier then orders warp 1's TMEM release
-  // after every epilogue warp's last TMEM read.
+  // after every epilogue warp's last TMEM read and after the abort drains above.
   __syncwarp();
   __syncthreads();
   if (warp == 1) {
@@ -493,20 +513,6 @@ bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// De-biasing factor: 1 + (mean shrink per promoted block) for a GEMM with K elements of K.
-// AJF_TC_BIAS overrides the four-instruction constant (calibration runs set it to 0 and measure
-// the shrink).
-double debias_scale(bool bf16, int64_t K) {
-  static const double forced = [] {
-    const char* e = std::getenv("AJF_TC_BIAS");
-    return e ? std::atof(e) : -1.0;
-  }();
-  const double e4 = forced >= 0 ? forced : (bf16 ? kBlockBiasBF16 : kBlockBiasTF32);
-  const int64_t per_instr = bf16 ? 16 : 8;  // K elements per tcgen05.mma (32 bytes)
-  const int64_t n = K / per_instr >= 4 ? 4 : (K / per_instr < 1 ? 1 : K / per_instr);
-  return 1.0 + e4 * static_cast<double>(n + 1) / 5.0;
-}
-
 // SM count of the current device (queried once per device).
 int sm_count() {
   static int counts[64] = {0};
@@ -528,7 +534,7 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   p.slots = static_cast<int32_t>(kSmemBudget / p.slot_bytes);
   if (p.slots > kMaxSlots) p.slots = kMaxSlots;
   if (p.slots < p.terms) return cudaErrorInvalidValue;
-  p.bufs = 512 / BN > kMaxBufs ? kMaxBufs : 512 / BN;
+  p.bufs = 256 / BN > kMaxBufs ? kMaxBufs : 256 / BN;  // each buffer: 2 partials x BN TMEM columns
   const size_t smem = size_t(p.slots) * p.slot_bytes + 1024 /* barriers */ + 1024 /* alignment */;
   const int64_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt;
@@ -627,11 +633,6 @@ cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, con
   p.status = d_status;
   p.M = M;
   p.N = N;
-  p.scale = debias_scale(bf16, K);
-  if (std::fabs(p.scale - 1.0) < std::ldexp(1.0, -10)) {
-    p.scale_q = std::llround(std::ldexp(p.scale - 1.0, kScaleFracBits));
-    p.scale_int = 1;
-  }
   p.terms = terms;
   p.wait_ns = wait_ns;
   p.stall_loads = stall_loads;

@@ -158,7 +158,7 @@ def test_precision_config_as_written_is_over_budget():
         with pytest.raises(ajf.AjfError) as e:
             ajf.ajf_plan(c.handle, 2, trials=2)
         assert e.value.status == ajf.AJF_E_BUDGET
-        assert e.value.info["width"] >= 64 and e.value.info["cmacs"] > 1e30
+        assert e.value.info["width"] >= 64 and e.value.info["cmacs"] > 1e25
         ajf.load_instance(c.handle, W.precision(0, depth=6))
         with pytest.raises(ajf.AjfError) as e:
             ajf.ajf_plan(c.handle, 2, trials=2, mem_budget_bytes=280e9)

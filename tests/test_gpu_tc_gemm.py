@@ -119,3 +119,58 @@ def test_k_split_gemm(M, N, K, T):
     ref, bound = split_ref(bits_to_f64(A), bits_to_f64(B))
     # per split at most 4096 K elements are summed in FP32; the splits add in FP64
     assert np.all(np.abs(C - ref) <= 4 * 4096 * 2.0 ** -23 * bound + 1e-30)
+
+
+# --------------------------------------------------------------------------- through the operand split
+# ajf_selftest_split_gemm runs the path's own gather (k_perm, which quantises each leading term to
+# a fixed-point multiple of a power of two per row and 128-byte K block) and the tensor-core GEMM.
+
+SPLIT_MODES = ["bf16x6", "tf32x3", "bf16x3"]
+
+
+@pytest.mark.parametrize("precision", SPLIT_MODES)
+@pytest.mark.parametrize("K", [64, 256])
+def test_split_gemm_exact_on_small_integers(precision, K):
+    """Integers |x| <= 127, scaled per row by powers of two: every term and every partial sum is
+    exactly representable, so the whole path (split, exact leading partial, correction partial,
+    FP32 promotion, FP64 store) must return the exact product, bit for bit."""
+    rng = np.random.default_rng(K + len(precision))
+    M, N = 64, 128
+    A = rng.integers(-127, 128, (M, K)).astype(np.float64) * np.exp2(rng.integers(-12, 12, (M, 1)))
+    B = rng.integers(-127, 128, (N, K)).astype(np.float64) * np.exp2(rng.integers(-12, 12, (N, 1)))
+    C = ajf.ajf_selftest_split_gemm(0, precision, A, B)
+    np.testing.assert_array_equal(C, A @ B.T)
+
+
+@pytest.mark.parametrize("precision", SPLIT_MODES)
+@pytest.mark.parametrize("K", [256, 4096, 16384])
+def test_split_gemm_has_no_truncation_bias(precision, K):
+    """Positive operands make a truncating accumulation visible (a plain TMEM sum drifts by about
+    -(K/8) 2^-24 relative). With the leading product accumulated exactly and only the small
+    correction partial truncated, the mean relative error must stay at rounding-noise level
+    (|mean| < 1e-8) for every split mode and K, with no correction factor anywhere."""
+    rng = np.random.default_rng(K)
+    A = rng.random((64, K))
+    B = rng.random((128, K))
+    C = ajf.ajf_selftest_split_gemm(0, precision, A, B)
+    ref = A @ B.T
+    rel = (C - ref) / ref
+    print(f"{precision} K={K}: mean {rel.mean():.2e} max {np.abs(rel).max():.2e}")
+    assert abs(rel.mean()) < 1e-8
+    assert np.abs(rel).max() < {"bf16x6": 1e-6, "tf32x3": 1e-5, "bf16x3": 1e-4}[precision]
+
+
+@pytest.mark.parametrize("precision", SPLIT_MODES)
+@pytest.mark.parametrize("M,N,K", [(64, 64, 64), (128, 512, 1024), (16, 1024, 32), (512, 64, 8192)])
+def test_split_gemm_random_signs(precision, M, N, K):
+    """Random-sign Gaussian operands against the FP64 product: the error is bounded by the split's
+    representation error (relative to each row block's largest entry: 2^-25 for bf16x6, 2^-20 for
+    tf32x3, 2^-17 for bf16x3) plus FP32 round-to-nearest promotion."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = ajf.ajf_selftest_split_gemm(0, precision, A, B)
+    ref = A @ B.T
+    absprod = np.abs(A) @ np.abs(B).T
+    bits = {"bf16x6": 22, "tf32x3": 18, "bf16x3": 15}[precision]
+    assert np.all(np.abs(C - ref) <= 2.0 ** -bits * absprod * 8)
