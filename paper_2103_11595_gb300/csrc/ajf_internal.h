@@ -95,6 +95,7 @@ struct PlanParams {
   double peak_flops = 1e12;   // contraction throughput of the chosen precision (time model)
   double peak_bw = 6.5e12;    // bytes/s
   double elem_bytes = 16;
+  bool tensor_cores = true;   // GEMM-class steps of the TF32 / bf16 modes run on tcgen05
   // learned merge scorer: weights and a batched scoring function (device kernels or host)
   const float* mlp = nullptr;
   std::function<void(const float* w, const float* x, int n, float* out)> scorer;
@@ -102,6 +103,8 @@ struct PlanParams {
 };
 
 Path plan_path(const Network& net, const PlanParams& p);
+// Estimated device time of a step (ranks of the operands, of their union and of the result).
+double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p);
 void evaluate_path(const Network& net, Path& path, const PlanParams& p);
 Path plan_greedy(const Network& net, const PlanParams& p, uint64_t seed, double temperature);
 Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed);

@@ -1071,6 +1071,7 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
     pp.trials = o.trials;
     pp.seed = o.seed;
     pp.elem_bytes = o.precision == AJF_PREC_F64 ? 16 : 8;
+    pp.tensor_cores = c->tc_device;
     switch (o.precision) {
       case AJF_PREC_F64: pp.peak_flops = 1.0e12; break;
       case AJF_PREC_F32: pp.peak_flops = 40e12; break;

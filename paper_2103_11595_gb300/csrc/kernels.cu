@@ -431,15 +431,17 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Split operand modes make their leading term a fixed-point number: an integer multiple of
-// q = 2^qexp with |x_0 / q| <= 2^kLeadBits, q fixed per operand row and 128-byte K block (64 bf16
-// or 32 TF32 elements). Then every product of leading terms within one K block is a multiple of
-// q_a q_b below 2^(2 kLeadBits) q_a q_b, and their block sum -- 64 products of at most 2^16, or 32
-// of at most 2^18 -- stays below 2^24 q_a q_b, so the tensor core's FP32 accumulation of the leading
-// product is exact (it truncates nothing). The remainder x - x_0 (exact in FP32, |.| <= q/2) is
-// split into the correction terms in floating point as usual.
-__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_TF32X2 || mode >= OPM_BF16X2; }
-__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_TF32X2 ? 9 : 8; }
+// The six-product bf16 split makes its leading term a fixed-point number: an integer multiple of
+// q = 2^qexp with |x_0 / q| <= 2^8, q fixed per operand row and 128-byte K block (64 elements).
+// Then every product of leading terms within one K block is a multiple of q_a q_b below
+// 2^16 q_a q_b, and their block sum of 64 stays below 2^24 q_a q_b, so the tensor core's FP32
+// accumulation of the leading product is exact (it truncates nothing). The remainder x - x_0
+// (exact in FP32, |.| <= q/2) is split into the middle and low terms in floating point, which
+// keeps x to 2^-26 of the block's largest entry. The two-term splits keep a floating leading term:
+// with a fixed-point one their single correction term would leave entries far below the block's
+// largest with only its 8 or 11 bits.
+__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_BF16X3; }
+__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_BF16X3 ? 8 : 0; }
 
 // qexp for a row block whose largest magnitude is m: q = 2^(floor(log2 m) + 1 - lead bits), so
 // that m / q < 2^lead bits; clamped to the normal FP32 range (zero blocks take the floor).
@@ -470,21 +472,21 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
           make_float2(to_tf32(static_cast<float>(v0)), to_tf32(static_cast<float>(v1)));
       break;
-    case OPM_TF32X2: {
+    case OPM_TF32X2: {  // floating split: hi = tf32(x), lo = tf32(x - hi)
       const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
-      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
+      const float h0 = to_tf32(x0), h1 = to_tf32(x1);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(h0, h1);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[1]) + idx) =
           make_float2(to_tf32(x0 - h0), to_tf32(x1 - h1));
       break;
     }
-    case OPM_BF16X2: {
+    case OPM_BF16X2: {  // floating split: hi = bf16(x), lo = bf16(x - hi)
       const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
-      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
-      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) =
-          __floats2bfloat162_rn(h0, h1);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) =
-          __floats2bfloat162_rn(x0 - h0, x1 - h1);
+          __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
       break;
     }
     default: {  // OPM_BF16X3
@@ -503,8 +505,8 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
   }
 }
 
-// Tile of 32 rows x TK k per iteration, 256 threads; TK = 32, or for bf16 split modes 64 = one
-// 128-byte K block of the operand (the leading-term quantum is fixed per row and block). The
+// Tile of 32 rows x TK k per iteration, 256 threads; TK = 32, or for the six-product bf16 split
+// 64 = one 128-byte K block of the operand (the leading-term quantum is fixed per row and block). The
 // source offsets of the tile's rows and columns are computed once per tile; loads run with lanes
 // along whichever index is contiguous in the source, stores with lanes along k and two elements
 // per vector store.
@@ -526,7 +528,7 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   const int lead = lead_bits(p.mode);
   // K block of the GEMM in complex k: 64 bf16 or 32 TF32 elements of one plane; with K below
   // that, one block holds both planes of the row (Re and -Im, or Im and Re, or Re and Im)
-  const int W = (p.mode >= OPM_BF16X2) ? 64 : 32;
+  const int W = split ? 64 : 32;
   const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
   const int TK = p.kbits >= 6 && W == 64 ? 64 : (p.kbits >= 5 ? 32 : (1 << p.kbits));
   const bool joint = (int64_t(1) << p.kbits) < W;  // the quantum spans both planes

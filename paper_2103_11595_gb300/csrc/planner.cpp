@@ -16,7 +16,7 @@
 //  * Learned: an MLP scores candidate merges (planner_learned.cpp); the greedy planner is its
 //    fallback and judge.
 // The AUTO planner runs restarts of both and keeps the path with the smallest estimated time
-// sum_s max(8 cmacs_s / peak_flops, bytes_s / peak_bw).
+// (step_seconds: a model of the lowered kernels on GB300), after subtree reconfiguration.
 #include <algorithm>
 #include <array>
 #include <bitset>
@@ -98,6 +98,57 @@ void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& 
 
 }  // namespace
 
+// Estimated device time of one pairwise step with operand ranks ra, rb and result rank rc (labels
+// of dimension 2; runion = |a u b|, so K = 2^(ra + rb - runion)), following the lowering's choice
+// of kernel class (program.cpp) and GB300's rates: every tensor is complex FP64 in HBM, the
+// gate-absorption, split-K and trace kernels compute in FP64 on the CUDA cores, GEMM-class steps
+// gather both operands into the precision's operand terms and run one real GEMM of
+// 2M x N x 2K on the tensor cores (or on the CUDA cores in the FP64 / FP32 modes), and every
+// GEMM-class step carries a fixed cost of its two launches. A GEMM whose output tiles cannot
+// occupy every SM runs proportionally slower.
+double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
+  constexpr double kBw = 5.0e12;        // achieved HBM bandwidth of the streaming kernels (B/s)
+  constexpr double kFp64 = 1.0e12;      // FP64 CUDA-core rate (flop/s)
+  constexpr double kFp32 = 40e12;       // FP32 CUDA-core rate
+  constexpr double kSMs = 152;
+  const int rk = ra + rb - runion;
+  const double flops = 8.0 * std::ldexp(1.0, runion);  // 8 per complex multiply-add
+  const double io = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * 16.0;
+  if (rc == 0) return std::max(io / kBw, flops / (p.precision == AJF_PREC_F64 ? kFp64 : kFp32)) + 3e-6;
+  const int ma = ra - rk, nb = rb - rk;
+  const bool gemm = ma >= 4 && nb >= 4 && rk >= 3 && ma + nb + rk >= 18;
+  if (!gemm) {
+    if (rc <= 12 && rk >= 10) return std::max(io / kBw, flops / kFp64) + 3e-6;  // split-K
+    return std::max(io / kBw, flops / kFp64) + 1e-6;                            // one thread per output
+  }
+  // GEMM class: X (the smaller operand) embedded as 2M x 2K, Y as N x 2K
+  const int m = ra <= rb ? ma : nb, n = ra <= rb ? nb : ma;
+  const double Mt = std::ldexp(1.0, m + 1), Nt = std::ldexp(1.0, n), Kt = std::ldexp(1.0, rk + 1);
+  const bool tc = p.tensor_cores && p.precision >= AJF_PREC_TF32;
+  int terms = 1, passes = 1;
+  double eb = 8, rate = kFp64, tm = 64, tn = 64;
+  if (p.precision == AJF_PREC_F32) {
+    eb = 4;
+    rate = kFp32;
+    tm = 128;
+  } else if (tc) {
+    const bool bf16 = p.precision == AJF_PREC_BF16X3 || p.precision == AJF_PREC_BF16X6;
+    terms = p.precision == AJF_PREC_TF32 ? 1 : (p.precision == AJF_PREC_BF16X6 ? 3 : 2);
+    passes = p.precision == AJF_PREC_TF32 ? 1 : (p.precision == AJF_PREC_BF16X6 ? 6 : 3);
+    eb = bf16 ? 2 : 4;
+    rate = bf16 ? 1.1e15 : 0.55e15;  // sustained tensor rate of the split GEMM's hardware products
+    tm = 128;
+    tn = Nt >= 128 ? 128 : Nt;
+  }
+  const double operands = terms * eb * (Mt * Kt + Nt * Kt);
+  const double gather = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb)) * 16.0 + operands;
+  const double out = Mt * Nt * 8.0;
+  double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn);
+  if (tc) tiles *= std::max(1.0, std::min(std::ceil(kSMs / tiles) * 2.0, Kt * eb / 1024.0));  // K splits
+  const double eff = std::min(1.0, tiles / kSMs);
+  return gather / kBw + std::max(passes * flops / (rate * eff), (operands + out) / kBw) + 14e-6;
+}
+
 void evaluate_path(const Network& net, Path& path, const PlanParams& p) {
   std::vector<int> rank;
   for (auto& l : net.leaf_labels) rank.push_back(static_cast<int>(l.size()));
@@ -109,8 +160,7 @@ void evaluate_path(const Network& net, Path& path, const PlanParams& p) {
     const int k = (ra + rb - rc) / 2;
     const double c = std::ldexp(1.0, ra + rb - k);
     cm += c;
-    const double bytes = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * p.elem_bytes;
-    secs += std::max(8.0 * c / p.peak_flops, bytes / p.peak_bw) + 2e-6;
+    secs += step_seconds(ra, rb, ra + rb - k, rc, p);
     rank.push_back(rc);
     width = std::max(width, rc);
     maxsz = std::max(maxsz, std::ldexp(1.0, rc));
@@ -457,16 +507,10 @@ Path plan_minfill(const Network& net, const PlanParams& p, uint64_t seed) {
 namespace {
 
 constexpr int kReconfInputs = 8;
-constexpr size_t kReconfCandidates = 64;  // candidate paths that get reconfigured (the best by estimate)
+constexpr size_t kReconfCandidates = 16;  // candidate paths that get reconfigured (the best by estimate)
 constexpr int kReconfPasses = 4;
 constexpr int kReconfLabels = 512;
 using LSet = std::bitset<kReconfLabels>;
-
-double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
-  const double c = std::ldexp(1.0, runion);
-  const double bytes = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * p.elem_bytes;
-  return std::max(8.0 * c / p.peak_flops, bytes / p.peak_bw) + 2e-6;
-}
 
 struct Forest {
   int L = 0;
@@ -547,7 +591,7 @@ bool reconfigure_node(Forest& f, int v, const PlanParams& p) {
     cur += step_seconds(static_cast<int>(f.lab[f.ca[u]].size()), static_cast<int>(f.lab[f.cb[u]].size()), ru,
                         static_cast<int>(f.lab[u].size()), p);
   }
-  if (cur - 2e-6 * static_cast<double>(inner.size()) < 1e-6) return false;
+  if (cur < 1e-6 + 1e-6 * static_cast<double>(inner.size())) return false;
   // local label numbering
   std::unordered_map<int, int> local;
   auto loc = [&](int x) {

@@ -12,19 +12,24 @@
 // Accuracy. The tensor core's FP32 accumulation truncates toward zero: measured on GB300 with
 // positive operands, a TMEM accumulation over K drifts by about -(K/8) * 2^-24 relative, far above
 // round-to-nearest FP32, and a drift of that kind compounds over the dozens of GEMMs of one
-// contraction. The kernel removes the drift by construction instead of correcting it:
+// contraction. In the six-product split the kernel removes the drift by construction instead of
+// correcting it:
 //  * exact leading product: the operand preparation (k_perm) makes every leading term x_0 an
-//    integer multiple of a power of two q fixed per row and 128-byte K block, with |x_0 / q| <= 2^8
-//    (bf16) or 2^9 (TF32). Within one K block every product x_0 y_0 is then a multiple of q_x q_y of
-//    magnitude <= 2^16 (2^18) q_x q_y, and the block's sum of 64 (32) of them stays below 2^24 q_x q_y:
-//    the TMEM accumulation of the leading product loses no bit at all;
-//  * two partials per K block: the leading product goes into its own fresh TMEM partial P0 (exact),
-//    the correction products (about 2^-8 of it) into a second fresh partial P1, whose truncation
-//    is relative to |P1| and so at most ~2^-31 of the result per instruction;
+//    integer multiple of a power of two q fixed per row and 128-byte K block, with |x_0 / q| <= 2^8.
+//    Within one K block every product x_0 y_0 is then a multiple of q_x q_y of magnitude at most
+//    2^16 q_x q_y, and the block's sum of 64 of them stays below 2^24 q_x q_y: the TMEM accumulation
+//    of the leading product loses no bit at all (the middle and low terms carry the remainder
+//    x - x_0 to 2^-26 of the block's largest entry);
+//  * two partials per K block: the leading product goes into its own fresh TMEM partial P0, the
+//    correction products (about 2^-8 of it) into a second fresh partial P1, whose truncation is
+//    relative to |P1| and so at most ~2^-31 of the result per instruction;
 //  * promotion: eight epilogue warps add P0 + P1 of every K block into FP32 registers with
 //    round-to-nearest (unbiased), at most kMaxBlocksPerSplit blocks per register sum; longer
 //    contractions are split over K and the FP64 partial tiles summed in a fixed order.
 // No calibrated correction factor is involved; the result is stored as FP32 -> FP64 exactly.
+// The two-term splits (TF32 and bf16 three-product modes) keep a floating leading term, whose 11
+// or 8 significant bits follow each entry: their P0 truncates like a plain accumulation, one
+// promoted K block at a time, and they are bounded modes, not FP32-class ones.
 //
 // Kernel structure (persistent: one CTA per SM walks the 128 x BN output tiles in a grouped
 // raster order; 320 threads; the slot and TMEM-buffer rings continue from tile to tile so the
@@ -546,7 +551,10 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   // persistent grid: one CTA per SM (the kernel holds 1 CTA/SM), each walking tiles with a stride
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
-  const int64_t grid = tiles < sms ? tiles : sms;
+  // work items are (tile, K split) pairs: a GEMM with few tiles but many K splits still spreads
+  // over every SM
+  const int64_t work = tiles * static_cast<int64_t>(p.ksplit);
+  const int64_t grid = work < sms ? work : sms;
   const uint32_t fmt = BF16 ? 1u : 2u;  // A/B type: TF32 = 2, BF16 = 1; D = F32; both K-major
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
             (static_cast<uint32_t>(kBM >> 4) << 24);

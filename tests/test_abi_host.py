@@ -151,8 +151,8 @@ def test_host_context_cannot_run():
 
 def test_precision_config_as_written_is_over_budget():
     """The 4x5 grid at depth 12 (the precision config as written) plans to a width near 2^80
-    elements for Alg. II: the call reports AJF_E_BUDGET with that width and cost. Depth 6
-    (2^38 elements, about 10 TB) is over a one-GB300 budget; depth 4 (2^24) fits."""
+    elements for Alg. II: the call reports AJF_E_BUDGET with that width and cost. Depth 6 needs
+    arenas of about 2^32 elements and more (over a 50 GB budget); depth 4 (2^22-2^24) fits."""
     with host_ctx() as c:
         ajf.load_instance(c.handle, W.precision(0, depth=12))
         with pytest.raises(ajf.AjfError) as e:
@@ -161,7 +161,7 @@ def test_precision_config_as_written_is_over_budget():
         assert e.value.info["width"] >= 64 and e.value.info["cmacs"] > 1e25
         ajf.load_instance(c.handle, W.precision(0, depth=6))
         with pytest.raises(ajf.AjfError) as e:
-            ajf.ajf_plan(c.handle, 2, trials=2, mem_budget_bytes=280e9)
+            ajf.ajf_plan(c.handle, 2, trials=2, mem_budget_bytes=50e9)
         assert e.value.status == ajf.AJF_E_BUDGET
         ajf.load_instance(c.handle, W.precision(0, depth=4))
         info = ajf.ajf_plan(c.handle, 2, trials=2, mem_budget_bytes=280e9)
