@@ -456,24 +456,25 @@ __device__ __forceinline__ float pow2f(int e) { return __uint_as_float(static_ca
 // Leading term of x: rint(x / q) q, exact (power-of-two scalings of a float with |x / q| < 2^9).
 __device__ __forceinline__ float lead_term(float x, int qexp) { return rintf(x * pow2f(-qexp)) * pow2f(qexp); }
 
-// Two consecutive operand elements (idx even, same row and K block) with one vector store per
-// split term. qexp: the block's quantum (split modes only).
-__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, double v0, double v1,
+// Two consecutive operand elements (idx even) of the FP64 operand mode.
+__device__ __forceinline__ void store_operand2_f64(const PermDev& p, char* base, int64_t idx, double v0, double v1) {
+  *reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx) = make_double2(v0, v1);
+}
+
+// Two consecutive operand elements (idx even, same row and K block) of an FP32-based operand mode
+// (the values already rounded to FP32), with one vector store per split term. qexp: the block's
+// leading-term quantum (six-product split only).
+__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, float x0, float x1,
                                                int qexp) {
   switch (p.mode) {
-    case OPM_F64:
-      *reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx) = make_double2(v0, v1);
-      break;
     case OPM_F32:
-      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
-          make_float2(static_cast<float>(v0), static_cast<float>(v1));
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(x0, x1);
       break;
     case OPM_TF32:
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
-          make_float2(to_tf32(static_cast<float>(v0)), to_tf32(static_cast<float>(v1)));
+          make_float2(to_tf32(x0), to_tf32(x1));
       break;
     case OPM_TF32X2: {  // floating split: hi = tf32(x), lo = tf32(x - hi)
-      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
       const float h0 = to_tf32(x0), h1 = to_tf32(x1);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(h0, h1);
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[1]) + idx) =
@@ -481,7 +482,6 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
       break;
     }
     case OPM_BF16X2: {  // floating split: hi = bf16(x), lo = bf16(x - hi)
-      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
       const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
       const float2 hf = __bfloat1622float2(h);
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
@@ -489,8 +489,7 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
           __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
       break;
     }
-    default: {  // OPM_BF16X3
-      const float x0 = static_cast<float>(v0), x1 = static_cast<float>(v1);
+    default: {  // OPM_BF16X3: fixed-point leading term, floating middle and low terms
       const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
       const float r0 = x0 - h0, r1 = x1 - h1;
       const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
@@ -506,16 +505,19 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
 }
 
 // Tile of 32 rows x TK k per iteration, 256 threads; TK = 32, or for the six-product bf16 split
-// 64 = one 128-byte K block of the operand (the leading-term quantum is fixed per row and block). The
-// source offsets of the tile's rows and columns are computed once per tile; loads run with lanes
-// along whichever index is contiguous in the source, stores with lanes along k and two elements
-// per vector store.
-template <typename T>
-__global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const T* __restrict__ arena,
+// 64 = one 128-byte K block of the operand (the leading-term quantum is fixed per row and block).
+// The tile is staged in shared memory in S: double for the FP64 operand mode, float for every
+// other mode (which splits the FP32 rounding of each value), so that a 32 x 64 float tile takes
+// the space of a 32 x 32 double one. The source offsets of the tile's rows and columns are
+// computed once per tile; loads run with lanes along whichever index is contiguous in the source,
+// stores with lanes along k and two elements per vector store.
+template <typename S>
+__global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms, const double* __restrict__ arena,
                                               char* __restrict__ base) {
+  constexpr int TKMAX = sizeof(S) == 8 ? 32 : 64;
   extern __shared__ int64_t tab[];
-  __shared__ T tre[32][65], tim[32][65];
-  __shared__ int64_t roff[32], koff[64];
+  __shared__ S tre[32][TKMAX + 1], tim[32][TKMAX + 1];
+  __shared__ int64_t roff[32], koff[TKMAX];
   __shared__ int qre[32], qim[32];
   const PermDev& p = perms[blockIdx.y];
   const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
@@ -524,10 +526,10 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   build_table(p.rows, t_r);
   build_table(p.cols, t_k);
   __syncthreads();
-  const bool split = split_mode(p.mode);
+  const bool split = sizeof(S) == 4 && split_mode(p.mode);
   const int lead = lead_bits(p.mode);
-  // K block of the GEMM in complex k: 64 bf16 or 32 TF32 elements of one plane; with K below
-  // that, one block holds both planes of the row (Re and -Im, or Im and Re, or Re and Im)
+  // K block of the six-product split in complex k: 64 elements of one plane; with K below that,
+  // one block holds both planes of the row (Re and -Im, or Im and Re, or Re and Im)
   const int W = split ? 64 : 32;
   const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
   const int TK = p.kbits >= 6 && W == 64 ? 64 : (p.kbits >= 5 ? 32 : (1 << p.kbits));
@@ -535,17 +537,18 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
   const int KW = TK > 32 ? 64 : 32;                // k extent of the thread mapping
   const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
   const int64_t ntr = R / TR, ntk = K / TK;
-  const T* src = arena + p.src;
+  const double* src = arena + p.src;
   const int64_t ld = 2 * K;
   for (int64_t tile = blockIdx.x; tile < ntr * ntk; tile += gridDim.x) {
     const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
     if (threadIdx.x < 32) roff[threadIdx.x] = threadIdx.x < TR ? lookup(t_r, c_r, r0 + threadIdx.x) : 0;
-    else if (threadIdx.x < 96) koff[threadIdx.x - 32] = threadIdx.x - 32 < TK ? lookup(t_k, c_k, k0 + threadIdx.x - 32) : 0;
+    else if (threadIdx.x < 32 + TKMAX)
+      koff[threadIdx.x - 32] = threadIdx.x - 32 < TK ? lookup(t_k, c_k, k0 + threadIdx.x - 32) : 0;
     __syncthreads();
     // all loads (x 2 planes) of a thread are issued before its shared-memory stores
-    T vr[8], vi[8];
+    double vr[8], vi[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < TKMAX / 8; ++q) {
       if (q < KW / 8) {
         const int l = threadIdx.x + 256 * q;
         const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
@@ -557,19 +560,19 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
       }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < TKMAX / 8; ++q) {
       if (q < KW / 8) {
         const int l = threadIdx.x + 256 * q;
         const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
         if (rr < TR && kk < TK) {
-          tre[rr][kk] = vr[q];
-          tim[rr][kk] = vi[q];
+          tre[rr][kk] = static_cast<S>(vr[q]);
+          tim[rr][kk] = static_cast<S>(vi[q]);
         }
       }
     }
     __syncthreads();
     if (split) {
-      // per row: the largest |Re| and |Im| of the tile's k range (as the FP32 values that are
+      // per row: the largest |Re| and |Im| of the tile's k range (of the FP32 values that are
       // split), one warp per four rows
       const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
       for (int i = wp; i < TR; i += 8) {
@@ -594,17 +597,30 @@ __global__ void __launch_bounds__(256) k_perm(const PermDev* __restrict__ perms,
     const int pairs = TK >> 1;
     for (int w = threadIdx.x; w < TR * pairs; w += blockDim.x) {
       const int i = w / pairs, j = 2 * (w % pairs);
-      const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
-      const int qr = split ? qre[i] : 0, qi = split ? qim[i] : 0;
       const int64_t r = r0 + i, k = k0 + j;
-      if (p.embed) {
-        store_operand2(p, base, r * ld + k, re0, re1, qr);             // (s=0, t=0):  Re
-        store_operand2(p, base, r * ld + K + k, -im0, -im1, qi);       // (s=0, t=1): -Im
-        store_operand2(p, base, (R + r) * ld + k, im0, im1, qi);       // (s=1, t=0):  Im
-        store_operand2(p, base, (R + r) * ld + K + k, re0, re1, qr);   // (s=1, t=1):  Re
+      if constexpr (sizeof(S) == 8) {
+        const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+        if (p.embed) {
+          store_operand2_f64(p, base, r * ld + k, re0, re1);             // (s=0, t=0):  Re
+          store_operand2_f64(p, base, r * ld + K + k, -im0, -im1);       // (s=0, t=1): -Im
+          store_operand2_f64(p, base, (R + r) * ld + k, im0, im1);       // (s=1, t=0):  Im
+          store_operand2_f64(p, base, (R + r) * ld + K + k, re0, re1);   // (s=1, t=1):  Re
+        } else {
+          store_operand2_f64(p, base, r * ld + k, re0, re1);
+          store_operand2_f64(p, base, r * ld + K + k, im0, im1);
+        }
       } else {
-        store_operand2(p, base, r * ld + k, re0, re1, qr);
-        store_operand2(p, base, r * ld + K + k, im0, im1, qi);
+        const float re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+        const int qr = split ? qre[i] : 0, qi = split ? qim[i] : 0;
+        if (p.embed) {
+          store_operand2(p, base, r * ld + k, re0, re1, qr);             // (s=0, t=0):  Re
+          store_operand2(p, base, r * ld + K + k, -im0, -im1, qi);       // (s=0, t=1): -Im
+          store_operand2(p, base, (R + r) * ld + k, im0, im1, qi);       // (s=1, t=0):  Im
+          store_operand2(p, base, (R + r) * ld + K + k, re0, re1, qr);   // (s=1, t=1):  Re
+        } else {
+          store_operand2(p, base, r * ld + k, re0, re1, qr);
+          store_operand2(p, base, r * ld + K + k, im0, im1, qi);
+        }
       }
     }
     __syncthreads();
@@ -979,9 +995,12 @@ cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t sm
                         bool op_f64, cudaStream_t s) {
   if (nperm == 0) return cudaSuccess;
   dim3 grid(grid_x, nperm);
-  // tensors are FP64 in every mode; the operand format (FP64 or a reduced one) is in each PermDev
-  (void)op_f64;
-  k_perm<double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
+  // tensors are FP64 in every mode; the operand format (FP64 or a reduced one) is in each PermDev,
+  // and every PermDev of one launch has the same one
+  if (op_f64)
+    k_perm<double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
+  else
+    k_perm<float><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
   return cudaGetLastError();
 }
 
@@ -1028,6 +1047,7 @@ cudaError_t set_kernel_smem_limits() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;

@@ -108,6 +108,7 @@ void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& 
 // occupy every SM runs proportionally slower.
 double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
   constexpr double kBw = 5.0e12;        // achieved HBM bandwidth of the streaming kernels (B/s)
+  constexpr double kGatherBw = 2.0e12;  // achieved bandwidth of the operand gather (permuted reads)
   constexpr double kFp64 = 1.0e12;      // FP64 CUDA-core rate (flop/s)
   constexpr double kFp32 = 40e12;       // FP32 CUDA-core rate
   constexpr double kSMs = 152;
@@ -146,7 +147,7 @@ double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
   double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn);
   if (tc) tiles *= std::max(1.0, std::min(std::ceil(kSMs / tiles) * 2.0, Kt * eb / 1024.0));  // K splits
   const double eff = std::min(1.0, tiles / kSMs);
-  return gather / kBw + std::max(passes * flops / (rate * eff), (operands + out) / kBw) + 14e-6;
+  return gather / kGatherBw + std::max(passes * flops / (rate * eff), (operands + out) / kBw) + 14e-6;
 }
 
 void evaluate_path(const Network& net, Path& path, const PlanParams& p) {
