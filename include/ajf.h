@@ -495,6 +495,36 @@ ajf_status ajf_fidelity_batch(ajf_ctx *const *ctxs, int n_ctx, int alg, double e
  * AJF_E_STATE (a context without a persistent-lowered plan), AJF_E_NOMEM, AJF_E_CUDA. */
 ajf_status ajf_launch_persistent(ajf_ctx *const *ctxs, int n_ctx, double *dev_results);
 
+/* Persistent step interpreter (no paper counterpart for the kernel; Sec. IV-A remarks that the
+ * evaluations of different circuits are independent): ONE launch of a persistent kernel, captured
+ * in a CUDA graph, runs the default-lowered programs of all n_ctx contexts -- their leaves,
+ * CUDA-core steps, operand gathers, tensor-core GEMM tiles (tcgen05) and final reductions -- as one
+ * queue of tasks that the kernel's blocks (one per SM) take in order, each task after the previous
+ * launch of its own program has completed. Contexts must be planned with the default lowering in a
+ * tensor-core precision mode (or F64 plans without GEMM-class steps), unsliced, on one tcgen05
+ * device; each context's inputs are uploaded if needed. The launch is enqueued on ctxs[0]'s stream
+ * after the other contexts' streams (and they wait for it); results land in every context's own
+ * result area (and in dev_results[3 i .. 3 i + 2] = S, F, 1 - F when dev_results is not NULL).
+ * Errors: AJF_E_ARG, AJF_E_STATE (a context without a default-lowered unsliced plan),
+ * AJF_E_UNSUPPORTED (CUDA-core GEMM steps or FP64 operands, no tcgen05 device), AJF_E_NOMEM,
+ * AJF_E_CUDA. A device-side wait that expires is reported by ajf_fidelity_batch_queue. */
+ajf_status ajf_launch_queue(ajf_ctx *const *ctxs, int n_ctx, double *dev_results);
+
+/* Batch evaluation through one step-interpreter launch (ajf_launch_queue): out[i] receives
+ * context i's result. Synchronises the contexts' streams.
+ * Errors: those of ajf_launch_queue, AJF_E_ARG (alg, eps, out), AJF_E_STATE (a plan of the other
+ * algorithm), AJF_E_TIMEOUT (a bounded device-side wait expired; the launch returned early). */
+ajf_status ajf_fidelity_batch_queue(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out);
+
+/* Autotuner of the step interpreter's work decomposition (no paper counterpart): times `reps`
+ * launches over the batch for each shape -- tensor-core GEMM work items (128 x BN tiles or K
+ * splits) per task in {1, 2, 4}, and tasks per CUDA-core launch in {152, 304, 608} -- and keeps the
+ * fastest for the process under the batch's signature (device and the programs' structures), used
+ * by every later launch of a batch with that signature. The shape chosen is written to
+ * *gemm_items and *body_tasks (either may be NULL). Synchronises the leading context's stream.
+ * Errors: those of ajf_fidelity_batch_queue, AJF_E_ARG (reps < 1). */
+ajf_status ajf_autotune_queue(ajf_ctx *const *ctxs, int n_ctx, int reps, int32_t *gemm_items, int32_t *body_tasks);
+
 /* Autotune the persistent launch of this batch (no paper counterpart): its block size -- how many
  * output elements of a step one network's thread block computes at once -- is measured at 256,
  * 128 and 64 threads (CUDA events around `reps` launches each, after a warm-up launch), and the

@@ -143,6 +143,11 @@ def lib() -> ctypes.CDLL:
             "ajf_profile_enable": (I32, [P, ctypes.c_int]),
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
             "ajf_launch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_launch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_fidelity_batch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D,
+                                               ctypes.POINTER(Result)]),
+            "ajf_autotune_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32),
+                                         ctypes.POINTER(I32)]),
             "ajf_fidelity_batch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D,
                                                     ctypes.POINTER(Result), ctypes.POINTER(I32)]),
         }
@@ -479,6 +484,33 @@ def ajf_launch_persistent(ctxs: Sequence, dev_results: int = 0) -> None:
     st = lib().ajf_launch_persistent(arr, len(ctxs), ctypes.c_void_p(dev_results) if dev_results else None)
     if st != AJF_OK:
         raise AjfError(st, "; ".join(ajf_last_error(c) for c in ctxs if ajf_last_error(c)))
+
+
+def ajf_launch_queue(ctxs: Sequence, dev_results: int = 0) -> None:
+    """One step-interpreter launch over the contexts (enqueued on the first context's stream)."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    st = lib().ajf_launch_queue(arr, len(ctxs), ctypes.c_void_p(dev_results) if dev_results else None)
+    if st != AJF_OK:
+        raise AjfError(st, ajf_last_error(ctxs[0]))
+
+
+def ajf_fidelity_batch_queue(ctxs: Sequence, alg: int, eps: float = -1.0) -> list:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    res = (Result * len(ctxs))()
+    st = lib().ajf_fidelity_batch_queue(arr, len(ctxs), int(alg), float(eps), res)
+    if st != AJF_OK:
+        raise AjfError(st, ajf_last_error(ctxs[0]))
+    return [r.as_dict() for r in res]
+
+
+def ajf_autotune_queue(ctxs: Sequence, reps: int = 3) -> tuple:
+    """(GEMM work items per task, tasks per CUDA-core launch) chosen for this batch."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    gi, bt = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().ajf_autotune_queue(arr, len(ctxs), int(reps), ctypes.byref(gi), ctypes.byref(bt))
+    if st != AJF_OK:
+        raise AjfError(st, ajf_last_error(ctxs[0]))
+    return int(gi.value), int(bt.value)
 
 
 def ajf_autotune_persistent(ctxs: Sequence, reps: int = 5) -> int:

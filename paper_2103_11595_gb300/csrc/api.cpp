@@ -119,6 +119,16 @@ struct ajf_ctx {
   TcPrepSet tc_own, tc_static;
   // device address of the fixed arena of ajf_fidelity_noalloc, resolved by ajf_create
   char* static_arena = nullptr;
+  // step-interpreter launches led by this context: phase/task tables, GEMM parameter blocks,
+  // counters and status word in one device buffer, the CUDA graph of the launch, and what they
+  // were built for
+  char* q_dev = nullptr;
+  size_t q_cap = 0;
+  std::vector<uintptr_t> q_key;
+  int q_nphases = 0, q_ntasks = 0;
+  size_t q_off_phases = 0, q_off_tasks = 0, q_off_counters = 0, q_off_status = 0;
+  cudaGraphExec_t q_graph = nullptr;
+  double q_flops = 0, q_bytes = 0;
   // profiling
   struct ProfRec {
     cudaEvent_t a, b;
@@ -365,6 +375,30 @@ void drain_profile(ajf_ctx* c) {
 }
 
 // Enqueue the device program: leaves, contraction launches, FP64 final reduction.
+// Host set-up of the program's tensor-core GEMM launches (tensor maps, tiling, kernel parameters)
+// for the context's current arena, kept in `tc` until the program or the arena changes.
+ajf_status prepare_tc_set(ajf_ctx* c, ajf_ctx::TcPrepSet* tc) {
+  const Program& P = c->prog;
+  char* base = c->arena;
+  if (tc->gen == c->prog_gen && tc->arena == base && tc->prep.size() == P.launches.size()) return AJF_OK;
+  int* status = reinterpret_cast<int*>(base + P.off_status);
+  tc->prep.assign(P.launches.size(), TcPrepared{});
+  for (size_t i = 0; i < P.launches.size(); ++i) {
+    const Launch& ln = P.launches[i];
+    if (ln.kind != LK_GEMM_TC) continue;
+    const cudaError_t e = tc_gemm_prepare(&tc->prep[i], base, ln.a_off, ln.b_off, ln.npass,
+                                          reinterpret_cast<double*>(base + ln.c_off), ln.M, ln.N, ln.K, ln.tc_kind,
+                                          reinterpret_cast<double*>(base + ln.ws_off), ln.ksplit, status, kTcWaitNs, 0);
+    if (e != cudaSuccess) {
+      tc->gen = -1;
+      return cuda_fail(c, e, "tensor-core GEMM set-up");
+    }
+  }
+  tc->gen = c->prog_gen;
+  tc->arena = base;
+  return AJF_OK;
+}
+
 ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = nullptr) {
   const Program& P = c->prog;
   char* base = c->arena;
@@ -385,21 +419,9 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = 
   int* status = reinterpret_cast<int*>(base + P.off_status);
   // tensor-core GEMM set-up (tensor maps, tiling) is done on the host once per program and arena,
   // outside the timed launches
-  if (tc->gen != c->prog_gen || tc->arena != base || tc->prep.size() != P.launches.size()) {
-    tc->prep.assign(P.launches.size(), TcPrepared{});
-    for (size_t i = 0; i < P.launches.size(); ++i) {
-      const Launch& ln = P.launches[i];
-      if (ln.kind != LK_GEMM_TC) continue;
-      e = tc_gemm_prepare(&tc->prep[i], base, ln.a_off, ln.b_off, ln.npass, reinterpret_cast<double*>(base + ln.c_off),
-                          ln.M, ln.N, ln.K, ln.tc_kind, reinterpret_cast<double*>(base + ln.ws_off), ln.ksplit, status,
-                          kTcWaitNs, 0);
-      if (e != cudaSuccess) {
-        tc->gen = -1;
-        return cuda_fail(c, e, "tensor-core GEMM set-up");
-      }
-    }
-    tc->gen = c->prog_gen;
-    tc->arena = base;
+  {
+    const ajf_status st = prepare_tc_set(c, tc);
+    if (st != AJF_OK) return st;
   }
   for (size_t li = 0; li < P.launches.size(); ++li) {
     const Launch& ln = P.launches[li];
@@ -868,6 +890,8 @@ void ajf_destroy(ajf_ctx* c) {
   if (c->own_arena && c->arena && !c->user_ws) cudaFree(c->arena);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->pers_dev) cudaFree(c->pers_dev);
+  if (c->q_graph) cudaGraphExecDestroy(c->q_graph);
+  if (c->q_dev) cudaFree(c->q_dev);
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -2215,9 +2239,403 @@ ajf_status launch_persistent_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_r
   return AJF_OK;
 }
 
+// ---- persistent step interpreter: one launch for the default-lowered programs of many contexts
+//
+// Task granularity, the interpreter's tunable shape: GEMM work items per task, and the number of
+// tasks a CUDA-core phase is cut into (at most; never more than its blocks). The process keeps the
+// fastest measured setting per batch signature (ajf_autotune_queue).
+struct QueueShape {
+  int gemm_items = 2;
+  int body_tasks = 304;
+};
+std::map<std::vector<int64_t>, QueueShape> g_tuned_queue;
+
+QueueShape tuned_queue(ajf_ctx* const* ctxs, int n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_queue.find(batch_signature(ctxs, n));
+  return it == g_tuned_queue.end() ? QueueShape{} : it->second;
+}
+
+int queue_sms(int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  return sms;
+}
+
+// Phase and task tables of an interpreter launch over ctxs, in ctxs[0]'s device buffer; rebuilt
+// only when a context, its arena, its program, the result pointer or the shape changed.
+ajf_status queue_table(ajf_ctx* const* ctxs, int n, double* dev_results, const QueueShape& shape) {
+  ajf_ctx* lead = ctxs[0];
+  std::vector<uintptr_t> key = {reinterpret_cast<uintptr_t>(dev_results), static_cast<uintptr_t>(shape.gemm_items),
+                                static_cast<uintptr_t>(shape.body_tasks)};
+  for (int i = 0; i < n; ++i) {
+    key.push_back(reinterpret_cast<uintptr_t>(ctxs[i]));
+    key.push_back(reinterpret_cast<uintptr_t>(ctxs[i]->arena));
+    key.push_back(static_cast<uintptr_t>(ctxs[i]->prog_gen));
+    key.push_back(static_cast<uintptr_t>(ctxs[i]->plan_gen));
+  }
+  if (lead->q_dev && key == lead->q_key) return AJF_OK;
+  const size_t gp_bytes = queue_gemm_params_bytes();
+  // per program: its phases in launch order (prev filled in below); GEMM parameter blocks
+  std::vector<std::vector<QPhase>> progs(n);
+  std::vector<std::vector<int>> gemm_param_index(n);  // per phase: index of its parameter block or -1
+  std::vector<char> params;
+  double flops = 0, bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    ajf_ctx* c = ctxs[i];
+    const Program& P = c->prog;
+    char* base = c->arena;
+    flops += P.flops;
+    bytes += P.bytes;
+    ajf_status st = prepare_tc_set(c, &c->tc_own);
+    if (st != AJF_OK) return st;
+    auto add = [&](QPhase ph, int gp) {
+      ph.base = base;
+      progs[i].push_back(ph);
+      gemm_param_index[i].push_back(gp);
+    };
+    const StepDev* steps = reinterpret_cast<const StepDev*>(base + P.off_steps);
+    const PermDev* perms = reinterpret_cast<const PermDev*>(base + P.off_perms);
+    double* partial = reinterpret_cast<double*>(base + P.off_partial);
+    double* scalars = reinterpret_cast<double*>(base + P.off_scalars);
+    QPhase ph;
+    std::memset(&ph, 0, sizeof(ph));
+    ph.kind = QK_LEAVES;
+    ph.nblocks = ph.count = static_cast<int32_t>(P.leaves.size());
+    ph.desc = base + P.off_leaves;
+    ph.p0 = reinterpret_cast<double*>(base + P.off_inputs);
+    add(ph, -1);
+    for (size_t li = 0; li < P.launches.size(); ++li) {
+      const Launch& ln = P.launches[li];
+      std::memset(&ph, 0, sizeof(ph));
+      switch (ln.kind) {
+        case LK_SMALL:
+          ph.kind = QK_SMALL;
+          ph.nblocks = ln.blocks;
+          ph.count = ln.count;
+          ph.desc = steps + ln.first;
+          add(ph, -1);
+          break;
+        case LK_SPLITK:
+        case LK_DOT: {
+          ph.kind = ln.kind == LK_DOT ? QK_DOT : QK_SPLITK;
+          ph.nblocks = ln.blocks;
+          ph.count = ln.count;
+          ph.flag = ln.op_f64 == 0 ? 1 : 0;
+          ph.desc = steps + ln.first;
+          ph.p0 = partial;
+          add(ph, -1);
+          QPhase d;
+          std::memset(&d, 0, sizeof(d));
+          d.kind = QK_SPLITK_DONE;
+          d.nblocks = d.count = ln.count;
+          d.desc = steps + ln.first;
+          d.p0 = partial;
+          d.p1 = scalars;
+          add(d, -1);
+          break;
+        }
+        case LK_PERM:
+          if (ln.op_f64) return fail(c, AJF_E_UNSUPPORTED, "step interpreter: FP64 GEMM operands (use a tensor-core mode)");
+          ph.kind = QK_PERM;
+          ph.grid_x = ln.blocks;
+          ph.count = ln.count;
+          ph.nblocks = ln.blocks * ln.count;
+          ph.desc = perms + ln.first;
+          add(ph, -1);
+          break;
+        case LK_GEMM_TC: {
+          int bn = 0, bf16 = 0, nwork = 0;
+          const size_t at = params.size();
+          params.resize(at + gp_bytes, 0);
+          const cudaError_t e = queue_gemm_params(c->tc_own.prep[li], params.data() + at, &bn, &bf16, &nwork);
+          if (e != cudaSuccess) return cuda_fail(c, e, "step interpreter: GEMM parameters");
+          ph.kind = QK_GEMM;
+          ph.nblocks = nwork;
+          ph.flag = bf16;
+          ph.bn = bn;
+          add(ph, static_cast<int>(at / gp_bytes));
+          if (ln.ksplit > 1) {
+            QPhase d;
+            std::memset(&d, 0, sizeof(d));
+            d.kind = QK_SPLIT_SUM;
+            d.n = ln.M * ln.N;
+            d.nblocks = static_cast<int32_t>(std::min<int64_t>((d.n + 255) / 256, 4096));
+            d.ksplit = ln.ksplit;
+            d.p0 = reinterpret_cast<double*>(base + ln.ws_off);
+            d.p1 = reinterpret_cast<double*>(base + ln.c_off);
+            add(d, -1);
+          }
+          break;
+        }
+        default:
+          return fail(c, AJF_E_UNSUPPORTED, "step interpreter: CUDA-core GEMM steps (use a tensor-core mode)");
+      }
+    }
+    std::memset(&ph, 0, sizeof(ph));
+    ph.kind = QK_OPEN;
+    ph.nblocks = P.final_blocks;
+    ph.desc = base + P.off_final;
+    ph.p0 = scalars;
+    ph.p1 = reinterpret_cast<double*>(base + P.off_traces);
+    ph.p2 = reinterpret_cast<double*>(base + P.off_open_partial);
+    add(ph, -1);
+    QPhase f = ph;
+    f.kind = QK_FINAL;
+    f.nblocks = 1;
+    f.p1 = reinterpret_cast<double*>(base + P.off_result);
+    f.p3 = dev_results ? dev_results + 3 * static_cast<size_t>(i) : nullptr;
+    add(f, -1);
+  }
+  // interleave the programs' phases (round r holds phase r of every program) and cut them into tasks
+  const int sms = std::max(1, queue_sms(lead->device));
+  std::vector<QPhase> phases;
+  std::vector<QTask> tasks;
+  std::vector<int> last(n, -1);
+  std::vector<std::pair<int, int>> gemm_fix;  // (phase, parameter block)
+  size_t rounds = 0;
+  for (auto& v : progs) rounds = std::max(rounds, v.size());
+  for (size_t r = 0; r < rounds; ++r) {
+    for (int i = 0; i < n; ++i) {
+      if (r >= progs[i].size()) continue;
+      QPhase ph = progs[i][r];
+      const int idx = static_cast<int>(phases.size());
+      ph.prev = last[i];
+      last[i] = idx;
+      int per = 1;
+      if (ph.kind == QK_GEMM) per = std::max(1, shape.gemm_items);
+      else if (ph.kind != QK_FINAL) per = std::max(1, (ph.nblocks + shape.body_tasks - 1) / shape.body_tasks);
+      ph.ntasks = 0;
+      for (int b = 0; b < std::max(1, ph.nblocks); b += per) {
+        tasks.push_back(QTask{idx, b, std::min(std::max(1, ph.nblocks), b + per), 0});
+        ++ph.ntasks;
+      }
+      const int gp = gemm_param_index[i][r];
+      if (gp >= 0) gemm_fix.push_back({idx, gp});
+      phases.push_back(ph);
+    }
+  }
+  (void)sms;
+  // device buffer: GEMM parameter blocks (1024-byte aligned) | phases | tasks | counters | status
+  auto al = [](size_t x) { return (x + 1023) / 1024 * 1024; };
+  const size_t off_params = 0;
+  const size_t off_phases = off_params + al(params.size());
+  const size_t off_tasks = off_phases + al(sizeof(QPhase) * phases.size());
+  const size_t off_counters = off_tasks + al(sizeof(QTask) * tasks.size());
+  const size_t off_status = off_counters + al(sizeof(int) * (kQPhase0 + phases.size()));
+  const size_t total = off_status + 1024;
+  if (total > lead->q_cap) {
+    if (lead->q_dev) {
+      CUDA_TRY(lead, cudaStreamSynchronize(lead->stream));
+      cudaFree(lead->q_dev);
+      lead->q_dev = nullptr;
+      lead->q_cap = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, total) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(lead, AJF_E_NOMEM, "step interpreter tables");
+    }
+    lead->q_dev = static_cast<char*>(p);
+    lead->q_cap = total;
+  }
+  for (auto& [idx, gp] : gemm_fix) phases[idx].gemm = lead->q_dev + off_params + static_cast<size_t>(gp) * gp_bytes;
+  std::vector<char> host(off_counters, 0);
+  if (!params.empty()) std::memcpy(host.data() + off_params, params.data(), params.size());
+  std::memcpy(host.data() + off_phases, phases.data(), sizeof(QPhase) * phases.size());
+  std::memcpy(host.data() + off_tasks, tasks.data(), sizeof(QTask) * tasks.size());
+  CUDA_TRY(lead, cudaMemcpyAsync(lead->q_dev, host.data(), host.size(), cudaMemcpyHostToDevice, lead->stream));
+  CUDA_TRY(lead, cudaMemsetAsync(lead->q_dev + off_status, 0, 1024, lead->stream));
+  CUDA_TRY(lead, cudaStreamSynchronize(lead->stream));  // `host` goes out of scope
+  lead->q_key = key;
+  lead->q_nphases = static_cast<int>(phases.size());
+  lead->q_ntasks = static_cast<int>(tasks.size());
+  lead->q_off_phases = off_phases;
+  lead->q_off_tasks = off_tasks;
+  lead->q_off_counters = off_counters;
+  lead->q_off_status = off_status;
+  lead->q_flops = flops;
+  lead->q_bytes = bytes;
+  if (lead->q_graph) {
+    cudaGraphExecDestroy(lead->q_graph);
+    lead->q_graph = nullptr;
+  }
+  return AJF_OK;
+}
+
+ajf_status check_queue_batch(ajf_ctx* const* ctxs, int n_ctx) {
+  ajf_status st = check_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  for (int i = 0; i < n_ctx; ++i) {
+    const ajf_ctx* c = ctxs[i];
+    if (!c->planned || c->prog.persistent)
+      return fail(ctxs[i], AJF_E_STATE, "step interpreter: context without a default-lowered plan");
+    if (multi_run(c)) return fail(ctxs[i], AJF_E_STATE, "step interpreter: sliced plans run through ajf_fidelity_alg1/2");
+    if (!c->tc_device) return fail(ctxs[i], AJF_E_UNSUPPORTED, "step interpreter needs a tcgen05 device");
+  }
+  return AJF_OK;
+}
+
+// Enqueue one interpreter launch over ctxs on ctxs[0]'s stream (after every context's stream).
+ajf_status launch_queue_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_results, const QueueShape& shape) {
+  ajf_ctx* lead = ctxs[0];
+  CUDA_TRY(lead, cudaSetDevice(lead->device));
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]->uploaded) {
+      ajf_status st = do_upload(ctxs[i]);
+      if (st != AJF_OK) return st;
+    }
+  }
+  ajf_status st = queue_table(ctxs, n_ctx, dev_results, shape);
+  if (st != AJF_OK) return st;
+  cudaStream_t s0 = lead->stream;
+  for (int i = 1; i < n_ctx; ++i) {
+    if (ctxs[i]->stream == s0) continue;
+    cudaEvent_t ev = nullptr;
+    if ((st = sync_event(ctxs[i], &ev)) != AJF_OK) return st;
+    CUDA_TRY(ctxs[i], cudaEventRecord(ev, ctxs[i]->stream));
+    CUDA_TRY(lead, cudaStreamWaitEvent(s0, ev, 0));
+  }
+  const int blocks = std::max(1, std::min(queue_sms(lead->device), lead->q_ntasks));
+  auto enqueue = [&](cudaStream_t s) {
+    return launch_queue(reinterpret_cast<const QPhase*>(lead->q_dev + lead->q_off_phases),
+                        lead->q_nphases, reinterpret_cast<const QTask*>(lead->q_dev + lead->q_off_tasks),
+                        lead->q_ntasks, reinterpret_cast<int*>(lead->q_dev + lead->q_off_counters),
+                        reinterpret_cast<int*>(lead->q_dev + lead->q_off_status), blocks, s);
+  };
+  if (lead->profiling) {
+    ProfScope ps(lead, s0, 7, lead->q_flops, lead->q_bytes);
+    const cudaError_t e = enqueue(s0);
+    if (e != cudaSuccess) return cuda_fail(lead, e, "step interpreter");
+  } else {
+    // the launch (counter reset + kernel) is captured once into a CUDA graph and replayed
+    if (!lead->q_graph) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(lead, cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t e = enqueue(s0);
+      const cudaError_t e2 = cudaStreamEndCapture(s0, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(lead, e != cudaSuccess ? e : e2, "step interpreter graph capture");
+      }
+      const cudaError_t e3 = cudaGraphInstantiate(&lead->q_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e3 != cudaSuccess) return cuda_fail(lead, e3, "step interpreter graph");
+    }
+    CUDA_TRY(lead, cudaGraphLaunch(lead->q_graph, s0));
+  }
+  cudaEvent_t ev0 = nullptr;
+  if ((st = sync_event(lead, &ev0)) != AJF_OK) return st;
+  CUDA_TRY(lead, cudaEventRecord(ev0, s0));
+  for (int i = 1; i < n_ctx; ++i)
+    if (ctxs[i]->stream != s0) CUDA_TRY(ctxs[i], cudaStreamWaitEvent(ctxs[i]->stream, ev0, 0));
+  for (int i = 0; i < n_ctx; ++i)
+    if (ctxs[i]->alg == 1) ctxs[i]->have_alg1 = true;
+  return AJF_OK;
+}
+
+ajf_status queue_status(ajf_ctx* lead) {
+  int status = 0;
+  CUDA_TRY(lead, cudaMemcpyAsync(&status, lead->q_dev + lead->q_off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 lead->stream));
+  CUDA_TRY(lead, cudaStreamSynchronize(lead->stream));
+  if (status != 0)
+    return fail(lead, AJF_E_TIMEOUT, "step interpreter: a bounded device-side wait expired (code " +
+                                         std::to_string(status) + ")");
+  return AJF_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+ajf_status ajf_launch_queue(ajf_ctx* const* ctxs, int n_ctx, double* dev_results) {
+  Range nvtx_range("ajf step interpreter launch");
+  ajf_status st = check_queue_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  return launch_queue_ctxs(ctxs, n_ctx, dev_results, tuned_queue(ctxs, n_ctx));
+}
+
+ajf_status ajf_fidelity_batch_queue(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out) {
+  ajf_status st = check_queue_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  if (!out || (alg != 1 && alg != 2)) return fail(ctxs[0], AJF_E_ARG, "bad alg or out");
+  if (eps > 1.0) return fail(ctxs[0], AJF_E_ARG, "eps > 1");
+  for (int i = 0; i < n_ctx; ++i)
+    if (ctxs[i]->alg != alg) return fail(ctxs[i], AJF_E_STATE, "context without an Alg. " + std::to_string(alg) + " plan");
+  st = launch_queue_ctxs(ctxs, n_ctx, nullptr, tuned_queue(ctxs, n_ctx));
+  if (st != AJF_OK) return st;
+  st = queue_status(ctxs[0]);
+  if (st != AJF_OK) return st;
+  for (int i = 0; i < n_ctx; ++i) {
+    ajf_ctx* c = ctxs[i];
+    double res[3];
+    CUDA_TRY(c, cudaMemcpyAsync(res, c->arena + c->prog.off_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    st = check_status_words(c);
+    if (st != AJF_OK) return st;
+    out[i].S = res[0];
+    out[i].F = res[1];
+    out[i].one_minus_F = res[2];
+    out[i].traces_done = alg == 1 ? real_combinations(c) : 0;
+    out[i].equivalent = eps < 0 ? -1 : (res[1] > 1.0 - eps ? 1 : 0);
+    out[i].reserved = 0;
+    if (alg == 1) c->have_alg1 = true;
+  }
+  return AJF_OK;
+}
+
+ajf_status ajf_autotune_queue(ajf_ctx* const* ctxs, int n_ctx, int reps, int32_t* gemm_items, int32_t* body_tasks) {
+  ajf_status st = check_queue_batch(ctxs, n_ctx);
+  if (st != AJF_OK) return st;
+  if (reps < 1) return fail(ctxs[0], AJF_E_ARG, "reps < 1");
+  ajf_ctx* lead = ctxs[0];
+  CUDA_TRY(lead, cudaSetDevice(lead->device));
+  const bool prof = lead->profiling;
+  lead->profiling = false;
+  // candidate shapes: GEMM work items per task x tasks per CUDA-core phase; a shape must beat the
+  // best so far by 2% to replace it (timing noise)
+  const int items[3] = {1, 2, 4};
+  const int bodies[3] = {152, 304, 608};
+  QueueShape best;
+  float best_ms = -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(lead, cudaEventCreate(&e0));
+  CUDA_TRY(lead, cudaEventCreate(&e1));
+  for (int gi : items) {
+    for (int bt : bodies) {
+      QueueShape sh;
+      sh.gemm_items = gi;
+      sh.body_tasks = bt;
+      st = launch_queue_ctxs(ctxs, n_ctx, nullptr, sh);  // warm-up (tables, graph)
+      if (st == AJF_OK) st = queue_status(lead);
+      if (st != AJF_OK) break;
+      cudaEventRecord(e0, lead->stream);
+      for (int r = 0; r < reps && st == AJF_OK; ++r) st = launch_queue_ctxs(ctxs, n_ctx, nullptr, sh);
+      cudaEventRecord(e1, lead->stream);
+      if (st == AJF_OK) st = queue_status(lead);
+      if (st != AJF_OK) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best_ms < 0 || ms < 0.98f * best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+    if (st != AJF_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lead->profiling = prof;
+  if (st != AJF_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_queue[batch_signature(ctxs, n_ctx)] = best;
+  }
+  if (gemm_items) *gemm_items = best.gemm_items;
+  if (body_tasks) *body_tasks = best.body_tasks;
+  return AJF_OK;
+}
 
 ajf_status ajf_launch_persistent(ajf_ctx* const* ctxs, int n_ctx, double* dev_results) {
   Range nvtx_range("ajf persistent launch");

@@ -1,0 +1,735 @@
+// Device bodies of the contraction program's CUDA-core kernels (sm_103a), shared by the
+// standalone kernels (kernels.cu: one launch per program step, block index = blockIdx.x) and the
+// persistent step interpreter (queue.cu: one launch for many programs, whose thread blocks run
+// these bodies as tasks with virtual block indices).
+//
+// Every body runs on kBodyThreads = 256 threads (threads 0..255 of the block) and synchronises
+// them through the Sync policy: __syncthreads() in a standalone kernel, a named barrier of those
+// 256 threads in the interpreter, whose blocks carry more warps. Shared-memory scratch comes in
+// through pointers, so that the interpreter can place it in its own dynamic shared memory.
+//
+//  leaf_body        builds a leaf tensor of the miter network from the uploaded complex128
+//                   gate/Kraus matrices (gate, conjugate, adjoint, transpose, Kraus stack with an
+//                   open index, superoperator M_N = sum_k N_k (x) N_k^*; Sec. IV-A/IV-B).
+//  small_body       small pairwise contractions, one gather per operand element through 8-bit
+//                   offset tables (bits of any binary-index layout).
+//  splitk_body      contractions with few outputs and a long contracted index: FP64 partial sums
+//                   per block; splitk_done_body sums them in a fixed order (deterministic).
+//  dot_body         tiled full contraction to a scalar (the trace of a closed network).
+//  perm_body        gathers a complex tensor into a real, K-contiguous GEMM operand (the complex
+//                   product C = A B becomes the real product [[Ar,-Ai],[Ai,Ar]] [Br;Bi] = [Cr;Ci]),
+//                   in the operand format of the precision mode.
+//  split_sum_body   sums the FP64 K-split partial tiles of a tensor-core GEMM in a fixed order.
+//  open_body/final_body  the FP64 end of the path: t_i for Alg. I, sum |t_i|^2, F_J and 1 - F_J.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device.h"
+#include "fp_bits.h"
+
+namespace ajf {
+
+constexpr int kBodyThreads = 256;
+
+// Barrier policies of the bodies.
+struct SyncBlock {  // a standalone kernel of kBodyThreads threads
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+struct SyncBody {  // threads 0..kBodyThreads-1 of a larger block: named barrier 1
+  __device__ __forceinline__ static void sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBodyThreads) : "memory"); }
+};
+
+// ------------------------------------------------------------------ offset tables
+
+__device__ __forceinline__ int nchunks(int nbits) { return (nbits + 7) >> 3; }
+
+// Fill `tab` (nchunks * 256 entries) for map `m`; all threads of the block participate.
+__device__ __forceinline__ void build_table(const BitMap& m, int64_t* tab) {
+  const int nc = nchunks(m.nbits);
+  for (int e = threadIdx.x; e < nc * 256; e += kBodyThreads) {
+    const int c = e >> 8, v = e & 255;
+    int64_t off = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int bit = c * 8 + i;
+      if (bit < m.nbits && ((v >> i) & 1) && m.pos[bit] >= 0) off += int64_t(1) << m.pos[bit];
+    }
+    tab[e] = off;
+  }
+}
+
+__device__ __forceinline__ int64_t lookup(const int64_t* tab, int nc, int64_t idx) {
+  int64_t off = 0;
+  for (int c = 0; c < nc; ++c) off += tab[(c << 8) | ((idx >> (8 * c)) & 255)];
+  return off;
+}
+
+// ------------------------------------------------------------------ leaves
+
+// Element e of leaf L (complex, FP64) from the uploaded complex128 matrices.
+__device__ __forceinline__ void leaf_value(const LeafDev& L, const double* __restrict__ in, int64_t e, double& re,
+                                           double& im) {
+  re = 0;
+  im = 0;
+  const int a = L.a;
+  const int64_t dim = int64_t(1) << a;
+  switch (L.kind) {
+    case 0: case 1: case 2: case 3: {  // gate, conj, adjoint, transpose
+      const int64_t r = e >> a, c = e & (dim - 1);
+      const bool swap = (L.kind == 2 || L.kind == 3);
+      const int64_t idx = swap ? (c * dim + r) : (r * dim + c);
+      re = in[2 * (L.src + idx)];
+      im = in[2 * (L.src + idx) + 1];
+      if (L.kind == 1 || L.kind == 2) im = -im;
+      break;
+    }
+    case 4: {  // Kraus stack with open index kappa above the 2a operator bits
+      const int64_t kappa = e >> (2 * a);
+      const int64_t rc = e & (dim * dim - 1);
+      if (kappa < L.nk) {
+        re = in[2 * (L.src + kappa * dim * dim + rc)];
+        im = in[2 * (L.src + kappa * dim * dim + rc) + 1];
+      }
+      break;
+    }
+    case 5: {  // M_N over wires (q..., q'...): a = 2 * noise arity
+      const int an = a / 2;
+      const int64_t nd = int64_t(1) << an;
+      const int64_t R = e >> a, C = e & (dim - 1);
+      const int64_t o = R >> an, op = R & (nd - 1), i = C >> an, ip = C & (nd - 1);
+      for (int k = 0; k < L.nk; ++k) {
+        const int64_t base = L.src + int64_t(k) * nd * nd;
+        const double xr = in[2 * (base + o * nd + i)], xi = in[2 * (base + o * nd + i) + 1];
+        const double yr = in[2 * (base + op * nd + ip)], yi = -in[2 * (base + op * nd + ip) + 1];
+        re += xr * yr - xi * yi;
+        im += xr * yi + xi * yr;
+      }
+      break;
+    }
+    default:  // identity delta[out][in]
+      re = (e == 0 || e == 3) ? 1.0 : 0.0;
+      break;
+  }
+}
+
+// Index into the full (unsliced) leaf of element e of a leaf whose sliced labels are fixed:
+// e's bits fill the free positions from the lowest up, the sliced positions take fix_val.
+__device__ __forceinline__ int64_t leaf_full_index(const LeafDev& L, int64_t e) {
+  if (L.fix_mask == 0) return e;
+  int64_t full = L.fix_val;
+  int src = 0;
+  for (int p = 0; p < 16 && src < L.bits; ++p) {
+    if ((L.fix_mask >> p) & 1) continue;
+    full |= ((e >> src) & 1) << p;
+    ++src;
+  }
+  return full;
+}
+
+// One leaf per (virtual) block.
+template <typename T>
+__device__ __forceinline__ void leaf_body(const LeafDev* leaves, const double* __restrict__ in, T* __restrict__ arena,
+                                          int vb) {
+  const LeafDev L = leaves[vb];
+  const int64_t n = int64_t(1) << L.bits;
+  for (int64_t e = threadIdx.x; e < n; e += kBodyThreads) {
+    double re, im;
+    leaf_value(L, in, leaf_full_index(L, e), re, im);
+    arena[L.off + e] = static_cast<T>(re);
+    arena[L.off + L.plane + e] = static_cast<T>(im);
+  }
+}
+
+// ------------------------------------------------------------------ small contractions
+
+__device__ __forceinline__ int find_step(const StepDev* steps, int nsteps, int block) {
+  int lo = 0, hi = nsteps - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (steps[mid].block0 <= block) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, typename Acc, typename Sync>
+__device__ __forceinline__ void small_body(const StepDev* __restrict__ steps, int nsteps, int total_blocks,
+                                           T* __restrict__ arena, int vb, int64_t* tab) {
+  const int s = find_step(steps, nsteps, vb);
+  const StepDev& st = steps[s];
+  const int end = (s + 1 < nsteps) ? steps[s + 1].block0 : total_blocks;
+  const int nb = end - st.block0;
+  const int c_oa = nchunks(st.oa.nbits), c_ob = nchunks(st.ob.nbits);
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  int64_t* t_oa = tab;
+  int64_t* t_ob = t_oa + c_oa * 256;
+  int64_t* t_ka = t_ob + c_ob * 256;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  build_table(st.oa, t_oa);
+  build_table(st.ob, t_ob);
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  Sync::sync();
+  const int64_t nout = int64_t(1) << st.rc, nk = int64_t(1) << st.rk;
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  T* C = arena + st.c;
+  for (int64_t o = int64_t(vb - st.block0) * kBodyThreads + threadIdx.x; o < nout;
+       o += int64_t(nb) * kBodyThreads) {
+    const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
+    Acc re = 0, im = 0;
+    for (int64_t kk = 0; kk < nk; ++kk) {
+      const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+      const Acc ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+    C[o] = static_cast<T>(re);
+    C[st.pc + o] = static_cast<T>(im);
+  }
+}
+
+
+template <typename T, typename Sync>
+__device__ __forceinline__ void splitk_body(const StepDev* __restrict__ steps, int nsteps, const T* __restrict__ arena,
+                                            double2* __restrict__ partial, int vb, int64_t* tab, double* red_re,
+                                            double* red_im) {
+  const int s = find_step(steps, nsteps, vb);
+  const StepDev& st = steps[s];
+  const int local = vb - st.block0;
+  const int64_t o = local / st.nsplit;
+  const int split = local % st.nsplit;
+  const int c_oa = nchunks(st.oa.nbits), c_ob = nchunks(st.ob.nbits);
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  int64_t* t_oa = tab;
+  int64_t* t_ob = t_oa + c_oa * 256;
+  int64_t* t_ka = t_ob + c_ob * 256;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  build_table(st.oa, t_oa);
+  build_table(st.ob, t_ob);
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  Sync::sync();
+  const int64_t nk = int64_t(1) << st.rk;
+  const int64_t chunk = (nk + st.nsplit - 1) / st.nsplit;
+  const int64_t k0 = int64_t(split) * chunk;
+  const int64_t k1 = min(nk, k0 + chunk);
+  const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  double re = 0, im = 0;
+  for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += kBodyThreads) {
+    const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+    const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+    re += ar * br - ai * bi;
+    im += ar * bi + ai * br;
+  }
+  red_re[threadIdx.x] = re;
+  red_im[threadIdx.x] = im;
+  Sync::sync();
+  for (int w = kBodyThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + w];
+      red_im[threadIdx.x] += red_im[threadIdx.x + w];
+    }
+    Sync::sync();
+  }
+  if (threadIdx.x == 0) partial[st.poff + o * st.nsplit + split] = make_double2(red_re[0], red_im[0]);
+}
+
+
+// Full contraction S = sum_kk A[a(kk)] B[b(kk)] of two tensors (the trace of a closed network),
+// tiled so that both operands are read along their contiguous bits. A tile fixes all contracted
+// bits but ntl of them: the ones on A's lowest positions and the ones on B's lowest positions.
+// Phase 1 stages the tile of A in shared memory in A order (lanes along A's contiguous bits);
+// phase 2 streams the tile of B in B order and multiplies with the staged A values. FP64 partial
+// sums per block; k_splitk_done adds them in a fixed order. kF32 (reduced-precision modes): the
+// products of each tile are formed and summed in FP32 per thread (FP32 rounding of the operands,
+// relative error ~1e-7 per term) and the tile sums are accumulated in FP64.
+template <typename T, bool kF32, typename Sync>
+__device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int nsteps, const T* __restrict__ arena,
+                                         double2* __restrict__ partial, int vb, int64_t* tab, double* red_re,
+                                         double* red_im) {
+  const int s = find_step(steps, nsteps, vb);
+  const StepDev& st = steps[s];
+  const int split = vb - st.block0;
+  const int c_ka = nchunks(st.ka.nbits), c_kb = nchunks(st.kb.nbits);
+  const int ntl = st.ntl, nt = 1 << ntl;
+  int64_t* t_ka = tab;
+  int64_t* t_kb = t_ka + c_ka * 256;
+  int64_t* locA = t_kb + c_kb * 256;         // [nt] offset in A of tile-local index (A order)
+  int64_t* locB = locA + nt;                 // [nt] offset in B of tile-local index (B order)
+  double* sre = reinterpret_cast<double*>(locB + nt);
+  double* sim = sre + nt;
+  uint16_t* a_of_b = reinterpret_cast<uint16_t*>(sim + nt);  // B-order local index -> A-order
+  build_table(st.ka, t_ka);
+  build_table(st.kb, t_kb);
+  uint64_t tilemask = 0;
+  for (int i = 0; i < ntl; ++i) tilemask |= uint64_t(1) << st.tl[i];
+  for (int l = threadIdx.x; l < nt; l += kBodyThreads) {
+    int64_t oa = 0, ob = 0;
+    uint64_t kk = 0;
+    for (int i = 0; i < ntl; ++i) {
+      if ((l >> i) & 1) {
+        oa += int64_t(1) << st.ka.pos[st.tl[i]];
+        ob += int64_t(1) << st.kb.pos[st.tlb[i]];
+        kk |= uint64_t(1) << st.tlb[i];
+      }
+    }
+    locA[l] = oa;
+    locB[l] = ob;
+    int la = 0;  // A-order local index of the contracted-index value kk
+    for (int i = 0; i < ntl; ++i)
+      if ((kk >> st.tl[i]) & 1) la |= 1 << i;
+    a_of_b[l] = static_cast<uint16_t>(la);
+  }
+  Sync::sync();
+  const int64_t ntiles = int64_t(1) << (st.rk - ntl);
+  const T* A = arena + st.a;
+  const T* B = arena + st.b;
+  // the tile's base offsets in A and B: the tile number spread over the non-tile bits
+  auto tile_base = [&](int64_t t, int64_t& ba, int64_t& bb) {
+    uint64_t base = 0;
+    int64_t rem = t;
+    for (int i = 0; i < st.rk && rem; ++i) {
+      if ((tilemask >> i) & 1) continue;
+      if (rem & 1) base |= uint64_t(1) << i;
+      rem >>= 1;
+    }
+    ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
+    bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
+  };
+  // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
+  // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
+  // so the loads of two tiles are in flight. Staged A values sit at index l ^ ((l >> 5) & 31):
+  // B-ordered reads that stride across A's index (B's low bits on A's high bits) then fall into
+  // distinct shared-memory banks.
+  constexpr int kPer = 4;
+  double are[kPer], aim[kPer], bre[kPer], bim[kPer];
+  auto load_tile = [&](int64_t t) {
+    int64_t ba, bb;
+    tile_base(t, ba, bb);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int l = threadIdx.x + q * kBodyThreads;
+      if (l < nt) {
+        are[q] = A[ba + locA[l]];
+        aim[q] = A[st.pa + ba + locA[l]];
+        bre[q] = B[bb + locB[l]];
+        bim[q] = B[st.pb + bb + locB[l]];
+      }
+    }
+  };
+  double re = 0, im = 0;
+  int64_t t = split;
+  if (t < ntiles) load_tile(t);
+  while (t < ntiles) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int l = threadIdx.x + q * kBodyThreads;
+      if (l < nt) {
+        const int sl = l ^ ((l >> 5) & 31);
+        sre[sl] = are[q];
+        sim[sl] = aim[q];
+      }
+    }
+    double cbr[kPer], cbi[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      cbr[q] = bre[q];
+      cbi[q] = bim[q];
+    }
+    Sync::sync();
+    const int64_t tn = t + st.nsplit;
+    if (tn < ntiles) load_tile(tn);
+    if (kF32) {
+      float fre = 0.0f, fim = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int l = threadIdx.x + q * kBodyThreads;
+        if (l < nt) {
+          const int la = a_of_b[l];
+          const int sl = la ^ ((la >> 5) & 31);
+          const float ar = static_cast<float>(sre[sl]), ai = static_cast<float>(sim[sl]);
+          const float br = static_cast<float>(cbr[q]), bi = static_cast<float>(cbi[q]);
+          fre += ar * br - ai * bi;
+          fim += ar * bi + ai * br;
+        }
+      }
+      re += fre;
+      im += fim;
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int l = threadIdx.x + q * kBodyThreads;
+        if (l < nt) {
+          const int la = a_of_b[l];
+          const int sl = la ^ ((la >> 5) & 31);
+          const double ar = sre[sl], ai = sim[sl];
+          re += ar * cbr[q] - ai * cbi[q];
+          im += ar * cbi[q] + ai * cbr[q];
+        }
+      }
+    }
+    Sync::sync();
+    t = tn;
+  }
+  red_re[threadIdx.x] = re;
+  red_im[threadIdx.x] = im;
+  Sync::sync();
+  for (int w = kBodyThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + w];
+      red_im[threadIdx.x] += red_im[threadIdx.x + w];
+    }
+    Sync::sync();
+  }
+  if (threadIdx.x == 0) partial[st.poff + split] = make_double2(red_re[0], red_im[0]);
+}
+
+
+// Sum the split-K partials of every output in a fixed order (deterministic): with many splits a
+// whole block reduces each output (strided per-thread sums, then a tree), otherwise one thread
+// sums one output's splits.
+template <typename T, typename Sync>
+__device__ __forceinline__ void splitk_done_body(const StepDev* __restrict__ steps, const double2* __restrict__ partial,
+                                                 T* __restrict__ arena, double2* __restrict__ scalars, int vb,
+                                                 double* red_re, double* red_im) {
+  const StepDev& st = steps[vb];
+  const int64_t nout = int64_t(1) << st.rc;
+  auto emit = [&](int64_t o, double re, double im) {
+    if (st.scalar_slot >= 0) {
+      scalars[st.scalar_slot] = make_double2(re, im);
+    } else {
+      arena[st.c + o] = static_cast<T>(re);
+      arena[st.c + st.pc + o] = static_cast<T>(im);
+    }
+  };
+  if (st.nsplit >= 64) {
+    for (int64_t o = 0; o < nout; ++o) {
+      double re = 0, im = 0;
+      for (int sp = threadIdx.x; sp < st.nsplit; sp += kBodyThreads) {
+        const double2 v = partial[st.poff + o * st.nsplit + sp];
+        re += v.x;
+        im += v.y;
+      }
+      red_re[threadIdx.x] = re;
+      red_im[threadIdx.x] = im;
+      Sync::sync();
+      for (int w = kBodyThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+          red_re[threadIdx.x] += red_re[threadIdx.x + w];
+          red_im[threadIdx.x] += red_im[threadIdx.x + w];
+        }
+        Sync::sync();
+      }
+      if (threadIdx.x == 0) emit(o, red_re[0], red_im[0]);
+      Sync::sync();
+    }
+    return;
+  }
+  for (int64_t o = threadIdx.x; o < nout; o += kBodyThreads) {
+    double re = 0, im = 0;
+    for (int sp = 0; sp < st.nsplit; ++sp) {
+      const double2 v = partial[st.poff + o * st.nsplit + sp];
+      re += v.x;
+      im += v.y;
+    }
+    emit(o, re, im);
+  }
+}
+
+
+// ------------------------------------------------------------------ GEMM operand preparation
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// The six-product bf16 split makes its leading term a fixed-point number: an integer multiple of
+// q = 2^qexp with |x_0 / q| <= 2^8, q fixed per operand row and 128-byte K block (64 elements).
+// Then every product of leading terms within one K block is a multiple of q_a q_b below
+// 2^16 q_a q_b, and their block sum of 64 stays below 2^24 q_a q_b, so the tensor core's FP32
+// accumulation of the leading product is exact (it truncates nothing). The remainder x - x_0
+// (exact in FP32, |.| <= q/2) is split into the middle and low terms in floating point, which
+// keeps x to 2^-26 of the block's largest entry. The two-term splits keep a floating leading term:
+// with a fixed-point one their single correction term would leave entries far below the block's
+// largest with only its 8 or 11 bits.
+__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_BF16X3; }
+__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_BF16X3 ? 8 : 0; }
+
+// qexp for a row block whose largest magnitude is m: q = 2^(floor(log2 m) + 1 - lead bits), so
+// that m / q < 2^lead bits; clamped to the normal FP32 range (zero blocks take the floor).
+__device__ __forceinline__ int quantum_exp(float m, int lead) {
+  const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xFFu) - 127;  // floor(log2 m), m normal
+  const int qe = e + 1 - lead;
+  return qe < -126 ? -126 : qe;
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float(static_cast<uint32_t>(127 + e) << 23); }
+
+// Leading term of x: rint(x / q) q, exact (power-of-two scalings of a float with |x / q| < 2^9).
+__device__ __forceinline__ float lead_term(float x, int qexp) { return rintf(x * pow2f(-qexp)) * pow2f(qexp); }
+
+// Two consecutive operand elements (idx even) of the FP64 operand mode.
+__device__ __forceinline__ void store_operand2_f64(const PermDev& p, char* base, int64_t idx, double v0, double v1) {
+  *reinterpret_cast<double2*>(reinterpret_cast<double*>(base + p.dst[0]) + idx) = make_double2(v0, v1);
+}
+
+// Two consecutive operand elements (idx even, same row and K block) of an FP32-based operand mode
+// (the values already rounded to FP32), with one vector store per split term. qexp: the block's
+// leading-term quantum (six-product split only).
+__device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int64_t idx, float x0, float x1,
+                                               int qexp) {
+  switch (p.mode) {
+    case OPM_F32:
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(x0, x1);
+      break;
+    case OPM_TF32:
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) =
+          make_float2(to_tf32(x0), to_tf32(x1));
+      break;
+    case OPM_TF32X2: {  // floating split: hi = tf32(x), lo = tf32(x - hi)
+      const float h0 = to_tf32(x0), h1 = to_tf32(x1);
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[0]) + idx) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(base + p.dst[1]) + idx) =
+          make_float2(to_tf32(x0 - h0), to_tf32(x1 - h1));
+      break;
+    }
+    case OPM_BF16X2: {  // floating split: hi = bf16(x), lo = bf16(x - hi)
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) =
+          __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+      break;
+    }
+    default: {  // OPM_BF16X3: fixed-point leading term, floating middle and low terms
+      const float h0 = lead_term(x0, qexp), h1 = lead_term(x1, qexp);
+      const float r0 = x0 - h0, r1 = x1 - h1;
+      const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+      const float2 mf = __bfloat1622float2(m);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) =
+          __floats2bfloat162_rn(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) = m;
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[2]) + idx) =
+          __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+      break;
+    }
+  }
+}
+
+// Tile of 32 rows x TK k per iteration, 256 threads; TK = 32, or for the six-product bf16 split
+// 64 = one 128-byte K block of the operand (the leading-term quantum is fixed per row and block).
+// The tile is staged in shared memory in S: double for the FP64 operand mode, float for every
+// other mode (which splits the FP32 rounding of each value), so that a 32 x 64 float tile takes
+// the space of a 32 x 32 double one. The source offsets of the tile's rows and columns are
+// computed once per tile; loads run with lanes along whichever index is contiguous in the source,
+// stores with lanes along k and two elements per vector store.
+// Shared-memory scratch of one gather block (the tile in S, row and column offsets, quanta).
+template <typename S>
+struct PermSmem {
+  static constexpr int TKMAX = sizeof(S) == 8 ? 32 : 64;
+  S tre[32][TKMAX + 1], tim[32][TKMAX + 1];
+  int64_t roff[32], koff[TKMAX];
+  int qre[32], qim[32];
+};
+
+template <typename S, typename Sync>
+__device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, const double* __restrict__ arena,
+                                          char* __restrict__ base, int vb, int vg, int vy, int64_t* tab,
+                                          PermSmem<S>& sm) {
+  constexpr int TKMAX = PermSmem<S>::TKMAX;
+  auto& tre = sm.tre;
+  auto& tim = sm.tim;
+  auto& roff = sm.roff;
+  auto& koff = sm.koff;
+  auto& qre = sm.qre;
+  auto& qim = sm.qim;
+  const PermDev& p = perms[vy];
+  const int c_r = nchunks(p.rows.nbits), c_k = nchunks(p.cols.nbits);
+  int64_t* t_r = tab;
+  int64_t* t_k = tab + c_r * 256;
+  build_table(p.rows, t_r);
+  build_table(p.cols, t_k);
+  Sync::sync();
+  const bool split = sizeof(S) == 4 && split_mode(p.mode);
+  const int lead = lead_bits(p.mode);
+  // K block of the six-product split in complex k: 64 elements of one plane; with K below that,
+  // one block holds both planes of the row (Re and -Im, or Im and Re, or Re and Im)
+  const int W = split ? 64 : 32;
+  const int TR = p.rbits >= 5 ? 32 : (1 << p.rbits);
+  const int TK = p.kbits >= 6 && W == 64 ? 64 : (p.kbits >= 5 ? 32 : (1 << p.kbits));
+  const bool joint = (int64_t(1) << p.kbits) < W;  // the quantum spans both planes
+  const int KW = TK > 32 ? 64 : 32;                // k extent of the thread mapping
+  const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
+  const int64_t ntr = R / TR, ntk = K / TK;
+  const double* src = arena + p.src;
+  const int64_t ld = 2 * K;
+  for (int64_t tile = vb; tile < ntr * ntk; tile += vg) {
+    const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
+    if (threadIdx.x < 32) roff[threadIdx.x] = threadIdx.x < TR ? lookup(t_r, c_r, r0 + threadIdx.x) : 0;
+    else if (threadIdx.x < 32 + TKMAX)
+      koff[threadIdx.x - 32] = threadIdx.x - 32 < TK ? lookup(t_k, c_k, k0 + threadIdx.x - 32) : 0;
+    Sync::sync();
+    // all loads (x 2 planes) of a thread are issued before its shared-memory stores
+    double vr[8], vi[8];
+#pragma unroll
+    for (int q = 0; q < TKMAX / 8; ++q) {
+      if (q < KW / 8) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
+        if (rr < TR && kk < TK) {
+          const int64_t off = roff[rr] + koff[kk];
+          vr[q] = src[off];
+          vi[q] = src[p.plane + off];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < TKMAX / 8; ++q) {
+      if (q < KW / 8) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
+        if (rr < TR && kk < TK) {
+          tre[rr][kk] = static_cast<S>(vr[q]);
+          tim[rr][kk] = static_cast<S>(vi[q]);
+        }
+      }
+    }
+    Sync::sync();
+    if (split) {
+      // per row: the largest |Re| and |Im| of the tile's k range (of the FP32 values that are
+      // split), one warp per four rows
+      const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+      for (int i = wp; i < TR; i += 8) {
+        float mr = 0.f, mi = 0.f;
+        for (int k = ln; k < TK; k += 32) {
+          mr = fmaxf(mr, fabsf(static_cast<float>(tre[i][k])));
+          mi = fmaxf(mi, fabsf(static_cast<float>(tim[i][k])));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+          mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+        }
+        if (ln == 0) {
+          if (joint) mr = mi = fmaxf(mr, mi);
+          qre[i] = quantum_exp(mr, lead);
+          qim[i] = quantum_exp(mi, lead);
+        }
+      }
+      Sync::sync();
+    }
+    const int pairs = TK >> 1;
+    for (int w = threadIdx.x; w < TR * pairs; w += kBodyThreads) {
+      const int i = w / pairs, j = 2 * (w % pairs);
+      const int64_t r = r0 + i, k = k0 + j;
+      if constexpr (sizeof(S) == 8) {
+        const double re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+        if (p.embed) {
+          store_operand2_f64(p, base, r * ld + k, re0, re1);             // (s=0, t=0):  Re
+          store_operand2_f64(p, base, r * ld + K + k, -im0, -im1);       // (s=0, t=1): -Im
+          store_operand2_f64(p, base, (R + r) * ld + k, im0, im1);       // (s=1, t=0):  Im
+          store_operand2_f64(p, base, (R + r) * ld + K + k, re0, re1);   // (s=1, t=1):  Re
+        } else {
+          store_operand2_f64(p, base, r * ld + k, re0, re1);
+          store_operand2_f64(p, base, r * ld + K + k, im0, im1);
+        }
+      } else {
+        const float re0 = tre[i][j], re1 = tre[i][j + 1], im0 = tim[i][j], im1 = tim[i][j + 1];
+        const int qr = split ? qre[i] : 0, qi = split ? qim[i] : 0;
+        if (p.embed) {
+          store_operand2(p, base, r * ld + k, re0, re1, qr);             // (s=0, t=0):  Re
+          store_operand2(p, base, r * ld + K + k, -im0, -im1, qi);       // (s=0, t=1): -Im
+          store_operand2(p, base, (R + r) * ld + k, im0, im1, qi);       // (s=1, t=0):  Im
+          store_operand2(p, base, (R + r) * ld + K + k, re0, re1, qr);   // (s=1, t=1):  Re
+        } else {
+          store_operand2(p, base, r * ld + k, re0, re1, qr);
+          store_operand2(p, base, r * ld + K + k, im0, im1, qi);
+        }
+      }
+    }
+    Sync::sync();
+  }
+}
+
+
+// ------------------------------------------------------------------ final FP64 reduction
+
+template <typename T, typename Sync>
+__device__ __forceinline__ void open_body(const FinalDev* __restrict__ fd, const T* __restrict__ arena,
+                                          const double2* __restrict__ scalars, double* __restrict__ traces,
+                                          double* __restrict__ partial, int vb, int vg, int64_t* tab, double* red) {
+  const FinalDev& f = *fd;
+  // common factor: product of scalar components and 2 per untouched wire
+  double sr = ldexp(1.0, f.loops), si = 0;
+  for (int i = 0; i < f.n_scalars; ++i) {
+    const double2 v = scalars[i];
+    const double nr = sr * v.x - si * v.y, ni = sr * v.y + si * v.x;
+    sr = nr;
+    si = ni;
+  }
+  const int c = nchunks(f.open_map.nbits);
+  build_table(f.open_map, tab);
+  Sync::sync();
+  const int64_t n = int64_t(1) << f.open_bits;
+  double acc = 0;
+  for (int64_t j = int64_t(vb) * kBodyThreads + threadIdx.x; j < n; j += int64_t(vg) * kBodyThreads) {
+    double tr = 1, ti = 0;
+    if (f.open_off >= 0) {
+      const int64_t off = lookup(tab, c, j);
+      tr = static_cast<double>(arena[f.open_off + off]);
+      ti = static_cast<double>(arena[f.open_off + f.open_plane + off]);
+    }
+    const double vr = tr * sr - ti * si, vi = tr * si + ti * sr;
+    traces[2 * j] = vr;
+    traces[2 * j + 1] = vi;
+    acc += vr * vr + vi * vi;
+  }
+  red[threadIdx.x] = acc;
+  Sync::sync();
+  for (int w = kBodyThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    Sync::sync();
+  }
+  if (threadIdx.x == 0) partial[vb] = red[0];
+}
+
+// Thread 0 only.
+__device__ __forceinline__ void final_body(const FinalDev* __restrict__ fd, const double2* __restrict__ scalars,
+                                           const double* __restrict__ partial, double* __restrict__ result) {
+  const FinalDev& f = *fd;
+  double S = 0;
+  if (f.alg == 2) {
+    double sr = ldexp(1.0, f.loops), si = 0;
+    for (int i = 0; i < f.n_scalars; ++i) {
+      const double2 v = scalars[i];
+      const double nr = sr * v.x - si * v.y, ni = sr * v.y + si * v.x;
+      sr = nr;
+      si = ni;
+    }
+    S = sr;
+  } else {
+    for (int b = 0; b < f.nblocks; ++b) S += partial[b];
+  }
+  const double d2 = ldexp(1.0, 2 * f.n_qubits);
+  result[0] = S;
+  result[1] = S / d2;
+  result[2] = (d2 - S) / d2;
+}
+
+// C[i] = sum over splits s (in order) of W[s][i], block vb of vg.
+__device__ __forceinline__ void split_sum_body(const double* __restrict__ W, int ksplit, int64_t n,
+                                               double* __restrict__ C, int vb, int vg) {
+  for (int64_t i = int64_t(vb) * kBodyThreads + threadIdx.x; i < n; i += int64_t(vg) * kBodyThreads) {
+    double v = 0;
+    for (int s = 0; s < ksplit; ++s) v += W[s * n + i];
+    C[i] = v;
+  }
+}
+
+}  // namespace ajf

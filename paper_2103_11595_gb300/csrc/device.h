@@ -100,3 +100,62 @@ struct InterpOp {
 };
 
 }  // namespace ajf
+
+namespace ajf {
+
+// ------------------------------------------------------------------ persistent step interpreter
+// One launch (k_queue, queue.cu) runs the default-lowered programs of many networks: every launch
+// of every program becomes a phase, every phase a few tasks (ranges of the kernel's blocks, or of
+// a tensor-core GEMM's work items), and the tasks form one queue that the launch's persistent
+// thread blocks take in order. A task waits until the previous phase of its program is complete,
+// which keeps each program's launch order; different programs overlap freely.
+
+enum QKind : int32_t {
+  QK_LEAVES = 0,       // leaf_body, one block per leaf
+  QK_SMALL = 1,        // small_body
+  QK_SPLITK = 2,       // splitk_body
+  QK_SPLITK_DONE = 3,  // splitk_done_body, one block per step
+  QK_DOT = 4,          // dot_body
+  QK_PERM = 5,         // perm_body, blocks = grid_x * (number of perms)
+  QK_GEMM = 6,         // tensor-core GEMM work items
+  QK_SPLIT_SUM = 7,    // split_sum_body over the K-split workspace
+  QK_OPEN = 8,         // open_body
+  QK_FINAL = 9,        // final_body (one block)
+};
+
+struct QPhase {
+  int32_t kind;
+  int32_t ntasks;      // tasks of the phase: its completion count
+  int32_t prev;        // phase that must be complete first (-1: none)
+  int32_t nblocks;     // the kernel's blocks, or the GEMM's work items
+  int32_t count;       // steps / perms / leaves of the launch
+  int32_t grid_x;      // QK_PERM: blocks per perm
+  int32_t flag;        // QK_DOT: FP32 products; QK_GEMM: bf16 operands
+  int32_t bn;          // QK_GEMM: tile width
+  int32_t ksplit;      // QK_SPLIT_SUM: splits
+  int32_t pad;
+  int64_t n;           // QK_SPLIT_SUM: elements of the result
+  char* base;          // the program's arena
+  const void* desc;    // steps / perms / leaves / final record (device)
+  const void* gemm;    // QK_GEMM: the GEMM's parameter block (device, 64-byte aligned)
+  // per kind: LEAVES p0 = packed inputs; SPLITK / DOT p0 = split partials; SPLITK_DONE p0 =
+  // partials, p1 = scalar slots; SPLIT_SUM p0 = workspace, p1 = result; OPEN p0 = scalar slots,
+  // p1 = traces, p2 = block partials; FINAL p0 = scalar slots, p1 = result, p2 = block partials,
+  // p3 = optional copy of (S, F, 1 - F)
+  double* p0;
+  double* p1;
+  double* p2;
+  double* p3;
+};
+
+struct QTask {
+  int32_t phase;
+  int32_t b0, b1;      // blocks (work items) [b0, b1) of the phase
+  int32_t pad;
+};
+
+// Counters of one interpreter launch (int32, zeroed before it): the next task to take, an error
+// flag (a bounded wait expired), then one completion count per phase.
+constexpr int kQNext = 0, kQError = 1, kQPhase0 = 4;
+
+}  // namespace ajf
