@@ -446,6 +446,14 @@ ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
 ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t N, int64_t K, const void *A,
                              const void *B, double *C);
 
+/* Self-test of the step interpreter's failure path (no paper counterpart; used by the test suite):
+ * one launch on device `device` whose second task waits for a first phase that can never
+ * complete, with every wait bounded by wait_ms (0 < wait_ms <= 10000). The wait expires, the
+ * kernel records code 21 in *code, every block stops taking tasks and returns, and the call
+ * reports AJF_E_TIMEOUT; the device stays usable. Allocates and frees its own device memory and
+ * synchronises the device. Errors: AJF_E_ARG, AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT (expected). */
+ajf_status ajf_selftest_queue_timeout(int device, double wait_ms, int32_t *code);
+
 /* Self-test of one real product through the path's own operand preparation and tensor-core GEMM
  * (no paper counterpart; used by the test suite): C[M][N] = A[M][K] . B[N][K]^T for FP64 A and B
  * (row-major, host memory), on device `device`, in precision mode `precision` (AJF_PREC_TF32,

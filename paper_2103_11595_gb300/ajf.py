@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
             "ajf_launch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
             "ajf_launch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_selftest_queue_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
             "ajf_fidelity_batch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D,
                                                ctypes.POINTER(Result)]),
             "ajf_autotune_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(I32),
@@ -492,6 +493,13 @@ def ajf_launch_queue(ctxs: Sequence, dev_results: int = 0) -> None:
     st = lib().ajf_launch_queue(arr, len(ctxs), ctypes.c_void_p(dev_results) if dev_results else None)
     if st != AJF_OK:
         raise AjfError(st, ajf_last_error(ctxs[0]))
+
+
+def ajf_selftest_queue_timeout(device: int, wait_ms: float) -> tuple:
+    """(status, code): AJF_E_TIMEOUT and code 21 when the interpreter's bounded wait works."""
+    code = ctypes.c_int32()
+    st = lib().ajf_selftest_queue_timeout(int(device), float(wait_ms), ctypes.byref(code))
+    return int(st), int(code.value)
 
 
 def ajf_fidelity_batch_queue(ctxs: Sequence, alg: int, eps: float = -1.0) -> list:

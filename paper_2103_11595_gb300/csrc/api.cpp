@@ -1723,6 +1723,50 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
   return st;
 }
 
+ajf_status ajf_selftest_queue_timeout(int device, double wait_ms, int32_t* code) {
+  if (!code || !(wait_ms > 0) || wait_ms > 10000) return AJF_E_ARG;
+  *code = 0;
+  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
+  // phase 0 declares two tasks but the queue holds one of them, so the task of phase 1, which
+  // waits for phase 0 to complete, waits for a count that never arrives
+  const size_t off_tasks = 1024, off_counters = 2048, off_status = 3072, off_data = 4096;
+  char* d = nullptr;
+  if (cudaMalloc(&d, off_data + 1024) != cudaSuccess) return AJF_E_NOMEM;
+  QPhase ph[2];
+  std::memset(ph, 0, sizeof(ph));
+  for (int i = 0; i < 2; ++i) {
+    ph[i].kind = QK_SPLIT_SUM;
+    ph[i].nblocks = 1;
+    ph[i].n = 1;
+    ph[i].ksplit = 1;
+    ph[i].p0 = reinterpret_cast<double*>(d + off_data);
+    ph[i].p1 = reinterpret_cast<double*>(d + off_data + 512);
+  }
+  ph[0].ntasks = 2;
+  ph[0].prev = -1;
+  ph[1].ntasks = 1;
+  ph[1].prev = 0;
+  QTask tk[2] = {{0, 0, 1, 0}, {1, 0, 1, 0}};
+  ajf_status st = AJF_OK;
+  if (cudaMemcpy(d, ph, sizeof(ph), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d + off_tasks, tk, sizeof(tk), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d + off_status, 0, 1024) != cudaSuccess || cudaMemset(d + off_data, 0, 1024) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK &&
+      launch_queue(reinterpret_cast<const QPhase*>(d), 2, reinterpret_cast<const QTask*>(d + off_tasks), 2,
+                   reinterpret_cast<int*>(d + off_counters), reinterpret_cast<int*>(d + off_status), 2, 0,
+                   static_cast<unsigned long long>(wait_ms * 1e6)) != cudaSuccess)
+    st = AJF_E_CUDA;
+  if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
+  int status = 0;
+  if (st == AJF_OK && cudaMemcpy(&status, d + off_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = AJF_E_CUDA;
+  cudaFree(d);
+  if (st != AJF_OK) return st;
+  *code = status;
+  return status != 0 ? AJF_E_TIMEOUT : AJF_OK;
+}
+
 ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t N, int64_t K, const double* A,
                                    const double* B, double* C) {
   if (!A || !B || !C) return AJF_E_ARG;

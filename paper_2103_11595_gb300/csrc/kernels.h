@@ -67,20 +67,20 @@ cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, con
                             double* C, int64_t M, int64_t N, int64_t K, int kind, double* ws, int ksplit,
                             int* d_status, unsigned long long wait_ns, int stall_loads);
 cudaError_t tc_gemm_run(const TcPrepared& t, cudaStream_t s);
+// Bound of every device-side wait in the GEMM and the step interpreter (nanoseconds).
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
 // Persistent step interpreter (queue.cu): one launch of `blocks` blocks (at most one per SM) runs
 // the tasks of the phases (device tables; see device.h). d_counters: kQPhase0 + nphases ints,
 // zeroed by the launch. A dependency wait that expires sets *d_status (code 21) and the error
 // counter; a GEMM wait sets its own code, as in the standalone kernel.
 size_t queue_smem_bytes();
 cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tasks, int ntasks, int* d_counters,
-                         int* d_status, int blocks, cudaStream_t s);
+                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns = kTcWaitNs);
 // A prepared tensor-core GEMM's parameter block for the interpreter (its fixed pipeline geometry),
 // written to `out` (queue_gemm_params_bytes() bytes, 64-byte aligned in device memory when used);
 // its tile width, operand kind and work-item count.
 size_t queue_gemm_params_bytes();
 cudaError_t queue_gemm_params(const TcPrepared& t, void* out, int* bn, int* bf16, int* nwork);
-// Bound of every device-side wait in the GEMM (nanoseconds).
-constexpr unsigned long long kTcWaitNs = 2000000000ull;
 cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
                            int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s);
 // Same with an explicit bound on every device-side wait and a test hook: stall_loads = 1 makes the

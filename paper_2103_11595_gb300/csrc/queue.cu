@@ -53,6 +53,14 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 template <int BN, bool BF16>
 __device__ __noinline__ bool gemm_task(const QPhase& ph, const QTask& t, const TcShared& sh, TcRing& ring) {
   const TcParams& p = *static_cast<const TcParams*>(ph.gemm);
+  if (threadIdx.x == 0) {
+    // the tensor maps live in global memory (written before the launch): acquire them for the
+    // tensor-map proxy before the producer's first TMA load through them
+    for (int i = 0; i < p.terms; ++i) {
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.amap[i]) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.bmap[i]) : "memory");
+    }
+  }
   return tc_gemm_items<BN, BF16>(p, static_cast<uint32_t>(t.b0), static_cast<uint32_t>(t.b1), 1u, sh, ring);
 }
 
@@ -252,7 +260,7 @@ cudaError_t queue_gemm_params(const TcPrepared& t, void* out, int* bn, int* bf16
 size_t queue_gemm_params_bytes() { return (sizeof(TcParams) + 1023) / 1024 * 1024; }
 
 cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tasks, int ntasks, int* d_counters,
-                         int* d_status, int blocks, cudaStream_t s) {
+                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns) {
   if (ntasks == 0) return cudaSuccess;
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -265,7 +273,7 @@ cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tas
   }
   e = cudaMemsetAsync(d_counters, 0, sizeof(int) * (kQPhase0 + static_cast<size_t>(nphases)), s);
   if (e != cudaSuccess) return e;
-  k_queue<<<blocks, kThreads, kQSmem, s>>>(d_phases, d_tasks, ntasks, d_counters, d_status, kTcWaitNs);
+  k_queue<<<blocks, kThreads, kQSmem, s>>>(d_phases, d_tasks, ntasks, d_counters, d_status, wait_ns);
   return cudaGetLastError();
 }
 
