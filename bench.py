@@ -247,6 +247,8 @@ def main():
                     help="first mid-config seed (per-seed profiler captures)")
     ap.add_argument("--persistent-flops", type=float, default=2e6,
                     help="batching workload: networks up to this many flops run in the persistent kernel")
+    ap.add_argument("--no-queue", action="store_true",
+                    help="batching workload: skip the one-launch step-interpreter run")
     ap.add_argument("--no-batching", action="store_true",
                     help="mid workload: skip the batching-workload block of the line")
     ap.add_argument("--no-oracle-parity", action="store_true",
@@ -505,8 +507,8 @@ def main():
         batching = small_networks_line(bargs, world, rank, local)
         if rank == 0:
             batching = {k: batching[k] for k in ("value", "unit", "ms_per_step", "us_per_eval", "traces_per_s",
-                                                  "e2e", "default_path", "oracle_parity", "roofline", "config",
-                                                  "gpu_launches", "clocks", "dtype")}
+                                                  "e2e", "default_path", "one_launch", "oracle_parity", "roofline",
+                                                  "config", "gpu_launches", "clocks", "dtype")}
 
     if rank == 0:
         line = {
@@ -759,6 +761,53 @@ def small_networks_line(args, world, rank, local):
         for c in dctx:
             c.close()
 
+    # the same jobs in ONE launch of the persistent step interpreter (every network's default-lowered
+    # program, tensor-core GEMM tiles included, as one task queue; the launch is a CUDA graph),
+    # with its task shape autotuned first
+    one_launch = None
+    if args.workload == "batching" and not args.no_queue:
+        qctx = []
+        for inst, alg in jobs:
+            c = ajf.Context(dev, stream.cuda_stream)
+            ajf.load_instance(c.handle, inst)
+            ajf.ajf_plan(c.handle, alg, precision=args.precision, trials=args.trials)
+            ajf.ajf_upload(c.handle)
+            qctx.append(c)
+        qh = [c.handle for c in qctx]
+        qout = torch.zeros(n_jobs, 3, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            shape = ajf.ajf_autotune_queue(qh, reps=3)
+            for _ in range(max(3, args.warmup)):
+                ajf.ajf_launch_queue(qh, qout.data_ptr())
+            torch.cuda.synchronize()
+            q_ms = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ajf.ajf_launch_queue(qh, qout.data_ptr())
+                e1.record(stream)
+                e1.synchronize()
+                q_ms += e0.elapsed_time(e1)
+            ajf.ajf_profile_enable(qh[0], True)
+            ajf.ajf_launch_queue(qh, qout.data_ptr())
+            stream.synchronize()
+            qprof = ajf.ajf_queue_profile(qh[0])
+            ajf.ajf_profile_enable(qh[0], False)
+        F_q = qout[:, 1].cpu().numpy().copy()
+        q_s = max_over_ranks(q_ms / 1e3, world)
+        one_launch = {"value": n_jobs * args.steps * world / q_s, "unit": "evals/s",
+                      "ms_per_step": q_s * 1e3 / args.steps, "gpu_launches_per_step": 1,
+                      "task_shape": {"gemm_items_per_task": shape[0], "tasks_per_cuda_core_launch": shape[1]},
+                      "max_abs_dF_vs_default_path_run": float(np.max(np.abs(F_q - F_ord))),
+                      "task_busy_s": {k: round(v["busy_s"], 6) for k, v in qprof.items() if v["tasks"]},
+                      "task_wait_s": {k: round(v["wait_s"], 6) for k, v in qprof.items() if v["tasks"]},
+                      "path": "all networks, default lowering in " + args.precision + ", in one persistent "
+                              "step-interpreter launch replayed as a CUDA graph (ajf_launch_queue)"}
+        for c in qctx:
+            c.close()
+
     # end to end: load + plan (structural cache) per network, one batch call from host arrays
     e2e_ctx = pers + big
     packed = [ajf.pack_instance(inst) for inst, _ in jobs]  # the caller's flat host arrays
@@ -825,7 +874,7 @@ def small_networks_line(args, world, rank, local):
                        "parallelism": f"{world} independent ranks (weak scaling)"},
             "traces_per_s": n_traces * args.steps * world / total_s,
             "roofline": roof, "default_path": default, "e2e": e2e, "cpu_baseline": cpu,
-            "oracle_parity": parity,
+            "oracle_parity": parity, "one_launch": one_launch,
             "gpu_launches": (len(groups) + sum(i["n_launches"] for i, (k, _) in zip(infos, order) if k == "b"))
                             * args.steps,
             "clocks": clocks,

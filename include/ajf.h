@@ -524,6 +524,15 @@ ajf_status ajf_launch_queue(ajf_ctx *const *ctxs, int n_ctx, double *dev_results
  * algorithm), AJF_E_TIMEOUT (a bounded device-side wait expired; the launch returned early). */
 ajf_status ajf_fidelity_batch_queue(ajf_ctx *const *ctxs, int n_ctx, int alg, double eps, ajf_result *out);
 
+/* Task-level timing of the step-interpreter launches led by ctx (no paper counterpart), taken by
+ * launches made while ajf_profile_enable is on: for each kind of task k (0 leaves, 1 small steps,
+ * 2 split-K, 3 split-K sums, 4 tiled traces, 5 operand gathers, 6 tensor-core GEMM work items,
+ * 7 K-split sums, 8 open-tensor traces, 9 final), out[3k] = seconds the blocks spent running them,
+ * out[3k + 1] = seconds they waited for the previous launch of the same program, out[3k + 2] =
+ * tasks run; at most `cap` values. reset != 0 zeroes the counters. Synchronises ctx's stream.
+ * Errors: AJF_E_ARG, AJF_E_STATE (no interpreter launch led by ctx), AJF_E_CUDA. */
+ajf_status ajf_queue_profile(ajf_ctx *ctx, double *out, int cap, int reset);
+
 /* Autotuner of the step interpreter's work decomposition (no paper counterpart): times `reps`
  * launches over the batch for each shape -- tensor-core GEMM work items (128 x BN tiles or K
  * splits) per task in {1, 2, 4}, and tasks per CUDA-core launch in {152, 304, 608} -- and keeps the

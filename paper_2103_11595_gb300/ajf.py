@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "ajf_profile_read": (I32, [P, ctypes.POINTER(KernelStats), ctypes.c_int]),
             "ajf_launch_persistent": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
             "ajf_launch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "ajf_queue_profile": (I32, [P, P, ctypes.c_int, ctypes.c_int]),
             "ajf_selftest_queue_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
             "ajf_fidelity_batch_queue": (I32, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, D,
                                                ctypes.POINTER(Result)]),
@@ -500,6 +501,18 @@ def ajf_selftest_queue_timeout(device: int, wait_ms: float) -> tuple:
     code = ctypes.c_int32()
     st = lib().ajf_selftest_queue_timeout(int(device), float(wait_ms), ctypes.byref(code))
     return int(st), int(code.value)
+
+
+QUEUE_TASK_KINDS = ["leaves", "small", "splitk", "splitk_done", "dot", "gather", "gemm_tc", "split_sum", "open",
+                    "final"]
+
+
+def ajf_queue_profile(ctx, reset: bool = True) -> dict:
+    """Per kind of interpreter task: busy seconds, seconds waiting for the previous launch, tasks."""
+    out = np.zeros(3 * len(QUEUE_TASK_KINDS))
+    _check(ctx, lib().ajf_queue_profile(ctx, _ptr(out), out.size, 1 if reset else 0))
+    return {k: {"busy_s": out[3 * i], "wait_s": out[3 * i + 1], "tasks": int(out[3 * i + 2])}
+            for i, k in enumerate(QUEUE_TASK_KINDS)}
 
 
 def ajf_fidelity_batch_queue(ctxs: Sequence, alg: int, eps: float = -1.0) -> list:

@@ -2549,7 +2549,11 @@ ajf_status launch_queue_ctxs(ajf_ctx* const* ctxs, int n_ctx, double* dev_result
   };
   if (lead->profiling) {
     ProfScope ps(lead, s0, 7, lead->q_flops, lead->q_bytes);
-    const cudaError_t e = enqueue(s0);
+    const cudaError_t e = launch_queue(
+        reinterpret_cast<const QPhase*>(lead->q_dev + lead->q_off_phases), lead->q_nphases,
+        reinterpret_cast<const QTask*>(lead->q_dev + lead->q_off_tasks), lead->q_ntasks,
+        reinterpret_cast<int*>(lead->q_dev + lead->q_off_counters), reinterpret_cast<int*>(lead->q_dev + lead->q_off_status),
+        blocks, s0, kTcWaitNs, reinterpret_cast<unsigned long long*>(lead->q_dev + lead->q_off_status + 256));
     if (e != cudaSuccess) return cuda_fail(lead, e, "step interpreter");
   } else {
     // the launch (counter reset + kernel) is captured once into a CUDA graph and replayed
@@ -2598,6 +2602,18 @@ ajf_status ajf_launch_queue(ajf_ctx* const* ctxs, int n_ctx, double* dev_results
   ajf_status st = check_queue_batch(ctxs, n_ctx);
   if (st != AJF_OK) return st;
   return launch_queue_ctxs(ctxs, n_ctx, dev_results, tuned_queue(ctxs, n_ctx));
+}
+
+ajf_status ajf_queue_profile(ajf_ctx* c, double* out, int cap, int reset) {
+  if (!c || !out || cap < 0) return AJF_E_ARG;
+  if (!c->q_dev) return fail(c, AJF_E_STATE, "no step-interpreter launch led by this context");
+  unsigned long long v[3 * kQKinds] = {};
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemcpyAsync(v, c->q_dev + c->q_off_status + 256, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  if (reset) CUDA_TRY(c, cudaMemsetAsync(c->q_dev + c->q_off_status + 256, 0, sizeof(v), c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < cap && i < 3 * kQKinds; ++i) out[i] = static_cast<double>(v[i]) * (i % 3 == 2 ? 1.0 : 1e-9);
+  return AJF_OK;
 }
 
 ajf_status ajf_fidelity_batch_queue(ajf_ctx* const* ctxs, int n_ctx, int alg, double eps, ajf_result* out) {

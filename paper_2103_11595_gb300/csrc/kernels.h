@@ -74,8 +74,12 @@ constexpr unsigned long long kTcWaitNs = 2000000000ull;
 // zeroed by the launch. A dependency wait that expires sets *d_status (code 21) and the error
 // counter; a GEMM wait sets its own code, as in the standalone kernel.
 size_t queue_smem_bytes();
+// d_prof (optional, 3 * kQKinds counters, accumulated): per kind of task, its busy nanoseconds,
+// the nanoseconds its block waited for the previous phase, and its task count.
+constexpr int kQKinds = 10;
 cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tasks, int ntasks, int* d_counters,
-                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns = kTcWaitNs);
+                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns = kTcWaitNs,
+                         unsigned long long* d_prof = nullptr);
 // A prepared tensor-core GEMM's parameter block for the interpreter (its fixed pipeline geometry),
 // written to `out` (queue_gemm_params_bytes() bytes, 64-byte aligned in device memory when used);
 // its tile width, operand kind and work-item count.

@@ -135,7 +135,8 @@ __device__ __forceinline__ void body_task(const QPhase& ph, int v, uint8_t* smem
 __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict__ phases,
                                                        const QTask* __restrict__ tasks, int ntasks,
                                                        int* __restrict__ counters, int* __restrict__ status,
-                                                       unsigned long long wait_ns) {
+                                                       unsigned long long wait_ns,
+                                                       unsigned long long* __restrict__ prof) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ int s_task;
@@ -161,8 +162,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   sh.tmem = *tmem_slot;
   TcRing ring;
+  __shared__ unsigned long long s_t0, s_t1;
   for (;;) {
     if (tid == 0) {
+      if (prof) s_t0 = globaltimer();
       int t = ntasks;
       if (!*sh.abort_flag && ld_acquire(&counters[kQError]) == 0) t = atomicAdd(&counters[kQNext], 1);
       if (t < ntasks) {
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       s_task = t;
+      if (prof) s_t1 = globaltimer();
     }
     __syncthreads();
     const int t = s_task;
@@ -224,6 +228,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
       if (*sh.abort_flag) atomicExch(&counters[kQError], 1);
       __threadfence();
       atomicAdd(&counters[kQPhase0 + task.phase], 1);
+      if (prof) {  // per kind of task: busy time, time waiting for the previous phase, tasks
+        const unsigned long long t2 = globaltimer();
+        atomicAdd(&prof[3 * ph.kind + 0], t2 - s_t1);
+        atomicAdd(&prof[3 * ph.kind + 1], s_t1 - s_t0);
+        atomicAdd(&prof[3 * ph.kind + 2], 1ull);
+      }
     }
   }
   if (*sh.abort_flag) tc_drain_after_abort(kQSlots, wait_ns, status, sh, ring);
@@ -260,7 +270,8 @@ cudaError_t queue_gemm_params(const TcPrepared& t, void* out, int* bn, int* bf16
 size_t queue_gemm_params_bytes() { return (sizeof(TcParams) + 1023) / 1024 * 1024; }
 
 cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tasks, int ntasks, int* d_counters,
-                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns) {
+                         int* d_status, int blocks, cudaStream_t s, unsigned long long wait_ns,
+                         unsigned long long* d_prof) {
   if (ntasks == 0) return cudaSuccess;
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -273,7 +284,7 @@ cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tas
   }
   e = cudaMemsetAsync(d_counters, 0, sizeof(int) * (kQPhase0 + static_cast<size_t>(nphases)), s);
   if (e != cudaSuccess) return e;
-  k_queue<<<blocks, kThreads, kQSmem, s>>>(d_phases, d_tasks, ntasks, d_counters, d_status, wait_ns);
+  k_queue<<<blocks, kThreads, kQSmem, s>>>(d_phases, d_tasks, ntasks, d_counters, d_status, wait_ns, d_prof);
   return cudaGetLastError();
 }
 
