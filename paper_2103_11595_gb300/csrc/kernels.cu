@@ -49,8 +49,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_splitk(const StepDev* __restri
   splitk_body<T, SyncBlock>(steps, nsteps, arena, partial, blockIdx.x, tab, red_re, red_im);
 }
 
+// 4 blocks per SM (64 registers): the tiled trace is bound by memory latency, and its grid is
+// sized for 4 blocks per SM
 template <typename T, bool kF32>
-__global__ void __launch_bounds__(kBodyThreads) k_dot(const StepDev* __restrict__ steps, int nsteps,
+__global__ void __launch_bounds__(kBodyThreads, 4) k_dot(const StepDev* __restrict__ steps, int nsteps,
                                                       const T* __restrict__ arena, double2* __restrict__ partial) {
   extern __shared__ int64_t tab[];
   __shared__ double red_re[kBodyThreads], red_im[kBodyThreads];
@@ -66,8 +68,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_splitk_done(const StepDev* __r
   splitk_done_body<T, SyncBlock>(steps, partial, arena, scalars, blockIdx.x, red_re, red_im);
 }
 
+// 4 blocks per SM (64 registers): the gather is bound by memory latency; measured on GB300 with
+// 98 registers (2 blocks per SM) a large gather reached 1.2-1.3 TB/s
 template <typename S>
-__global__ void __launch_bounds__(kBodyThreads) k_perm(const PermDev* __restrict__ perms,
+__global__ void __launch_bounds__(kBodyThreads, 4) k_perm(const PermDev* __restrict__ perms,
                                                        const double* __restrict__ arena, char* __restrict__ base) {
   extern __shared__ int64_t tab[];
   __shared__ PermSmem<S> sm;
