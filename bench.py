@@ -363,8 +363,8 @@ def main():
     pk = peaks()
     d = classes[dom]
     if dom == "gemm_tc":
-        passes = {"tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6}[args.precision]
-        if args.precision.startswith("bf16"):
+        passes = {"tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "f16x3": 3}[args.precision]
+        if args.precision.startswith("bf16") or args.precision.startswith("f16"):
             peak = pk["bf16_tflops"]
             src = f"{pk['src']} bf16 dense burst (MEASURED_PEAKS.json)"
         else:
@@ -906,7 +906,7 @@ def run_precision(args, world, rank, local):
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
     seeds = [rank * 5 + i for i in range(5)]
     insts = [W.precision(s, depth=4) for s in seeds]
-    modes = ["f64", "f32", "tf32", "tf32x3", "bf16x3", "bf16x6"]
+    modes = ["f64", "f32", "tf32", "tf32x3", "bf16x3", "bf16x6", "f16x3"]
     out = torch.zeros(len(insts), 3, dtype=torch.float64, device=dev)
     F, rate = {}, {}
     steps = max(1, args.steps)

@@ -69,7 +69,9 @@ enum {
   AJF_PREC_TF32 = 2,   /* GEMM-class steps: one-pass TF32 tensor-core GEMMs (tcgen05), FP32 accumulate */
   AJF_PREC_TF32X3 = 3, /* split TF32 hi/lo operands, three tcgen05 products, FP32 accumulate   */
   AJF_PREC_BF16X3 = 4, /* bf16 operands split in two terms, three tcgen05 products             */
-  AJF_PREC_BF16X6 = 5  /* bf16 operands split in three terms, six tcgen05 products             */
+  AJF_PREC_BF16X6 = 5, /* bf16 operands split in three terms, six tcgen05 products             */
+  AJF_PREC_F16X3 = 6   /* fp16 operands in two terms scaled by a power of two per row and K block,
+                          three tcgen05 products (the scale undone per K block in the epilogue) */
 };
 /* Tensors are FP64 (planar complex) in device memory in every mode; a mode only sets how the
  * operands of the GEMM-class steps are rounded or split. Leaves, small steps, the final

@@ -21,8 +21,9 @@ AJF_IDEAL, AJF_IMPL = 0, 1
 AJF_UNITS_WHOLE, AJF_UNITS_KRAUS_SLICES, AJF_UNITS_BOND_SLICES = 0, 1, 2
 AJF_PLANNER_AUTO, AJF_PLANNER_GREEDY, AJF_PLANNER_MINFILL, AJF_PLANNER_LEARNED = 0, 1, 2, 3
 AJF_PREC_F64, AJF_PREC_F32, AJF_PREC_TF32, AJF_PREC_TF32X3, AJF_PREC_BF16X3, AJF_PREC_BF16X6 = 0, 1, 2, 3, 4, 5
+AJF_PREC_F16X3 = 6
 PRECISIONS = {"f64": AJF_PREC_F64, "f32": AJF_PREC_F32, "tf32": AJF_PREC_TF32, "tf32x3": AJF_PREC_TF32X3,
-              "bf16x3": AJF_PREC_BF16X3, "bf16x6": AJF_PREC_BF16X6}
+              "bf16x3": AJF_PREC_BF16X3, "bf16x6": AJF_PREC_BF16X6, "f16x3": AJF_PREC_F16X3}
 PLANNERS = {"auto": AJF_PLANNER_AUTO, "greedy": AJF_PLANNER_GREEDY, "minfill": AJF_PLANNER_MINFILL,
             "learned": AJF_PLANNER_LEARNED}
 

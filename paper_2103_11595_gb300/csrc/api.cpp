@@ -1001,7 +1001,7 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
   if (opts) o = *opts;
   if (o.trials <= 0) o.trials = 32;
   if (o.planner < AJF_PLANNER_AUTO || o.planner > AJF_PLANNER_LEARNED) return fail(c, AJF_E_ARG, "bad planner");
-  if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_BF16X6) return fail(c, AJF_E_ARG, "bad precision");
+  if (o.precision < AJF_PREC_F64 || o.precision > AJF_PREC_F16X3) return fail(c, AJF_E_ARG, "bad precision");
   for (int i = 0; i < 4; ++i)
     if (o.reserved[i] != 0) return fail(c, AJF_E_ARG, "reserved fields must be zero");
   if (o.slice_bonds < AJF_SLICE_AUTO || o.slice_bonds > AJF_MAX_SLICE_BONDS)
@@ -1776,6 +1776,7 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
     case AJF_PREC_TF32X3: mode = OPM_TF32X2; terms = 2; break;
     case AJF_PREC_BF16X3: mode = OPM_BF16X2; terms = 2; break;
     case AJF_PREC_BF16X6: mode = OPM_BF16X3; terms = 3; break;
+    case AJF_PREC_F16X3: mode = OPM_F16X2S; terms = 2; break;
     default: return AJF_E_ARG;
   }
   auto log2i = [](int64_t x) {
@@ -1785,11 +1786,11 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   };
   const int mb = log2i(M), nb = log2i(N), kb = log2i(K);
   if (mb < 4 || nb < 4 || kb < 3 || mb + kb > 30 || nb + kb > 30) return AJF_E_UNSUPPORTED;
-  const int kind = mode >= OPM_BF16X2 ? 1 : 0;
+  const int kind = mode == OPM_F16X2S ? 2 : (mode >= OPM_BF16X2 ? 1 : 0);
   const int64_t Mt = 2 * M, Kt = 2 * K;
   if (!tc_gemm_supported(Mt, N, Kt, kind)) return AJF_E_UNSUPPORTED;
   if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
-  const size_t eb = kind == 1 ? 2 : 4;
+  const size_t eb = kind != 0 ? 2 : 4;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   // device layout: A and B as planar complex FP64 (imaginary planes zero), operand terms, C,
   // K-split workspace, status word
@@ -1801,7 +1802,11 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   const int ksplit = tc_gemm_splits(Mt, N, Kt, kind);
   const size_t cbytes = al(size_t(Mt) * N * 8);
   const size_t w_off = c_off + cbytes, s_off = w_off + (ksplit > 1 ? ksplit * cbytes : 0);
-  const size_t p_off = s_off + 256, total = p_off + al(2 * sizeof(PermDev));
+  const size_t p_off = s_off + 256;
+  // scaled fp16: one FP32 scale per row and 128-byte K block of each operand
+  const size_t kblk = kind == 2 ? (size_t(Kt) * eb + 127) / 128 : 0;
+  const size_t xs_off = p_off + al(2 * sizeof(PermDev)), ys_off = xs_off + al(size_t(Mt) * kblk * 4);
+  const size_t total = ys_off + al(size_t(N) * kblk * 4);
   char* d = nullptr;
   if (cudaMalloc(&d, total) != cudaSuccess) return AJF_E_NOMEM;
   std::vector<PermDev> pd(2);
@@ -1822,6 +1827,7 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
     q.mode = mode;
     for (int t = 0; t < 3; ++t)
       q.dst[t] = static_cast<int64_t>((side == 0 ? x0 + t * xbytes : y0 + t * ybytes));
+    if (kind == 2) q.dst[2] = static_cast<int64_t>(side == 0 ? xs_off : ys_off);
   }
   ajf_status st = AJF_OK;
   std::vector<double> planar(2 * size_t(std::max(M, N)) * K, 0.0);
@@ -1845,6 +1851,10 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   for (int t = 0; t < terms; ++t) {
     ao[t] = static_cast<int64_t>(x0 + t * xbytes);
     bo[t] = static_cast<int64_t>(y0 + t * ybytes);
+  }
+  if (kind == 2) {
+    ao[2] = static_cast<int64_t>(xs_off);
+    bo[2] = static_cast<int64_t>(ys_off);
   }
   if (st == AJF_OK && launch_gemm_tc(d, ao, bo, terms, reinterpret_cast<double*>(d + c_off), Mt, N, Kt, kind,
                                      reinterpret_cast<double*>(d + w_off), ksplit, reinterpret_cast<int*>(d + s_off),

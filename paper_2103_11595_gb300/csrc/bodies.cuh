@@ -23,6 +23,7 @@
 //  open_body/final_body  the FP64 end of the path: t_i for Alg. I, sum |t_i|^2, F_J and 1 - F_J.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -458,8 +459,13 @@ __device__ __forceinline__ float to_tf32(float x) {
 // keeps x to 2^-26 of the block's largest entry. The two-term splits keep a floating leading term:
 // with a fixed-point one their single correction term would leave entries far below the block's
 // largest with only its 8 or 11 bits.
-__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_BF16X3; }
-__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_BF16X3 ? 8 : 0; }
+//
+// The scaled fp16 split (OPM_F16X2S) stores x / q instead: hi = rint(x / q), an integer of at most
+// 2^9 (exact in fp16), and lo = fp16(x / q - hi), with q kept per row and K block in a scale array
+// that the GEMM's epilogue applies to each K block's partial sums. 512^2 * 64 = 2^24 bounds the
+// block sum of the leading products, so their accumulation is exact as well.
+__device__ __forceinline__ bool split_mode(int mode) { return mode == OPM_BF16X3 || mode == OPM_F16X2S; }
+__device__ __forceinline__ int lead_bits(int mode) { return mode == OPM_BF16X3 ? 8 : (mode == OPM_F16X2S ? 9 : 0); }
 
 // qexp for a row block whose largest magnitude is m: q = 2^(floor(log2 m) + 1 - lead bits), so
 // that m / q < 2^lead bits; clamped to the normal FP32 range (zero blocks take the floor).
@@ -505,6 +511,15 @@ __device__ __forceinline__ void store_operand2(const PermDev& p, char* base, int
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[0]) + idx) = h;
       *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(base + p.dst[1]) + idx) =
           __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+      break;
+    }
+    case OPM_F16X2S: {  // x / q in fp16: an integer leading term and the remainder
+      const float sc = pow2f(-qexp);
+      const float y0 = x0 * sc, y1 = x1 * sc;
+      const float h0 = rintf(y0), h1 = rintf(y1);
+      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(base + p.dst[0]) + idx) = __floats2half2_rn(h0, h1);
+      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(base + p.dst[1]) + idx) =
+          __floats2half2_rn(y0 - h0, y1 - h1);
       break;
     }
     default: {  // OPM_BF16X3: fixed-point leading term, floating middle and low terms
@@ -623,6 +638,27 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
         }
       }
       Sync::sync();
+      if (p.mode == OPM_F16X2S && threadIdx.x < TR) {
+        // the scales q of this tile's rows, [K block][row] over the operand's rows (2R embedded):
+        // t = 0 holds Re (s = 0) or Im (s = 1), t = 1 holds -Im (s = 0) or Re (s = 1); a K below
+        // one block puts both halves of a row in block 0 with a joint quantum
+        const int i = threadIdx.x;
+        const int64_t r = r0 + i, Rt = p.embed ? 2 * R : R;
+        float* sc = reinterpret_cast<float*>(base + p.dst[2]);
+        const float fr = pow2f(qre[i]), fi = pow2f(qim[i]);
+        const int64_t kb0 = joint ? 0 : k0 / 64, kb1 = joint ? 0 : (K + k0) / 64;
+        if (p.embed) {
+          sc[kb0 * Rt + r] = fr;
+          sc[kb0 * Rt + R + r] = fi;
+          if (!joint) {
+            sc[kb1 * Rt + r] = fi;
+            sc[kb1 * Rt + R + r] = fr;
+          }
+        } else {
+          sc[kb0 * Rt + r] = fr;
+          if (!joint) sc[kb1 * Rt + r] = fi;
+        }
+      }
     }
     const int pairs = TK >> 1;
     for (int w = threadIdx.x; w < TR * pairs; w += kBodyThreads) {

@@ -41,7 +41,8 @@ struct StepDev {
 // plane t (N x 2K).
 struct PermDev {
   int64_t src, plane;     // source tensor (element offset of the real plane) and plane stride
-  int64_t dst[3];         // destination operand arrays (split terms: hi, mid, lo), byte offsets
+  int64_t dst[3];         // destination operand arrays (split terms: hi, mid, lo), byte offsets;
+                          // OPM_F16X2S: hi, lo and the scale array
   BitMap rows, cols;      // row-index bits / k-index bits -> source offsets
   int32_t rbits, kbits;   // log2 rows (M or N), log2 K
   int32_t embed;          // 1: X side (embedded), 0: Y side
@@ -57,6 +58,8 @@ enum OperandMode : int32_t {
   OPM_TF32X2 = 3,  // hi, lo (float, each TF32)
   OPM_BF16X2 = 4,  // hi, lo (bf16)
   OPM_BF16X3 = 5,  // hi, mid, lo (bf16)
+  OPM_F16X2S = 6,  // hi, lo (fp16) of x / q, with q a power of two per row and K block (dst[2]: the
+                   // FP32 q's, [K block][row])
 };
 
 // Leaf construction from the uploaded complex128 inputs.
@@ -130,7 +133,7 @@ struct QPhase {
   int32_t nblocks;     // the kernel's blocks, or the GEMM's work items
   int32_t count;       // steps / perms / leaves of the launch
   int32_t grid_x;      // QK_PERM: blocks per perm
-  int32_t flag;        // QK_DOT: FP32 products; QK_GEMM: bf16 operands
+  int32_t flag;        // QK_DOT: FP32 products; QK_GEMM: operand kind (0 TF32, 1 bf16, 2 scaled fp16)
   int32_t bn;          // QK_GEMM: tile width
   int32_t ksplit;      // QK_SPLIT_SUM: splits
   int32_t pad;

@@ -133,7 +133,7 @@ double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
     rate = kFp32;
     tm = 128;
   } else if (tc) {
-    const bool bf16 = p.precision == AJF_PREC_BF16X3 || p.precision == AJF_PREC_BF16X6;
+    const bool bf16 = p.precision == AJF_PREC_BF16X3 || p.precision == AJF_PREC_BF16X6 || p.precision == AJF_PREC_F16X3;
     terms = p.precision == AJF_PREC_TF32 ? 1 : (p.precision == AJF_PREC_BF16X6 ? 3 : 2);
     passes = p.precision == AJF_PREC_TF32 ? 1 : (p.precision == AJF_PREC_BF16X6 ? 6 : 3);
     eb = bf16 ? 2 : 4;

@@ -112,10 +112,13 @@ int operand_mode(int precision) {
     case AJF_PREC_TF32: return OPM_TF32;
     case AJF_PREC_TF32X3: return OPM_TF32X2;
     case AJF_PREC_BF16X3: return OPM_BF16X2;
+    case AJF_PREC_F16X3: return OPM_F16X2S;
     default: return OPM_BF16X3;
   }
 }
-int mode_terms(int mode) { return mode == OPM_TF32X2 || mode == OPM_BF16X2 ? 2 : (mode == OPM_BF16X3 ? 3 : 1); }
+int mode_terms(int mode) {
+  return mode == OPM_TF32X2 || mode == OPM_BF16X2 || mode == OPM_F16X2S ? 2 : (mode == OPM_BF16X3 ? 3 : 1);
+}
 size_t mode_bytes(int mode) { return mode == OPM_F64 ? 8 : (mode >= OPM_BF16X2 ? 2 : 4); }
 
 }  // namespace
@@ -242,7 +245,9 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   const int mode = operand_mode(precision);
   const int terms = mode_terms(mode);
   const size_t eb = mode_bytes(mode);
-  const int tc_kind = (mode >= OPM_BF16X2) ? 1 : 0;
+  // tensor-core operand kind: 0 TF32, 1 bf16, 2 fp16 with per-row-block scales
+  const int tc_kind = mode == OPM_F16X2S ? 2 : ((mode >= OPM_BF16X2) ? 1 : 0);
+  const bool scaled = mode == OPM_F16X2S;
   int scalar_slots = 0;
   size_t partials = 0;
 
@@ -372,6 +377,13 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       size_t xo[3] = {0, 0, 0}, yo[3] = {0, 0, 0};
       for (int t = 0; t < gterms; ++t) xo[t] = ff.alloc(xbytes);
       for (int t = 0; t < gterms; ++t) yo[t] = ff.alloc(ybytes);
+      // scaled fp16 operands: one FP32 power of two per row and 128-byte K block, [K block][row]
+      const size_t kblk = use_tc && scaled ? (size_t(Kt) * geb + 127) / 128 : 0;
+      const size_t xsb = kblk * size_t(Mt) * 4, ysb = kblk * size_t(Nt) * 4;
+      if (kblk) {
+        xo[2] = ff.alloc(xsb);
+        yo[2] = ff.alloc(ysb);
+      }
       // permute launch (X and Y)
       PermDev px, py;
       std::memset(&px, 0, sizeof(px));
@@ -434,6 +446,10 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
           lg.a_off[t] = static_cast<int64_t>(xo[t]);
           lg.b_off[t] = static_cast<int64_t>(yo[t]);
         }
+        if (kblk) {  // the scale arrays ride in the third slot of the offsets
+          lg.a_off[2] = static_cast<int64_t>(xo[2]);
+          lg.b_off[2] = static_cast<int64_t>(yo[2]);
+        }
         lg.npass = gterms;
         P.tensor_cores++;
       } else {
@@ -448,6 +464,10 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       P.launches.push_back(lg);
       for (int t = 0; t < gterms; ++t) ff.release(xo[t], xbytes);
       for (int t = 0; t < gterms; ++t) ff.release(yo[t], ybytes);
+      if (kblk) {
+        ff.release(xo[2], xsb);
+        ff.release(yo[2], ysb);
+      }
       if (ws_bytes) ff.release(ws, ws_bytes);
       ++i;
     }
@@ -717,6 +737,12 @@ std::string check_program(const Program& P) {
           if (!in_work(d)) return ws + ": operand term " + std::to_string(t) + " outside the work region";
           W.push_back(d);
         }
+        if (g.mode == OPM_F16X2S) {  // one FP32 scale per row and 128-byte K block
+          const size_t sb = rows * ((cols * mode_bytes(g.mode) + 127) / 128) * 4;
+          const Span d{static_cast<size_t>(g.dst[2]), static_cast<size_t>(g.dst[2]) + sb};
+          if (!in_work(d)) return ws + ": scale array outside the work region";
+          W.push_back(d);
+        }
       }
     } else if (ln.kind == LK_GEMM_TC || ln.kind == LK_GEMM_SIMT) {
       if (li == 0 || P.launches[li - 1].kind != LK_PERM) return who + ": GEMM without its gather";
@@ -735,6 +761,14 @@ std::string check_program(const Program& P) {
         const Span a{static_cast<size_t>(ln.a_off[t]), static_cast<size_t>(ln.a_off[t]) + size_t(ln.M) * size_t(ln.K) * eb};
         const Span b{static_cast<size_t>(ln.b_off[t]), static_cast<size_t>(ln.b_off[t]) + size_t(ln.N) * size_t(ln.K) * eb};
         if (!in_work(a) || !in_work(b)) return who + ": operand outside the work region";
+        R.push_back(a);
+        R.push_back(b);
+      }
+      if (ln.kind == LK_GEMM_TC && px.mode == OPM_F16X2S) {
+        const size_t kb = (size_t(ln.K) * eb + 127) / 128;
+        const Span a{static_cast<size_t>(ln.a_off[2]), static_cast<size_t>(ln.a_off[2]) + size_t(ln.M) * kb * 4};
+        const Span b{static_cast<size_t>(ln.b_off[2]), static_cast<size_t>(ln.b_off[2]) + size_t(ln.N) * kb * 4};
+        if (!in_work(a) || !in_work(b)) return who + ": scale array outside the work region";
         R.push_back(a);
         R.push_back(b);
       }

@@ -40,7 +40,7 @@ constexpr int kQTmemStride = 256;                          // two partials of up
 constexpr uint32_t kQTmemCols = kQBufs * kQTmemStride;
 constexpr size_t kQScratch = size_t(kQSlots) * kQSlotBytes;  // 192 KiB
 constexpr size_t kQArrays = 96 * 1024;                     // body arrays after the offset tables
-constexpr size_t kQSmem = kQScratch + 1024 /* barriers */ + 1024 /* alignment */;
+constexpr size_t kQSmem = kQScratch + kTcControlBytes + 1024 /* alignment */;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -50,7 +50,7 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 // Each kind of task is its own (not inlined) function, so that the register allocation of one
 // body does not constrain the others.
-template <int BN, bool BF16>
+template <int BN, int KIND>
 __device__ __noinline__ bool gemm_task(const QPhase& ph, const QTask& t, const TcShared& sh, TcRing& ring) {
   const TcParams& p = *static_cast<const TcParams*>(ph.gemm);
   if (threadIdx.x == 0) {
@@ -61,7 +61,7 @@ __device__ __noinline__ bool gemm_task(const QPhase& ph, const QTask& t, const T
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.bmap[i]) : "memory");
     }
   }
-  return tc_gemm_items<BN, BF16>(p, static_cast<uint32_t>(t.b0), static_cast<uint32_t>(t.b1), 1u, sh, ring);
+  return tc_gemm_items<BN, KIND>(p, static_cast<uint32_t>(t.b0), static_cast<uint32_t>(t.b1), 1u, sh, ring);
 }
 
 // One virtual block v of a CUDA-core phase (threads 0..255), one function per kind of body.
@@ -141,16 +141,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ int s_task;
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint8_t* bars = smem + kQScratch;
   TcShared sh;
-  sh.slots = smem;
-  sh.full0 = smem_u32(bars);
-  sh.empty0 = sh.full0 + 8 * kMaxSlots;
-  sh.accf0 = sh.empty0 + 8 * kMaxSlots;
-  sh.acce0 = sh.accf0 + 8 * kMaxBufs;
-  sh.drain0 = sh.acce0 + 8 * kMaxBufs;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 8);
-  sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 12);
+  uint32_t* tmem_slot = tc_layout(smem, smem + kQScratch, sh);
   if (tid == 0) tc_init_barriers(sh, kQSlots, kQBufs);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -206,15 +198,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
     const QTask task = tasks[t];
     const QPhase& ph = phases[task.phase];
     if (ph.kind == QK_GEMM) {
-      const bool bf16 = ph.flag != 0;
-      if (bf16) {
-        if (ph.bn == 128) gemm_task<128, true>(ph, task, sh, ring);
-        else if (ph.bn == 64) gemm_task<64, true>(ph, task, sh, ring);
-        else gemm_task<32, true>(ph, task, sh, ring);
+      if (ph.flag == 2) {
+        if (ph.bn == 128) gemm_task<128, 2>(ph, task, sh, ring);
+        else if (ph.bn == 64) gemm_task<64, 2>(ph, task, sh, ring);
+        else gemm_task<32, 2>(ph, task, sh, ring);
+      } else if (ph.flag == 1) {
+        if (ph.bn == 128) gemm_task<128, 1>(ph, task, sh, ring);
+        else if (ph.bn == 64) gemm_task<64, 1>(ph, task, sh, ring);
+        else gemm_task<32, 1>(ph, task, sh, ring);
       } else {
-        if (ph.bn == 128) gemm_task<128, false>(ph, task, sh, ring);
-        else if (ph.bn == 64) gemm_task<64, false>(ph, task, sh, ring);
-        else gemm_task<32, false>(ph, task, sh, ring);
+        if (ph.bn == 128) gemm_task<128, 0>(ph, task, sh, ring);
+        else if (ph.bn == 64) gemm_task<64, 0>(ph, task, sh, ring);
+        else gemm_task<32, 0>(ph, task, sh, ring);
       }
       __syncwarp();
     } else if (warp < kBodyThreads / 32) {
@@ -236,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_queue(const QPhase* __restrict_
       }
     }
   }
-  if (*sh.abort_flag) tc_drain_after_abort(kQSlots, wait_ns, status, sh, ring);
+  if (*sh.abort_flag) tc_drain_after_abort(kQSlots, kQBufs, wait_ns, status, sh, ring);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncwarp();
   __syncthreads();
@@ -261,7 +256,8 @@ cudaError_t queue_gemm_params(const TcPrepared& t, void* out, int* bn, int* bf16
   p.tmem_stride = kQTmemStride;
   const uint32_t bnbits = (p.idesc >> 17) & 0x3Fu;  // N >> 3 in the instruction descriptor
   *bn = static_cast<int>(bnbits << 3);
-  *bf16 = ((p.idesc >> 7) & 0x7u) == 1u ? 1 : 0;
+  const uint32_t fmt = (p.idesc >> 7) & 0x7u;  // 2 TF32, 1 bf16, 0 fp16 (scaled)
+  *bf16 = fmt == 2u ? 0 : (fmt == 1u ? 1 : 2);
   *nwork = static_cast<int>(p.tiles * p.ksplit);
   std::memcpy(out, &p, sizeof(p));
   return cudaSuccess;

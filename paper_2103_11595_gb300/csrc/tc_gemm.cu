@@ -66,7 +66,7 @@ namespace {
 
 using namespace tc;
 
-template <int BN, bool kBF16>
+template <int BN, int kKind>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -74,16 +74,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   // TMEM: NB buffers of two partials (P0: leading product, P1: corrections), BN columns each
   const uint32_t ncols =
       static_cast<uint32_t>(2 * p.bufs * BN) < 32u ? 32u : static_cast<uint32_t>(2 * p.bufs * BN);
-  uint8_t* bars = smem + p.slots * p.slot_bytes;
   TcShared sh;
-  sh.slots = smem;
-  sh.full0 = smem_u32(bars);
-  sh.empty0 = sh.full0 + 8 * kMaxSlots;
-  sh.accf0 = sh.empty0 + 8 * kMaxSlots;   // partial buffer b ready (MMA -> epilogue)
-  sh.acce0 = sh.accf0 + 8 * kMaxBufs;     // partial buffer b drained (epilogue -> MMA)
-  sh.drain0 = sh.acce0 + 8 * kMaxBufs;    // MMAs issued before an abort have completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 8);
-  sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 16 * kMaxBufs + 12);
+  uint32_t* tmem_slot = tc_layout(smem, smem + p.slots * p.slot_bytes, sh);
   if (threadIdx.x == 0) tc_init_barriers(sh, p.slots, p.bufs);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -96,8 +88,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   sh.tmem = *tmem_slot;
   TcRing ring;
   const uint32_t nwork = static_cast<uint32_t>(p.tiles) * static_cast<uint32_t>(p.ksplit);
-  tc_gemm_items<BN, kBF16>(p, blockIdx.x, nwork, gridDim.x, sh, ring);
-  if (*sh.abort_flag) tc_drain_after_abort(p.slots, p.wait_ns, p.status, sh, ring);
+  tc_gemm_items<BN, kKind>(p, blockIdx.x, nwork, gridDim.x, sh, ring);
+  if (*sh.abort_flag) tc_drain_after_abort(p.slots, p.bufs, p.wait_ns, p.status, sh, ring);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   // __syncthreads (bar.sync, the aligned form) must be executed by all threads of a warp
   // together; warps 0 and 1 get here diverged (lane 0 ran the producer / MMA loop, lanes 1-31 came
@@ -128,15 +120,17 @@ EncodeFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box_rows, bool bf16) {
+bool make_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t k, uint32_t box_rows, int kind) {
   EncodeFn fn = encode_fn();
   if (!fn) return false;
-  const size_t es = bf16 ? 2 : 4;
+  const size_t es = kind != 0 ? 2 : 4;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(k * es)};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / es), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box,
+  const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : (kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  return fn(map, dt, 2, ptr, dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -150,13 +144,13 @@ int sm_count() {
   return counts[dev];
 }
 
-template <int BN, bool BF16>
+template <int BN, int KIND>
 void run_tile(const void* params, unsigned grid, size_t smem, cudaStream_t s) {
-  k_gemm_tc<BN, BF16><<<grid, kThreads, smem, s>>>(*static_cast<const TcParams*>(params));
+  k_gemm_tc<BN, KIND><<<grid, kThreads, smem, s>>>(*static_cast<const TcParams*>(params));
 }
 
 // Fill the tile geometry of `p` and the launch shape of `t` (host only; nothing is enqueued).
-template <int BN, bool BF16>
+template <int BN, int KIND>
 cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   p.slot_bytes = static_cast<uint32_t>((kBM + BN) * kRowBytes);
   p.slots = static_cast<int32_t>(kSmemBudget / p.slot_bytes);
@@ -164,7 +158,7 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   if (p.slots < p.terms) return cudaErrorInvalidValue;
   p.bufs = 256 / BN > kMaxBufs ? kMaxBufs : 256 / BN;  // each buffer: 2 partials x BN TMEM columns
   p.tmem_stride = 2 * BN;
-  const size_t smem = size_t(p.slots) * p.slot_bytes + 1024 /* barriers */ + 1024 /* alignment */;
+  const size_t smem = size_t(p.slots) * p.slot_bytes + kTcControlBytes + 1024 /* alignment */;
   const int64_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt;
   if (mt > 0x7FFFFFFF || nt > 0x7FFFFFFF) return cudaErrorInvalidValue;
@@ -179,7 +173,8 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   // over every SM
   const int64_t work = tiles * static_cast<int64_t>(p.ksplit);
   const int64_t grid = work < sms ? work : sms;
-  const uint32_t fmt = BF16 ? 1u : 2u;  // A/B type: TF32 = 2, BF16 = 1; D = F32; both K-major
+  // A/B type: TF32 = 2 (kind::tf32), BF16 = 1, F16 = 0 (kind::f16); D = F32; both K-major
+  const uint32_t fmt = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
             (static_cast<uint32_t>(kBM >> 4) << 24);
   // the shared-memory opt-in is a per-function attribute: set once per device (the size is the
@@ -189,13 +184,13 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(k_gemm_tc<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    e = cudaFuncSetAttribute(k_gemm_tc<BN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   t->grid = static_cast<unsigned>(grid);
   t->smem = smem;
-  t->run = &run_tile<BN, BF16>;
+  t->run = &run_tile<BN, KIND>;
   return cudaSuccess;
 }
 
@@ -205,13 +200,13 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
 // rows of a box beyond M or N, and the K columns beyond the last full 128-byte row, with zeros, and
 // the epilogue stores only rows < M and columns < N. Row strides must be multiples of 16 bytes.
 bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind) {
-  const int64_t es = kind == 1 ? 2 : 4;
+  const int64_t es = kind != 0 ? 2 : 4;
   const bool pow2 = (M & (M - 1)) == 0 && (N & (N - 1)) == 0 && (K & (K - 1)) == 0;
   return pow2 && M >= 32 && N >= 16 && K * es >= 32 && M * N <= (int64_t(1) << 40) && K * es <= (int64_t(1) << 38);
 }
 
 int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind) {
-  const int64_t es = kind == 1 ? 2 : 4;
+  const int64_t es = kind != 0 ? 2 : 4;
   const int64_t bn = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
   const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + bn - 1) / bn);
   const int64_t kblocks = (K * es + kRowBytes - 1) / kRowBytes;
@@ -251,14 +246,18 @@ cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, con
   t->ready = false;
   if (!tc_gemm_supported(M, N, K, kind) || terms < 1 || terms > kMaxTerms) return cudaErrorNotSupported;
   if (ksplit < 1 || (ksplit > 1 && !ws)) return cudaErrorInvalidValue;
-  const bool bf16 = kind == 1;
+  if (kind < 0 || kind > 2 || (kind == 2 && terms != 2)) return cudaErrorInvalidValue;
   // BN = 256 would need 128 FP32 accumulators per epilogue thread and spill at 320 threads.
   const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
   TcParams p;
   std::memset(&p, 0, sizeof(p));
   for (int i = 0; i < terms; ++i) {
-    if (!make_map(&p.amap[i], base + a_off[i], M, K, kBM, bf16)) return cudaErrorInvalidValue;
-    if (!make_map(&p.bmap[i], base + b_off[i], N, K, static_cast<uint32_t>(bn), bf16)) return cudaErrorInvalidValue;
+    if (!make_map(&p.amap[i], base + a_off[i], M, K, kBM, kind)) return cudaErrorInvalidValue;
+    if (!make_map(&p.bmap[i], base + b_off[i], N, K, static_cast<uint32_t>(bn), kind)) return cudaErrorInvalidValue;
+  }
+  if (kind == 2) {  // the scale arrays ride in the third offset: [K block][M] and [K block][N] floats
+    p.sa = reinterpret_cast<const float*>(base + a_off[2]);
+    p.sb = reinterpret_cast<const float*>(base + b_off[2]);
   }
   p.C = C;
   p.ws = ws;
@@ -268,20 +267,24 @@ cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, con
   p.terms = terms;
   p.wait_ns = wait_ns;
   p.stall_loads = stall_loads;
-  const int64_t row_elems = kRowBytes / (bf16 ? 2 : 4);
+  const int64_t row_elems = kRowBytes / (kind != 0 ? 2 : 4);
   p.kblocks = static_cast<int32_t>((K + row_elems - 1) / row_elems);
   p.kb_split = (p.kblocks + ksplit - 1) / ksplit;
   p.ksplit = (p.kblocks + p.kb_split - 1) / p.kb_split;
   if (p.ksplit != ksplit) return cudaErrorInvalidValue;  // the workspace was sized for `ksplit` splits
   cudaError_t e;
-  if (bf16) {
-    if (bn == 128) e = prepare_tile<128, true>(p, t, M, N);
-    else if (bn == 64) e = prepare_tile<64, true>(p, t, M, N);
-    else e = prepare_tile<32, true>(p, t, M, N);
+  if (kind == 2) {
+    if (bn == 128) e = prepare_tile<128, 2>(p, t, M, N);
+    else if (bn == 64) e = prepare_tile<64, 2>(p, t, M, N);
+    else e = prepare_tile<32, 2>(p, t, M, N);
+  } else if (kind == 1) {
+    if (bn == 128) e = prepare_tile<128, 1>(p, t, M, N);
+    else if (bn == 64) e = prepare_tile<64, 1>(p, t, M, N);
+    else e = prepare_tile<32, 1>(p, t, M, N);
   } else {
-    if (bn == 128) e = prepare_tile<128, false>(p, t, M, N);
-    else if (bn == 64) e = prepare_tile<64, false>(p, t, M, N);
-    else e = prepare_tile<32, false>(p, t, M, N);
+    if (bn == 128) e = prepare_tile<128, 0>(p, t, M, N);
+    else if (bn == 64) e = prepare_tile<64, 0>(p, t, M, N);
+    else e = prepare_tile<32, 0>(p, t, M, N);
   }
   if (e != cudaSuccess) return e;
   std::memcpy(t->params, &p, sizeof(p));

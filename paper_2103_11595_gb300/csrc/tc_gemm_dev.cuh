@@ -37,6 +37,8 @@ struct TcParams {
   CUtensorMap amap[kMaxTerms];
   CUtensorMap bmap[kMaxTerms];
   double* C;
+  const float* sa;                   // scaled fp16 operands: A's scales [K block][M], B's [K block][N]
+  const float* sb;
   int* status;
   int64_t M, N;
   int32_t terms, kblocks, ntn, slots, bufs;
@@ -108,6 +110,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 1-D bulk copy global -> shared (16-byte aligned addresses, a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
@@ -119,9 +128,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-template <bool kBF16>
+// Operand kinds: 0 TF32 (kind::tf32), 1 bf16, 2 fp16 scaled per row and K block (kind::f16; the
+// instruction descriptor names the type).
+template <int kKind>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (kBF16) {
+  if (kKind != 0) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
@@ -157,9 +168,12 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 struct TcShared {
   uint8_t* slots;                    // S slots of p.slot_bytes, 1024-byte aligned
   uint32_t full0, empty0, accf0, acce0, drain0;  // barrier arrays (8 bytes per barrier)
+  uint32_t sfull0;                   // scaled fp16: the scales of TMEM buffer b have arrived
+  float* scales;                     // scaled fp16: per TMEM buffer, 128 row scales then 128 column scales
   volatile int* abort_flag;
   uint32_t tmem;
 };
+constexpr int kScaleFloats = 256;    // floats of scales per TMEM buffer
 
 // Ring positions of the three roles; they continue from one call of tc_gemm_items to the next
 // (the barrier phases must), so a caller keeps one TcRing per thread for the block's lifetime.
@@ -172,9 +186,27 @@ struct TcRing {
   int mbuf = 0;
   uint32_t mbphase = 0;
   bool any = false;                  // MMA issuer: MMAs issued so far
+  uint32_t scopies = 0;              // MMA issuer: scale copies issued so far (scaled fp16)
   int ebuf = 0;                      // epilogue: next TMEM buffer
   uint32_t ebphase = 0;
 };
+
+// Layout of the pipeline's control region (kTcControlBytes from `bars`, 16-byte aligned): the
+// barrier arrays, the TMEM address slot, the abort flag, then the scale buffers of the scaled fp16
+// kind (kMaxBufs x kScaleFloats floats).
+constexpr uint32_t kTcControlBytes = 256 + kMaxBufs * kScaleFloats * 4;
+__device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, TcShared& sh) {
+  sh.slots = slots;
+  sh.full0 = smem_u32(bars);
+  sh.empty0 = sh.full0 + 8 * kMaxSlots;
+  sh.accf0 = sh.empty0 + 8 * kMaxSlots;   // partial buffer b ready (MMA -> epilogue)
+  sh.acce0 = sh.accf0 + 8 * kMaxBufs;     // partial buffer b drained (epilogue -> MMA)
+  sh.drain0 = sh.acce0 + 8 * kMaxBufs;    // MMAs issued before an abort have completed
+  sh.sfull0 = sh.drain0 + 8;              // scales of buffer b arrived
+  sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 12);
+  sh.scales = reinterpret_cast<float*>(bars + 256);
+  return reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 8);  // TMEM address slot
+}
 
 // Initialise the pipeline barriers (thread 0; the block synchronises afterwards).
 __device__ __forceinline__ void tc_init_barriers(const TcShared& sh, int S, int NB) {
@@ -187,6 +219,7 @@ __device__ __forceinline__ void tc_init_barriers(const TcShared& sh, int S, int 
     mbar_init(sh.acce0 + 8 * b, kEpiWarps);
   }
   mbar_init(sh.drain0, 1);
+  for (int b = 0; b < NB; ++b) mbar_init(sh.sfull0 + 8 * b, 1);
   *sh.abort_flag = 0;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -196,7 +229,7 @@ __device__ __forceinline__ void tc_init_barriers(const TcShared& sh, int S, int 
 // lane 0 the TMA producer, warp 1 lane 0 the MMA issuer, warps 2..9 the epilogue; the other
 // lanes of warps 0 and 1 pass straight through. Returns false in a role that gave up (a bounded
 // wait expired, or another role set the abort flag); the roles' ring positions advance in `r`.
-template <int BN, bool kBF16>
+template <int BN, int kKind>
 __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, uint32_t wi1, uint32_t step,
                                               const TcShared& sh, TcRing& r) {
   static_assert(BN == 32 || BN == 64 || BN == 128, "tile width");
@@ -243,7 +276,7 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
             break;
           }
           const uint32_t sa = smem_u32(sh.slots + slot * p.slot_bytes);
-          const int32_t kx = kb * (kRowBytes / (kBF16 ? 2 : 4));
+          const int32_t kx = kb * (kRowBytes / (kKind != 0 ? 2 : 4));
           mbar_expect_tx(sh.full0 + 8 * slot, a_bytes + b_bytes);
           tma_load_2d(sa, &p.amap[t], kx, m0, sh.full0 + 8 * slot);
           tma_load_2d(sa + a_bytes, &p.bmap[t], kx, n0, sh.full0 + 8 * slot);
@@ -271,6 +304,17 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
         if (*sh.abort_flag || !mbar_wait(sh.acce0 + 8 * b, bphase ^ 1u, p.wait_ns, p.status, 14)) {
           ok = false;
           break;
+        }
+        if (kKind == 2) {
+          // the K block's row and column scales into buffer b's scale area (the epilogue has
+          // released the buffer, so also its scales)
+          const uint32_t rows = static_cast<uint32_t>(p.M - m0 < kBM ? p.M - m0 : kBM);
+          const uint32_t cols = static_cast<uint32_t>(p.N - n0 < BN ? p.N - n0 : BN);
+          const uint32_t sdst = smem_u32(sh.scales + b * kScaleFloats);
+          mbar_expect_tx(sh.sfull0 + 8 * b, 4 * (rows + cols));
+          bulk_load(sdst, p.sa + static_cast<int64_t>(kb) * p.M + m0, 4 * rows, sh.sfull0 + 8 * b);
+          bulk_load(sdst + 4 * 128, p.sb + static_cast<int64_t>(kb) * p.N + n0, 4 * cols, sh.sfull0 + 8 * b);
+          ++r.scopies;
         }
         if (++buf == NB) {
           buf = 0;
@@ -312,7 +356,7 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
         auto product = [&](uint32_t dst, uint64_t ad, uint64_t bd) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            mma<kBF16>(dst, ad + 2 * kk, bd + 2 * kk, p.idesc, acc);
+            mma<kKind>(dst, ad + 2 * kk, bd + 2 * kk, p.idesc, acc);
             acc = 1;
           }
         };
@@ -387,6 +431,21 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t col = static_cast<uint32_t>(b * p.tmem_stride + h * COLS);
+        float sa = 1.0f;
+        const float* sbv = nullptr;
+        if (kKind == 2) {
+          // this K block's scales: the row's (per lane) and the columns' (the same for every lane)
+          int ws = 1;
+          if (lane == 0) ws = mbar_wait(sh.sfull0 + 8 * b, (bphase ^ (buf == 0 ? 1u : 0u)) & 1u, p.wait_ns, p.status,
+                                        17) ? 1 : 0;
+          if (!__shfl_sync(0xffffffffu, ws, 0)) {
+            ok = false;
+            break;
+          }
+          const float* sbuf = sh.scales + b * kScaleFloats;
+          sa = sbuf[32 * q + lane];
+          sbv = sbuf + 128 + h * COLS;
+        }
 #pragma unroll
         for (int c0 = 0; c0 < COLS; c0 += CH) {
           uint32_t r0[CH], r1[CH];
@@ -397,7 +456,18 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
             for (int c1 = 0; c1 < CH; c1 += 16) tmem_ld16(tmem + lane_base + col + BN + c0 + c1, r1 + c1);
           }
           tmem_wait_ld();
-          if (T > 1) {
+          if (kKind == 2) {
+            // the block's partial in units of q_row q_col: scale it back (powers of two, exact
+            // while in the normal range) and accumulate with round-to-nearest
+#pragma unroll
+            for (int j = 0; j < CH; j += 4) {
+              const float4 e = *reinterpret_cast<const float4*>(sbv + c0 + j);
+              acc[c0 + j] += ((__uint_as_float(r0[j]) + __uint_as_float(r1[j])) * sa) * e.x;
+              acc[c0 + j + 1] += ((__uint_as_float(r0[j + 1]) + __uint_as_float(r1[j + 1])) * sa) * e.y;
+              acc[c0 + j + 2] += ((__uint_as_float(r0[j + 2]) + __uint_as_float(r1[j + 2])) * sa) * e.z;
+              acc[c0 + j + 3] += ((__uint_as_float(r0[j + 3]) + __uint_as_float(r1[j + 3])) * sa) * e.w;
+            }
+          } else if (T > 1) {
 #pragma unroll
             for (int j = 0; j < CH; ++j) acc[c0 + j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
           } else {
@@ -430,16 +500,22 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
 // After an abort (the abort flag set), before the block releases its shared memory and TMEM: the
 // producer waits (bounded) until the loads it issued have landed -- the last min(issued, S) slots;
 // earlier ones were consumed -- and the MMA issuer until every MMA it issued has completed.
-__device__ __forceinline__ void tc_drain_after_abort(int slots, unsigned long long wait_ns, int* status,
+__device__ __forceinline__ void tc_drain_after_abort(int slots, int nbufs, unsigned long long wait_ns, int* status,
                                                      const TcShared& sh, const TcRing& r) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t S = static_cast<uint32_t>(slots);
   if (warp == 0 && lane == 0 && r.issued > 0) {
     const uint32_t first = r.issued > S ? r.issued - S : 0u;
     for (uint32_t i = first; i < r.issued; ++i) mbar_wait(sh.full0 + 8 * (i % S), (i / S) & 1u, wait_ns, status, 15);
-  } else if (warp == 1 && lane == 0 && r.any) {
-    mma_commit(sh.drain0);
-    mbar_wait(sh.drain0, 0u, wait_ns, status, 16);
+  } else if (warp == 1 && lane == 0) {
+    if (r.any) {
+      mma_commit(sh.drain0);
+      mbar_wait(sh.drain0, 0u, wait_ns, status, 16);
+    }
+    // scale copies issued: the last min(issued, NB) may still be landing
+    const uint32_t NB = static_cast<uint32_t>(nbufs);
+    const uint32_t first = r.scopies > NB ? r.scopies - NB : 0u;
+    for (uint32_t i = first; i < r.scopies; ++i) mbar_wait(sh.sfull0 + 8 * (i % NB), (i / NB) & 1u, wait_ns, status, 18);
   }
 }
 

@@ -16,7 +16,7 @@ from paper_2103_11595_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "bf16x6": 1e-6}
+TOL = {"f64": 1e-12, "f32": 1e-6, "bf16x6": 1e-6, "f16x3": 1e-6}
 # bounded modes: the two-term splits keep a floating leading term whose TMEM accumulation truncates
 # once per promoted K block, a small systematic shrink of every GEMM result (F comes out low)
 BOUND = {"tf32x3": 5e-6, "bf16x3": 5e-6}
@@ -248,13 +248,13 @@ def mid0_oracle():
     return inst, network.alg2_fidelity(inst, order="minfill")
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "tf32x3", "bf16x6", "f16x3"])
 def test_mid_config_alg2(mid0_oracle, precision):
     """n=16 line, 200 gates, 10 mixed noises: Alg. II on the GPU vs the oracle's own network."""
     inst, ref = mid0_oracle
     r, _, info = run(inst, 2, precision, trials=16)
     assert info["width"] <= 28
-    if precision in ("tf32x3", "bf16x6"):
+    if precision in ("tf32x3", "bf16x6", "f16x3"):
         assert info["n_tc_gemms"] > 0
     if precision in BOUND:
         check_bounded(r, ref, precision)
@@ -281,7 +281,7 @@ def precision_oracle():
     return inst, network.alg2_fidelity(inst, order="minfill")
 
 
-@pytest.mark.parametrize("precision", ["f64", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["f64", "tf32x3", "bf16x6", "f16x3"])
 def test_precision_config_alg2(precision_oracle, precision):
     """4x5 grid, depth-4 brickwork of Haar SU(4), depolarising on both qubits of every gate
     (62 noises): Alg. II against the oracle; bf16x6 within 1e-6, tf32x3 within its bound."""
@@ -295,7 +295,7 @@ def test_precision_config_alg2(precision_oracle, precision):
         check(r, ref, TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x6", "f16x3"])
 def test_batching_circuit_alg1(precision):
     """A circuit of the batching workload (n=14, 296 gates, 6 depolarising noises, 4096 traces):
     Alg. I on tensor cores against Alg. I and Alg. II in FP64; two traces against the oracle."""
@@ -369,7 +369,7 @@ def _oracle_alg2(key, make):
     return _ORACLE_F[key]
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "tf32x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "f16x3", "tf32x3"])
 @pytest.mark.parametrize("seed", [4, 10, 29, 36])
 def test_batching_alg1_tensor_cores_vs_oracle(seed, precision):
     """Batching workload circuits with n <= 16 (6 depolarising noises, 4096 traces): Alg. I on the
@@ -387,12 +387,13 @@ def test_batching_alg1_tensor_cores_vs_oracle(seed, precision):
         check(r, ref, TOL[precision])
 
 
+@pytest.mark.parametrize("precision", ["bf16x6", "f16x3"])
 @pytest.mark.parametrize("seed", range(10))
-def test_mid_bench_seeds_bf16x6_vs_oracle(seed):
-    """Every instance the bench times (mid workload, seeds 0-9, Alg. II, bf16x6, the bench's 32
-    planner restarts) against the oracle's own network contraction."""
+def test_mid_bench_seeds_vs_oracle(seed, precision):
+    """Every instance the bench times (mid workload, seeds 0-9, Alg. II, the bench's 32 planner
+    restarts) in both FP32-class tensor-core modes against the oracle's own network contraction."""
     ref = _oracle_alg2(("mid", seed), lambda: W.mid(seed))
-    r, _, info = run(W.mid(seed), 2, "bf16x6", trials=32)
+    r, _, info = run(W.mid(seed), 2, precision, trials=32)
     assert info["n_tc_gemms"] > 0
-    print(f"mid seed {seed}: |dF| = {abs(r['F'] - ref['F']):.3e}")
-    check(r, ref, TOL["bf16x6"])
+    print(f"mid seed {seed} {precision}: |dF| = {abs(r['F'] - ref['F']):.3e}")
+    check(r, ref, TOL[precision])

@@ -126,7 +126,7 @@ def test_k_split_gemm(M, N, K, T):
 # each leading term to a fixed-point multiple of a power of two per row and 128-byte K block) and
 # the tensor-core GEMM.
 
-SPLIT_MODES = ["bf16x6", "tf32x3", "bf16x3"]
+SPLIT_MODES = ["bf16x6", "f16x3", "tf32x3", "bf16x3"]
 
 
 @pytest.mark.parametrize("precision", SPLIT_MODES)
@@ -143,8 +143,9 @@ def test_split_gemm_exact_on_small_integers(precision, K):
     np.testing.assert_array_equal(C, A @ B.T)
 
 
+@pytest.mark.parametrize("precision", ["bf16x6", "f16x3"])
 @pytest.mark.parametrize("K", [256, 4096, 16384])
-def test_split_gemm_has_no_truncation_bias(K):
+def test_split_gemm_has_no_truncation_bias(precision, K):
     """Positive operands make a truncating accumulation visible: a plain TMEM sum drifts by about
     -(K/8) 2^-24 relative, and one promoted K block at a time still loses about 7e-8 (all errors of
     one sign, so the mean relative error is as large as the typical one). In the six-product split
@@ -154,11 +155,11 @@ def test_split_gemm_has_no_truncation_bias(K):
     rng = np.random.default_rng(K)
     A = rng.random((64, K))
     B = rng.random((128, K))
-    C = ajf.ajf_selftest_split_gemm(0, "bf16x6", A, B)
+    C = ajf.ajf_selftest_split_gemm(0, precision, A, B)
     ref = A @ B.T
     rel = (C - ref) / ref
     rms = float(np.sqrt(np.mean(rel ** 2)))
-    print(f"bf16x6 K={K}: mean {rel.mean():.2e} rms {rms:.2e} max {np.abs(rel).max():.2e}")
+    print(f"{precision} K={K}: mean {rel.mean():.2e} rms {rms:.2e} max {np.abs(rel).max():.2e}")
     assert abs(rel.mean()) < 1e-8
     assert abs(rel.mean()) < 0.1 * rms + 1e-10
     assert np.abs(rel).max() < 1e-6
@@ -184,13 +185,28 @@ def test_two_term_splits_are_bounded(precision):
 @pytest.mark.parametrize("M,N,K", [(64, 64, 64), (128, 512, 1024), (16, 1024, 32), (512, 64, 8192)])
 def test_split_gemm_random_signs(precision, M, N, K):
     """Random-sign Gaussian operands against the FP64 product: the error is bounded by the split's
-    representation error (bf16x6: 2^-26 of each row block's largest entry; tf32x3 and bf16x3: 2^-22
-    and 2^-17 of each entry) plus FP32 promotion."""
+    representation error (bf16x6: 2^-26 of each row block's largest entry; f16x3: 2^-22 of it, with
+    the dropped low-term products at 2^-20; tf32x3 and bf16x3: 2^-22 and 2^-17 of each entry) plus
+    FP32 promotion."""
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K))
     B = rng.standard_normal((N, K))
     C = ajf.ajf_selftest_split_gemm(0, precision, A, B)
     ref = A @ B.T
     absprod = np.abs(A) @ np.abs(B).T
-    bits = {"bf16x6": 22, "tf32x3": 18, "bf16x3": 15}[precision]
+    bits = {"bf16x6": 22, "f16x3": 19, "tf32x3": 18, "bf16x3": 15}[precision]
     assert np.all(np.abs(C - ref) <= 2.0 ** -bits * absprod * 8)
+
+
+@pytest.mark.parametrize("K", [8, 16, 32, 64, 128])
+def test_f16x3_scales_follow_each_row(K):
+    """Scaled fp16: rows and columns of wildly different magnitudes (2^-40 .. 2^40) keep their
+    relative accuracy, because each row's K block carries its own power-of-two scale; K below one
+    128-byte block (8-32 complex elements) shares one scale between the real and imaginary halves."""
+    rng = np.random.default_rng(K)
+    A = rng.standard_normal((32, K)) * np.exp2(rng.integers(-40, 40, (32, 1)))
+    B = rng.standard_normal((64, K)) * np.exp2(rng.integers(-40, 40, (64, 1)))
+    C = ajf.ajf_selftest_split_gemm(0, "f16x3", A, B)
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B).T
+    assert np.all(np.abs(C - ref) <= 2.0 ** -18 * scale)
