@@ -40,7 +40,7 @@ constexpr int kQTmemStride = 256;                          // two partials of up
 constexpr uint32_t kQTmemCols = kQBufs * kQTmemStride;
 constexpr size_t kQScratch = size_t(kQSlots) * kQSlotBytes;  // 192 KiB
 constexpr size_t kQArrays = 96 * 1024;                     // body arrays after the offset tables
-constexpr size_t kQSmem = kQScratch + kTcControlBytes + 1024 /* alignment */;
+constexpr size_t kQSmem = kQScratch + kTcControlBytes + kTcStageBytes + 1024 /* alignment */;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;

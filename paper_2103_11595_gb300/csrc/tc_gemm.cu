@@ -42,7 +42,8 @@
 //                    to release slots and hand partials to the epilogue;
 //   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
 //                    the BN columns of its rows: tcgen05.ld, FP32 round-to-nearest accumulation in
-//                    registers, FP64 store of the tile (rows < M, columns < N).
+//                    registers, FP64 store of the tile (rows < M, columns < N) staged through
+//                    shared memory so that every warp store writes whole 64-byte row segments.
 // Work items are (tile, K split) pairs. GEMMs with fewer tiles than SMs, or with more than
 // kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP64 partial
 // tile to a workspace and k_split_sum adds the splits in a fixed order (deterministic).
@@ -158,7 +159,7 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   if (p.slots < p.terms) return cudaErrorInvalidValue;
   p.bufs = 256 / BN > kMaxBufs ? kMaxBufs : 256 / BN;  // each buffer: 2 partials x BN TMEM columns
   p.tmem_stride = 2 * BN;
-  const size_t smem = size_t(p.slots) * p.slot_bytes + kTcControlBytes + 1024 /* alignment */;
+  const size_t smem = size_t(p.slots) * p.slot_bytes + kTcControlBytes + kTcStageBytes + 1024 /* alignment */;
   const int64_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt;
   if (mt > 0x7FFFFFFF || nt > 0x7FFFFFFF) return cudaErrorInvalidValue;

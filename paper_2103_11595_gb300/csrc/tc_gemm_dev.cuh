@@ -171,9 +171,17 @@ struct TcShared {
   uint32_t sfull0;                   // scaled fp16: the scales of TMEM buffer b have arrived
   float* scales;                     // scaled fp16: per TMEM buffer, 128 row scales then 128 column scales
   volatile int* abort_flag;
+  double* stage;                     // epilogue store staging: per epilogue warp, 32 rows x kStageStride
   uint32_t tmem;
 };
 constexpr int kScaleFloats = 256;    // floats of scales per TMEM buffer
+// The epilogue writes its FP64 tile through shared memory, kStageCols columns at a time: a thread
+// owns one row, so storing straight from registers would touch 32 rows (32 cache lines) per warp
+// store. Staged, each warp store covers 8 rows x 64 contiguous bytes. Rows are padded to 80 bytes,
+// so both the row-wise writes and the column-wise reads are free of bank conflicts.
+constexpr int kStageCols = 8;
+constexpr int kStageStride = kStageCols + 2;
+constexpr uint32_t kTcStageBytes = kEpiWarps * 32 * kStageStride * 8;
 
 // Ring positions of the three roles; they continue from one call of tc_gemm_items to the next
 // (the barrier phases must), so a caller keeps one TcRing per thread for the block's lifetime.
@@ -193,7 +201,7 @@ struct TcRing {
 
 // Layout of the pipeline's control region (kTcControlBytes from `bars`, 16-byte aligned): the
 // barrier arrays, the TMEM address slot, the abort flag, then the scale buffers of the scaled fp16
-// kind (kMaxBufs x kScaleFloats floats).
+// kind (kMaxBufs x kScaleFloats floats); the epilogue's staging buffers (kTcStageBytes) follow it.
 constexpr uint32_t kTcControlBytes = 256 + kMaxBufs * kScaleFloats * 4;
 __device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, TcShared& sh) {
   sh.slots = slots;
@@ -205,6 +213,7 @@ __device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, Tc
   sh.sfull0 = sh.drain0 + 8;              // scales of buffer b arrived
   sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 12);
   sh.scales = reinterpret_cast<float*>(bars + 256);
+  sh.stage = reinterpret_cast<double*>(bars + kTcControlBytes);
   return reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 8);  // TMEM address slot
 }
 
@@ -482,12 +491,26 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
       if (!ok) break;
       // the MMA warp is already filling the next buffers while this tile is written; FP32 -> FP64
       // is exact and runs on the integer pipe (GB300's FP64 rate would make a hardware conversion
-      // per element a visible cost of the store)
+      // per element a visible cost of the store). `mine` is the same for the whole warp.
       if (mine) {
-        double2* dstp = reinterpret_cast<double2*>(dbase + row * p.N + col0);
+        double* st = sh.stage + (warp - kEpiWarp0) * 32 * kStageStride;
+        double2* srow = reinterpret_cast<double2*>(st + lane * kStageStride);
+        // read-back: lane l carries 16-byte piece l / 8 of rows 8 i + l % 8
+        const int rr = lane & 7, pc = lane >> 3;
+        double* drow = dbase + (row - lane + rr) * p.N + col0 + 2 * pc;
 #pragma unroll
-        for (int j = 0; j < COLS / 2; ++j)
-          dstp[j] = make_double2(f32_to_f64_scaled(acc[2 * j], 0, 1.0), f32_to_f64_scaled(acc[2 * j + 1], 0, 1.0));
+        for (int c = 0; c < COLS; c += kStageCols) {
+#pragma unroll
+          for (int j = 0; j < kStageCols / 2; ++j)
+            srow[j] = make_double2(f32_to_f64_scaled(acc[c + 2 * j], 0, 1.0),
+                                   f32_to_f64_scaled(acc[c + 2 * j + 1], 0, 1.0));
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<double2*>(drow + 8 * i * p.N + c) =
+                reinterpret_cast<const double2*>(st + (8 * i + rr) * kStageStride)[pc];
+          __syncwarp();
+        }
       }
     }
     if (!ok) *sh.abort_flag = 1;
