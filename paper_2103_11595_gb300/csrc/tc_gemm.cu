@@ -43,7 +43,7 @@
 //   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
 //                    the BN columns of its rows: tcgen05.ld, FP32 round-to-nearest accumulation in
 //                    registers, FP64 store of the tile (rows < M, columns < N) staged through
-//                    shared memory so that every warp store writes whole 64-byte row segments.
+//                    shared memory so that every warp store writes whole 128-byte row segments.
 // Work items are (tile, K split) pairs. GEMMs with fewer tiles than SMs, or with more than
 // kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP64 partial
 // tile to a workspace and k_split_sum adds the splits in a fixed order (deterministic).

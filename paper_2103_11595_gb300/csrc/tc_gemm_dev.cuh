@@ -171,17 +171,19 @@ struct TcShared {
   uint32_t sfull0;                   // scaled fp16: the scales of TMEM buffer b have arrived
   float* scales;                     // scaled fp16: per TMEM buffer, 128 row scales then 128 column scales
   volatile int* abort_flag;
-  double* stage;                     // epilogue store staging: per epilogue warp, 32 rows x kStageStride
+  float* stage;                      // epilogue store staging: per epilogue warp, 32 rows x kStageCols
   uint32_t tmem;
 };
 constexpr int kScaleFloats = 256;    // floats of scales per TMEM buffer
 // The epilogue writes its FP64 tile through shared memory, kStageCols columns at a time: a thread
 // owns one row, so storing straight from registers would touch 32 rows (32 cache lines) per warp
-// store. Staged, each warp store covers 8 rows x 64 contiguous bytes. Rows are padded to 80 bytes,
-// so both the row-wise writes and the column-wise reads are free of bank conflicts.
-constexpr int kStageCols = 8;
-constexpr int kStageStride = kStageCols + 2;
-constexpr uint32_t kTcStageBytes = kEpiWarps * 32 * kStageStride * 8;
+// store. Staged (as FP32; converted to FP64 after the read-back), each warp store covers 4 rows x
+// 128 contiguous bytes, whole L2 lines: on GB300 a 128 x 128 FP64 tile pattern written in 64-byte
+// row pieces reached 3.4 TB/s, in 128-byte pieces 5.4 TB/s. The 16-byte chunks of a staged row are
+// XOR-swizzled by (row / 2) % 4, so the row-wise writes (8 rows per phase) and the read-back (two
+// rows per half-warp) are both free of bank conflicts.
+constexpr int kStageCols = 16;
+constexpr uint32_t kTcStageBytes = kEpiWarps * 32 * kStageCols * 4;
 
 // Ring positions of the three roles; they continue from one call of tc_gemm_items to the next
 // (the barrier phases must), so a caller keeps one TcRing per thread for the block's lifetime.
@@ -213,7 +215,7 @@ __device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, Tc
   sh.sfull0 = sh.drain0 + 8;              // scales of buffer b arrived
   sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 12);
   sh.scales = reinterpret_cast<float*>(bars + 256);
-  sh.stage = reinterpret_cast<double*>(bars + kTcControlBytes);
+  sh.stage = reinterpret_cast<float*>(bars + kTcControlBytes);
   return reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 8);  // TMEM address slot
 }
 
@@ -493,22 +495,26 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
       // is exact and runs on the integer pipe (GB300's FP64 rate would make a hardware conversion
       // per element a visible cost of the store). `mine` is the same for the whole warp.
       if (mine) {
-        double* st = sh.stage + (warp - kEpiWarp0) * 32 * kStageStride;
-        double2* srow = reinterpret_cast<double2*>(st + lane * kStageStride);
-        // read-back: lane l carries 16-byte piece l / 8 of rows 8 i + l % 8
-        const int rr = lane & 7, pc = lane >> 3;
-        double* drow = dbase + (row - lane + rr) * p.N + col0 + 2 * pc;
+        float* st = sh.stage + (warp - kEpiWarp0) * 32 * kStageCols;
+        float4* srow = reinterpret_cast<float4*>(st + lane * kStageCols);
+        const int wsw = (lane >> 1) & 3;
+        // read-back: lane l carries the float pair l % 8 (columns 2 (l % 8), + 1) of rows 4 i + l / 8
+        const int rr = lane >> 3, pr = lane & 7;
+        double* drow = dbase + (row - lane + rr) * p.N + col0 + 2 * pr;
 #pragma unroll
         for (int c = 0; c < COLS; c += kStageCols) {
 #pragma unroll
-          for (int j = 0; j < kStageCols / 2; ++j)
-            srow[j] = make_double2(f32_to_f64_scaled(acc[c + 2 * j], 0, 1.0),
-                                   f32_to_f64_scaled(acc[c + 2 * j + 1], 0, 1.0));
+          for (int j = 0; j < kStageCols / 4; ++j)
+            srow[j ^ wsw] = make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
           __syncwarp();
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<double2*>(drow + 8 * i * p.N + c) =
-                reinterpret_cast<const double2*>(st + (8 * i + rr) * kStageStride)[pc];
+          for (int i = 0; i < 32 / 4; ++i) {
+            const int rs = 4 * i + rr;
+            const float2 v = reinterpret_cast<const float2*>(st + rs * kStageCols +
+                                                             4 * ((pr >> 1) ^ ((rs >> 1) & 3)))[pr & 1];
+            *reinterpret_cast<double2*>(drow + 4 * i * p.N + c) =
+                make_double2(f32_to_f64_scaled(v.x, 0, 1.0), f32_to_f64_scaled(v.y, 0, 1.0));
+          }
           __syncwarp();
         }
       }
