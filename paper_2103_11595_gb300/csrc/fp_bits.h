@@ -2,9 +2,8 @@
 //
 // GB300 executes FP64 arithmetic at a small fraction of its FP32 and INT32 rates (about
 // 1.25 TFLOP/s on the whole chip). The tensor-core GEMM epilogue widens every FP32 accumulator to
-// FP64 and applies the de-biasing factor; as a hardware conversion plus an FP64 multiply per
-// element that took about 4% of the GEMM time of the n = 16 line workload. This routine works
-// on the IEEE-754 encodings with integer operations instead:
+// FP64; as a hardware conversion per element that was a visible part of the GEMM time of the
+// n = 16 line workload. This routine works on the IEEE-754 encodings with integer operations:
 //   binary32: sign (1 bit), exponent (8 bits, bias 127), fraction (23 bits);
 //   binary64: sign (1 bit), exponent (11 bits, bias 1023), fraction (52 bits).
 // Only normal numbers take the integer path; zero is handled inline; subnormal, infinite and NaN

@@ -1,7 +1,8 @@
 """FP32 -> scaled FP64 conversion on the integer pipe (tensor-core GEMM epilogue).
 
-The GEMM epilogue widens every FP32 accumulator to FP64 times the de-biasing factor by integer
-operations on the IEEE-754 encodings instead of GB300's slow FP64 arithmetic. The checks below
+The GEMM epilogue widens every FP32 accumulator to FP64 (a factor 1 + q 2^-46 is supported, the
+epilogue uses 1) by integer operations on the IEEE-754 encodings instead of GB300's slow FP64
+arithmetic. The checks below
 compare it with IEEE 754 itself (numpy's exact widening and correctly rounded products) and with
 CUDA's own conversion, over every binary32 exponent (zero and subnormals, normals, infinities and
 NaNs), both signs, and factors of either sign around 1.
