@@ -415,9 +415,13 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       lp.op_f64 = gmode == OPM_F64 ? 1 : 0;
       lp.first = static_cast<int>(P.perms.size());
       lp.count = 2;
-      const int64_t tiles = std::max<int64_t>(int64_t(1) << std::max(0, I.m + I.k - 10),
-                                              int64_t(1) << std::max(0, I.n + I.k - 10));
-      lp.blocks = static_cast<int>(std::min<int64_t>(std::max<int64_t>(tiles, 1), 2048));
+      // tiles of the larger operand (32 x 32 elements, 32 x 64 in the fixed-point split modes);
+      // at most four resident blocks per SM (152 on GB300), each walking several tiles, so that
+      // a block's lookup-table set-up is shared by its tiles
+      const int tile_bits = gmode == OPM_BF16X3 || gmode == OPM_F16X2S ? 11 : 10;
+      const int64_t tiles = std::max<int64_t>(int64_t(1) << std::max(0, I.m + I.k - tile_bits),
+                                              int64_t(1) << std::max(0, I.n + I.k - tile_bits));
+      lp.blocks = static_cast<int>(std::min<int64_t>(std::max<int64_t>(tiles, 1), 4 * 152));
       lp.smem = std::max(perm_table_bytes(px), perm_table_bytes(py));
       // gather traffic: both complex FP64 operands read once, every operand term written once
       lp.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) + std::ldexp(1.0, static_cast<int>(ly.size()))) * 16.0 +
