@@ -441,8 +441,9 @@ ajf_status ajf_profile_read(ajf_ctx *ctx, ajf_kernel_stats *stats, int cap);
  * C[M][N] = sum_{i + j < terms} A_i[M][K] . B_j[N][K]^T on device `device` for split operand
  * terms A_0..A_{terms-1}, B_0..B_{terms-1} (terms 1..3), FP32 accumulation promoted per K block.
  * kind 0: A and B hold terms * M * K (resp. N * K) FP32 values (read as TF32); kind 1: bf16 bit
- * patterns (uint16). All pointers are host memory; C receives M * N doubles. The call allocates
- * and frees its own device memory and synchronises the device.
+ * patterns (uint16). All pointers are host memory; C receives M * N doubles (the kernel's FP32
+ * results, widened exactly). The call allocates and frees its own device memory and synchronises
+ * the device.
  * Errors: AJF_E_ARG, AJF_E_UNSUPPORTED (shape not tile-aligned: M % 128, N power of two >= 32,
  * K a multiple of 128 bytes), AJF_E_CUDA, AJF_E_TIMEOUT. */
 ajf_status ajf_selftest_gemm(int device, int kind, int terms, int64_t M, int64_t N, int64_t K, const void *A,
@@ -459,9 +460,11 @@ ajf_status ajf_selftest_queue_timeout(int device, double wait_ms, int32_t *code)
 /* Self-test of one real product through the path's own operand preparation and tensor-core GEMM
  * (no paper counterpart; used by the test suite): C[M][N] = A[M][K] . B[N][K]^T for FP64 A and B
  * (row-major, host memory), on device `device`, in precision mode `precision` (AJF_PREC_TF32,
- * _TF32X3, _BF16X3 or _BF16X6). A and B enter as complex tensors with zero imaginary part; the
- * gather splits them into the mode's operand terms (the leading term quantised per row and
- * K block) and the GEMM forms the product as it does in a contraction step. M, N, K: powers of
+ * _TF32X3, _BF16X3, _BF16X6 or _F16X3). A and B enter as complex64 tensors with zero imaginary
+ * part, as the reduced-precision modes store tensors (each value rounded to FP32, to nearest);
+ * the gather splits them into the mode's operand terms (the leading term quantised per row and
+ * K block) and the GEMM forms the product as it does in a contraction step (FP32 results, widened
+ * exactly into C). M, N, K: powers of
  * two with M >= 16, N >= 16, K >= 8. C receives M * N doubles. The call allocates and frees its
  * own device memory and synchronises the device.
  * Errors: AJF_E_ARG, AJF_E_UNSUPPORTED (shape), AJF_E_NOMEM, AJF_E_CUDA, AJF_E_TIMEOUT. */

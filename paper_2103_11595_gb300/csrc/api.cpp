@@ -387,8 +387,8 @@ ajf_status prepare_tc_set(ajf_ctx* c, ajf_ctx::TcPrepSet* tc) {
     const Launch& ln = P.launches[i];
     if (ln.kind != LK_GEMM_TC) continue;
     const cudaError_t e = tc_gemm_prepare(&tc->prep[i], base, ln.a_off, ln.b_off, ln.npass,
-                                          reinterpret_cast<double*>(base + ln.c_off), ln.M, ln.N, ln.K, ln.tc_kind,
-                                          reinterpret_cast<double*>(base + ln.ws_off), ln.ksplit, status, kTcWaitNs, 0);
+                                          reinterpret_cast<float*>(base + ln.c_off), ln.M, ln.N, ln.K, ln.tc_kind,
+                                          reinterpret_cast<float*>(base + ln.ws_off), ln.ksplit, status, kTcWaitNs, 0);
     if (e != cudaSuccess) {
       tc->gen = -1;
       return cuda_fail(c, e, "tensor-core GEMM set-up");
@@ -404,12 +404,11 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = 
   char* base = c->arena;
   if (!tc) tc = &c->tc_own;
   void* arena = base;
-  const bool f64 = P.f64;
   cudaError_t e;
   {
     ProfScope ps(c, s, 0, 0, 0);
     e = launch_leaves(reinterpret_cast<const LeafDev*>(base + P.off_leaves), static_cast<int>(P.leaves.size()),
-                      reinterpret_cast<const double*>(base + P.off_inputs), arena, f64, s);
+                      reinterpret_cast<const double*>(base + P.off_inputs), arena, s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "leaf kernel");
   const StepDev* steps = reinterpret_cast<const StepDev*>(base + P.off_steps);
@@ -432,10 +431,10 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = 
         e = launch_dot(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, ln.op_f64 == 0, s);
         break;
       case LK_SMALL:
-        e = launch_small(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, f64, s);
+        e = launch_small(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, s);
         break;
       case LK_SPLITK:
-        e = launch_splitk(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, f64, s);
+        e = launch_splitk(steps + ln.first, ln.count, ln.blocks, ln.smem, arena, partial, scalars, s);
         break;
       case LK_PERM:
         e = launch_perm(perms + ln.first, ln.count, ln.blocks, ln.smem, arena, base, ln.op_f64 != 0, s);
@@ -457,7 +456,7 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = 
     e = launch_final(reinterpret_cast<const FinalDev*>(base + P.off_final), P.final_nchunks, P.final_blocks, arena,
                      scalars, reinterpret_cast<double*>(base + P.off_traces),
                      reinterpret_cast<double*>(base + P.off_open_partial), reinterpret_cast<double*>(base + P.off_result),
-                     f64, s);
+                     s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "final reduction");
   return AJF_OK;
@@ -1180,7 +1179,7 @@ ajf_status plan_one(ajf_ctx* c, int alg, const ajf_plan_opts* opts, ajf_plan_inf
         pi.n_leaves = static_cast<int32_t>(c->net.leaf_labels.size());
         pi.n_open_bits = static_cast<int32_t>(c->net.open_labels.size());
         pi.planner_used = c->path.planner;
-        pi.arena_bytes = std::ldexp(1.0, c->path.width) * 16.0;
+        pi.arena_bytes = std::ldexp(1.0, c->path.width) * pp.elem_bytes;
         pi.n_sliced_bonds = static_cast<int32_t>(c->bond_labels.size());
         pi.cmacs = std::ldexp(pi.cmacs, pi.n_sliced_bonds);
         pi.flops = std::ldexp(pi.flops, pi.n_sliced_bonds);
@@ -1403,8 +1402,8 @@ ajf_status ajf_selftest_check_plan(ajf_ctx* c, int mutation) {
           if (pred(P.steps[k])) return &P.steps[k];
     return nullptr;
   };
-  // Point the reads of the tensor at element offset `from` (plane `plane`, written before launch
-  // `first`) to `to`: launches from `first` on, until one writes over its old place.
+  // Point the reads of the complex128 tensor at element offset `from` (plane `plane`, written
+  // before launch `first`) to `to`: launches from `first` on, until one writes over its old place.
   auto redirect = [&](int64_t from, int64_t plane, size_t first, int64_t to) {
     const int64_t lo = from, hi = from + 2 * plane;
     auto hits = [&](int64_t o, int64_t p) { return o < hi && lo < o + 2 * p; };
@@ -1414,21 +1413,22 @@ ajf_status ajf_selftest_check_plan(ajf_ctx* c, int mutation) {
       if (ln.kind == LK_SMALL || ln.kind == LK_SPLITK || ln.kind == LK_DOT) {
         for (int k = ln.first; k < ln.first + ln.count; ++k) {
           StepDev& d = P.steps[k];
-          if (d.a == from && d.pa == plane) d.a = to;
-          if (d.b == from && d.pb == plane) d.b = to;
+          if (d.a == from && d.pa == plane && !d.fa) d.a = to;
+          if (d.b == from && d.pb == plane && !d.fb) d.b = to;
         }
         for (int k = ln.first; k < ln.first + ln.count; ++k)
           overwritten = overwritten || (P.steps[k].scalar_slot < 0 && hits(P.steps[k].c, P.steps[k].pc));
       } else if (ln.kind == LK_PERM) {
         for (int k = ln.first; k < ln.first + ln.count; ++k)
-          if (P.perms[k].src == from && P.perms[k].plane == plane) P.perms[k].src = to;
+          if (P.perms[k].src == from && P.perms[k].plane == plane && !P.perms[k].src_f32) P.perms[k].src = to;
       } else {
-        const int64_t c0 = ln.c_off / static_cast<int64_t>(P.elem);
-        overwritten = hits(c0, ln.M * ln.N / 2);
+        // the GEMM's result, in FP64 units (complex64 from a reduced-precision GEMM)
+        const int64_t ce = ln.op_f64 ? 8 : 4;
+        overwritten = hits(ln.c_off / 8, ln.M * ln.N * ce / 16);
       }
       if (overwritten) return;
     }
-    if (P.fin.open_off == from && P.fin.open_plane == plane) P.fin.open_off = to;
+    if (P.fin.open_off == from && P.fin.open_plane == plane && !P.fin.open_f32) P.fin.open_off = to;
   };
   switch (mutation) {
     case 1:  // a leaf placed past the end of the work region
@@ -1691,7 +1691,7 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
   if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
   if (!tc_gemm_supported(M, N, K, kind)) return AJF_E_UNSUPPORTED;
   const size_t es = kind == 1 ? 2 : 4;
-  const size_t abytes = size_t(npass) * M * K * es, bbytes = size_t(npass) * N * K * es, cbytes = size_t(M) * N * 8;
+  const size_t abytes = size_t(npass) * M * K * es, bbytes = size_t(npass) * N * K * es, cbytes = size_t(M) * N * 4;
   const int ksplit = tc_gemm_splits(M, N, K, kind);
   const size_t wbytes = ksplit > 1 ? size_t(ksplit) * cbytes : 0;
   char* d = nullptr;
@@ -1710,14 +1710,17 @@ ajf_status ajf_selftest_gemm(int device, int kind, int npass, int64_t M, int64_t
       cudaMemcpy(d + off_b, B, bbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(d + off_s, 0, 256) != cudaSuccess)
     st = AJF_E_CUDA;
-  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, npass, reinterpret_cast<double*>(d + off_c), M, N, K, kind,
-                                     reinterpret_cast<double*>(d + off_w), ksplit, reinterpret_cast<int*>(d + off_s),
+  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, npass, reinterpret_cast<float*>(d + off_c), M, N, K, kind,
+                                     reinterpret_cast<float*>(d + off_w), ksplit, reinterpret_cast<int*>(d + off_s),
                                      0) != cudaSuccess)
     st = AJF_E_CUDA;
   if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
-  if (st == AJF_OK && (cudaMemcpy(C, d + off_c, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+  std::vector<float> cf(size_t(M) * N);
+  if (st == AJF_OK && (cudaMemcpy(cf.data(), d + off_c, cbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
                        cudaMemcpy(&status, d + off_s, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
     st = AJF_E_CUDA;
+  if (st == AJF_OK)
+    for (size_t i = 0; i < cf.size(); ++i) C[i] = cf[i];  // FP32 -> FP64, exact
   if (st == AJF_OK && status != 0) st = AJF_E_TIMEOUT;
   cudaFree(d);
   return st;
@@ -1792,15 +1795,15 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
   const size_t eb = kind != 0 ? 2 : 4;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  // device layout: A and B as planar complex FP64 (imaginary planes zero), operand terms, C,
-  // K-split workspace, status word
-  const size_t a_src = 0, b_src = al(2 * size_t(M) * K * 8);
-  const size_t x0 = b_src + al(2 * size_t(N) * K * 8);
+  // device layout: A and B as planar complex64 tensors (FP32 planes, imaginary planes zero; the
+  // tensors of the reduced-precision modes), operand terms, C (FP32), K-split workspace, status
+  const size_t a_src = 0, b_src = al(2 * size_t(M) * K * 4);
+  const size_t x0 = b_src + al(2 * size_t(N) * K * 4);
   const size_t xbytes = al(size_t(Mt) * Kt * eb), ybytes = al(size_t(N) * Kt * eb);
   const size_t y0 = x0 + terms * xbytes;
   const size_t c_off = y0 + terms * ybytes;
   const int ksplit = tc_gemm_splits(Mt, N, Kt, kind);
-  const size_t cbytes = al(size_t(Mt) * N * 8);
+  const size_t cbytes = al(size_t(Mt) * N * 4);
   const size_t w_off = c_off + cbytes, s_off = w_off + (ksplit > 1 ? ksplit * cbytes : 0);
   const size_t p_off = s_off + 256;
   // scaled fp16: one FP32 scale per row and 128-byte K block of each operand
@@ -1814,7 +1817,8 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   for (int side = 0; side < 2; ++side) {
     PermDev& q = pd[side];
     const int rb = side == 0 ? mb : nb;
-    q.src = static_cast<int64_t>((side == 0 ? a_src : b_src) / 8);
+    q.src = static_cast<int64_t>((side == 0 ? a_src : b_src) / 4);
+    q.src_f32 = 1;
     q.plane = (int64_t(1) << rb) * K;
     q.rows.nbits = rb;
     for (int i = 0; i < rb; ++i) q.rows.pos[i] = static_cast<int8_t>(kb + i);
@@ -1830,11 +1834,11 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
     if (kind == 2) q.dst[2] = static_cast<int64_t>(side == 0 ? xs_off : ys_off);
   }
   ajf_status st = AJF_OK;
-  std::vector<double> planar(2 * size_t(std::max(M, N)) * K, 0.0);
+  std::vector<float> planar(2 * size_t(std::max(M, N)) * K, 0.0f);
   auto upload = [&](const double* src, int64_t rows, size_t off) {
-    std::fill(planar.begin(), planar.end(), 0.0);
-    std::memcpy(planar.data(), src, size_t(rows) * K * sizeof(double));
-    return cudaMemcpy(d + off, planar.data(), 2 * size_t(rows) * K * sizeof(double), cudaMemcpyHostToDevice);
+    std::fill(planar.begin(), planar.end(), 0.0f);
+    for (size_t i = 0; i < size_t(rows) * K; ++i) planar[i] = static_cast<float>(src[i]);  // round to nearest
+    return cudaMemcpy(d + off, planar.data(), 2 * size_t(rows) * K * sizeof(float), cudaMemcpyHostToDevice);
   };
   if (upload(A, M, a_src) != cudaSuccess || upload(B, N, b_src) != cudaSuccess ||
       cudaMemcpy(d + p_off, pd.data(), 2 * sizeof(PermDev), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1856,16 +1860,19 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
     ao[2] = static_cast<int64_t>(xs_off);
     bo[2] = static_cast<int64_t>(ys_off);
   }
-  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, terms, reinterpret_cast<double*>(d + c_off), Mt, N, Kt, kind,
-                                     reinterpret_cast<double*>(d + w_off), ksplit, reinterpret_cast<int*>(d + s_off),
+  if (st == AJF_OK && launch_gemm_tc(d, ao, bo, terms, reinterpret_cast<float*>(d + c_off), Mt, N, Kt, kind,
+                                     reinterpret_cast<float*>(d + w_off), ksplit, reinterpret_cast<int*>(d + s_off),
                                      0) != cudaSuccess)
     st = AJF_E_CUDA;
   if (st == AJF_OK && cudaDeviceSynchronize() != cudaSuccess) st = AJF_E_CUDA;
   int status = 0;
   // the first M rows of C' = [[A, 0], [0, A]] [B | 0]^T hold A . B^T
-  if (st == AJF_OK && (cudaMemcpy(C, d + c_off, size_t(M) * N * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+  std::vector<float> cf(size_t(M) * N);
+  if (st == AJF_OK && (cudaMemcpy(cf.data(), d + c_off, cf.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
                        cudaMemcpy(&status, d + s_off, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
     st = AJF_E_CUDA;
+  if (st == AJF_OK)
+    for (size_t i = 0; i < cf.size(); ++i) C[i] = cf[i];  // FP32 -> FP64, exact
   if (st == AJF_OK && status != 0) st = AJF_E_TIMEOUT;
   cudaFree(d);
   return st;
@@ -1932,7 +1939,7 @@ ajf_status ajf_selftest_wait_timeout(int device, double wait_ms, int32_t* code) 
   const int64_t ao[1] = {0}, bo[1] = {static_cast<int64_t>(off_b)};
   if (cudaMemset(d, 0, off_s + 256) != cudaSuccess) st = AJF_E_CUDA;
   if (st == AJF_OK &&
-      launch_gemm_tc_ex(d, ao, bo, 1, reinterpret_cast<double*>(d + off_c), M, N, K, 0, nullptr, 1,
+      launch_gemm_tc_ex(d, ao, bo, 1, reinterpret_cast<float*>(d + off_c), M, N, K, 0, nullptr, 1,
                         reinterpret_cast<int*>(d + off_s), 0, static_cast<unsigned long long>(wait_ms * 1e6),
                         1) != cudaSuccess)
     st = AJF_E_CUDA;

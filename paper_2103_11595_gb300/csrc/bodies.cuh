@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "device.h"
 #include "fp_bits.h"
@@ -65,6 +66,23 @@ __device__ __forceinline__ int64_t lookup(const int64_t* tab, int nc, int64_t id
   int64_t off = 0;
   for (int c = 0; c < nc; ++c) off += tab[(c << 8) | ((idx >> (8 * c)) & 255)];
   return off;
+}
+
+// Operand `off` (element offset in its own type's units) of a step whose tensor is complex64 (f32:
+// FP32 planes, the product of a reduced-precision GEMM) or complex128 (FP64 planes, every other
+// tensor), and `arena` the arena as FP64 elements: calls fn with the typed pointer, so that each
+// combination of operand types gets its own loop.
+template <typename Fn>
+__device__ __forceinline__ void with_operands(const double* arena, int64_t a, bool fa, int64_t b, bool fb, Fn&& fn) {
+  const float* af = reinterpret_cast<const float*>(arena) + a;
+  const float* bf = reinterpret_cast<const float*>(arena) + b;
+  if (fa) {
+    if (fb) fn(af, bf);
+    else fn(af, arena + b);
+  } else {
+    if (fb) fn(arena + a, bf);
+    else fn(arena + a, arena + b);
+  }
 }
 
 // ------------------------------------------------------------------ leaves
@@ -173,22 +191,22 @@ __device__ __forceinline__ void small_body(const StepDev* __restrict__ steps, in
   build_table(st.kb, t_kb);
   Sync::sync();
   const int64_t nout = int64_t(1) << st.rc, nk = int64_t(1) << st.rk;
-  const T* A = arena + st.a;
-  const T* B = arena + st.b;
   T* C = arena + st.c;
-  for (int64_t o = int64_t(vb - st.block0) * kBodyThreads + threadIdx.x; o < nout;
-       o += int64_t(nb) * kBodyThreads) {
-    const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
-    Acc re = 0, im = 0;
-    for (int64_t kk = 0; kk < nk; ++kk) {
-      const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
-      const Acc ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
-      re += ar * br - ai * bi;
-      im += ar * bi + ai * br;
+  with_operands(arena, st.a, st.fa, st.b, st.fb, [&](const auto* A, const auto* B) {
+    for (int64_t o = int64_t(vb - st.block0) * kBodyThreads + threadIdx.x; o < nout;
+         o += int64_t(nb) * kBodyThreads) {
+      const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
+      Acc re = 0, im = 0;
+      for (int64_t kk = 0; kk < nk; ++kk) {
+        const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+        const Acc ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+        re += ar * br - ai * bi;
+        im += ar * bi + ai * br;
+      }
+      C[o] = static_cast<T>(re);
+      C[st.pc + o] = static_cast<T>(im);
     }
-    C[o] = static_cast<T>(re);
-    C[st.pc + o] = static_cast<T>(im);
-  }
+  });
 }
 
 
@@ -217,15 +235,15 @@ __device__ __forceinline__ void splitk_body(const StepDev* __restrict__ steps, i
   const int64_t k0 = int64_t(split) * chunk;
   const int64_t k1 = min(nk, k0 + chunk);
   const int64_t oa = lookup(t_oa, c_oa, o), ob = lookup(t_ob, c_ob, o);
-  const T* A = arena + st.a;
-  const T* B = arena + st.b;
   double re = 0, im = 0;
-  for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += kBodyThreads) {
-    const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
-    const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
-    re += ar * br - ai * bi;
-    im += ar * bi + ai * br;
-  }
+  with_operands(arena, st.a, st.fa, st.b, st.fb, [&](const auto* A, const auto* B) {
+    for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += kBodyThreads) {
+      const int64_t ia = oa + lookup(t_ka, c_ka, kk), ib = ob + lookup(t_kb, c_kb, kk);
+      const double ar = A[ia], ai = A[st.pa + ia], br = B[ib], bi = B[st.pb + ib];
+      re += ar * br - ai * bi;
+      im += ar * bi + ai * br;
+    }
+  });
   red_re[threadIdx.x] = re;
   red_im[threadIdx.x] = im;
   Sync::sync();
@@ -246,8 +264,9 @@ __device__ __forceinline__ void splitk_body(const StepDev* __restrict__ steps, i
 // Phase 1 stages the tile of A in shared memory in A order (lanes along A's contiguous bits);
 // phase 2 streams the tile of B in B order and multiplies with the staged A values. FP64 partial
 // sums per block; k_splitk_done adds them in a fixed order. kF32 (reduced-precision modes): the
-// products of each tile are formed and summed in FP32 per thread (FP32 rounding of the operands,
-// relative error ~1e-7 per term) and the tile sums are accumulated in FP64.
+// products of each tile are formed and summed in FP32 per thread (FP32 operands: complex64
+// tensors as they are, complex128 ones rounded; relative error ~1e-7 per term) and the tile sums
+// are accumulated in FP64.
 template <typename T, bool kF32, typename Sync>
 __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int nsteps, const T* __restrict__ arena,
                                          double2* __restrict__ partial, int vb, int64_t* tab, double* red_re,
@@ -261,8 +280,10 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
   int64_t* t_kb = t_ka + c_ka * 256;
   int64_t* locA = t_kb + c_kb * 256;         // [nt] offset in A of tile-local index (A order)
   int64_t* locB = locA + nt;                 // [nt] offset in B of tile-local index (B order)
-  double* sre = reinterpret_cast<double*>(locB + nt);
-  double* sim = sre + nt;
+  // staged and register values: FP32 for FP32 products, FP64 otherwise
+  using V = typename std::conditional<kF32, float, double>::type;
+  V* sre = reinterpret_cast<V*>(locB + nt);
+  V* sim = sre + nt;
   uint16_t* a_of_b = reinterpret_cast<uint16_t*>(sim + nt);  // B-order local index -> A-order
   build_table(st.ka, t_ka);
   build_table(st.kb, t_kb);
@@ -287,95 +308,95 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
   }
   Sync::sync();
   const int64_t ntiles = int64_t(1) << (st.rk - ntl);
-  const T* A = arena + st.a;
-  const T* B = arena + st.b;
-  // the tile's base offsets in A and B: the tile number spread over the non-tile bits
-  auto tile_base = [&](int64_t t, int64_t& ba, int64_t& bb) {
-    uint64_t base = 0;
-    int64_t rem = t;
-    for (int i = 0; i < st.rk && rem; ++i) {
-      if ((tilemask >> i) & 1) continue;
-      if (rem & 1) base |= uint64_t(1) << i;
-      rem >>= 1;
-    }
-    ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
-    bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
-  };
-  // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
-  // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
-  // so the loads of two tiles are in flight. Staged A values sit at index l ^ ((l >> 5) & 31):
-  // B-ordered reads that stride across A's index (B's low bits on A's high bits) then fall into
-  // distinct shared-memory banks.
-  constexpr int kPer = 4;
-  double are[kPer], aim[kPer], bre[kPer], bim[kPer];
-  auto load_tile = [&](int64_t t) {
-    int64_t ba, bb;
-    tile_base(t, ba, bb);
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int l = threadIdx.x + q * kBodyThreads;
-      if (l < nt) {
-        are[q] = A[ba + locA[l]];
-        aim[q] = A[st.pa + ba + locA[l]];
-        bre[q] = B[bb + locB[l]];
-        bim[q] = B[st.pb + bb + locB[l]];
-      }
-    }
-  };
   double re = 0, im = 0;
-  int64_t t = split;
-  if (t < ntiles) load_tile(t);
-  while (t < ntiles) {
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int l = threadIdx.x + q * kBodyThreads;
-      if (l < nt) {
-        const int sl = l ^ ((l >> 5) & 31);
-        sre[sl] = are[q];
-        sim[sl] = aim[q];
+  with_operands(arena, st.a, st.fa, st.b, st.fb, [&](const auto* A, const auto* B) {
+    // the tile's base offsets in A and B: the tile number spread over the non-tile bits
+    auto tile_base = [&](int64_t t, int64_t& ba, int64_t& bb) {
+      uint64_t base = 0;
+      int64_t rem = t;
+      for (int i = 0; i < st.rk && rem; ++i) {
+        if ((tilemask >> i) & 1) continue;
+        if (rem & 1) base |= uint64_t(1) << i;
+        rem >>= 1;
       }
-    }
-    double cbr[kPer], cbi[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      cbr[q] = bre[q];
-      cbi[q] = bim[q];
-    }
-    Sync::sync();
-    const int64_t tn = t + st.nsplit;
-    if (tn < ntiles) load_tile(tn);
-    if (kF32) {
-      float fre = 0.0f, fim = 0.0f;
+      ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
+      bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
+    };
+    // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
+    // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
+    // so the loads of two tiles are in flight. Staged A values sit at index l ^ ((l >> 5) & 31):
+    // B-ordered reads that stride across A's index (B's low bits on A's high bits) then fall into
+    // distinct shared-memory banks.
+    constexpr int kPer = 4;
+    V are[kPer], aim[kPer], bre[kPer], bim[kPer];
+    auto load_tile = [&](int64_t t) {
+      int64_t ba, bb;
+      tile_base(t, ba, bb);
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
         const int l = threadIdx.x + q * kBodyThreads;
         if (l < nt) {
-          const int la = a_of_b[l];
-          const int sl = la ^ ((la >> 5) & 31);
-          const float ar = static_cast<float>(sre[sl]), ai = static_cast<float>(sim[sl]);
-          const float br = static_cast<float>(cbr[q]), bi = static_cast<float>(cbi[q]);
-          fre += ar * br - ai * bi;
-          fim += ar * bi + ai * br;
+          are[q] = static_cast<V>(A[ba + locA[l]]);
+          aim[q] = static_cast<V>(A[st.pa + ba + locA[l]]);
+          bre[q] = static_cast<V>(B[bb + locB[l]]);
+          bim[q] = static_cast<V>(B[st.pb + bb + locB[l]]);
         }
       }
-      re += fre;
-      im += fim;
-    } else {
+    };
+    int64_t t = split;
+    if (t < ntiles) load_tile(t);
+    while (t < ntiles) {
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
         const int l = threadIdx.x + q * kBodyThreads;
         if (l < nt) {
-          const int la = a_of_b[l];
-          const int sl = la ^ ((la >> 5) & 31);
-          const double ar = sre[sl], ai = sim[sl];
-          re += ar * cbr[q] - ai * cbi[q];
-          im += ar * cbi[q] + ai * cbr[q];
+          const int sl = l ^ ((l >> 5) & 31);
+          sre[sl] = are[q];
+          sim[sl] = aim[q];
         }
       }
+      V cbr[kPer], cbi[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        cbr[q] = bre[q];
+        cbi[q] = bim[q];
+      }
+      Sync::sync();
+      const int64_t tn = t + st.nsplit;
+      if (tn < ntiles) load_tile(tn);
+      if (kF32) {
+        float fre = 0.0f, fim = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          const int l = threadIdx.x + q * kBodyThreads;
+          if (l < nt) {
+            const int la = a_of_b[l];
+            const int sl = la ^ ((la >> 5) & 31);
+            const float ar = static_cast<float>(sre[sl]), ai = static_cast<float>(sim[sl]);
+            const float br = static_cast<float>(cbr[q]), bi = static_cast<float>(cbi[q]);
+            fre += ar * br - ai * bi;
+            fim += ar * bi + ai * br;
+          }
+        }
+        re += fre;
+        im += fim;
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          const int l = threadIdx.x + q * kBodyThreads;
+          if (l < nt) {
+            const int la = a_of_b[l];
+            const int sl = la ^ ((la >> 5) & 31);
+            const double ar = sre[sl], ai = sim[sl], br = cbr[q], bi = cbi[q];
+            re += ar * br - ai * bi;
+            im += ar * bi + ai * br;
+          }
+        }
+      }
+      Sync::sync();
+      t = tn;
     }
-    Sync::sync();
-    t = tn;
-  }
+  });
   red_re[threadIdx.x] = re;
   red_im[threadIdx.x] = im;
   Sync::sync();
@@ -582,7 +603,9 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
   const int KW = TK > 32 ? 64 : 32;                // k extent of the thread mapping
   const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
   const int64_t ntr = R / TR, ntk = K / TK;
+  // the source: complex64 (p.src_f32, a reduced-precision GEMM's product) or complex128
   const double* src = arena + p.src;
+  const float* srcf = reinterpret_cast<const float*>(arena) + p.src;
   const int64_t ld = 2 * K;
   for (int64_t tile = vb; tile < ntr * ntk; tile += vg) {
     const int64_t r0 = (tile / ntk) * TR, k0 = (tile % ntk) * TK;
@@ -591,7 +614,7 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
       koff[threadIdx.x - 32] = threadIdx.x - 32 < TK ? lookup(t_k, c_k, k0 + threadIdx.x - 32) : 0;
     Sync::sync();
     // all loads (x 2 planes) of a thread are issued before its shared-memory stores
-    double vr[8], vi[8];
+    S vr[8], vi[8];
 #pragma unroll
     for (int q = 0; q < TKMAX / 8; ++q) {
       if (q < KW / 8) {
@@ -599,8 +622,13 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
         const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
         if (rr < TR && kk < TK) {
           const int64_t off = roff[rr] + koff[kk];
-          vr[q] = src[off];
-          vi[q] = src[p.plane + off];
+          if (p.src_f32) {
+            vr[q] = srcf[off];
+            vi[q] = srcf[p.plane + off];
+          } else {
+            vr[q] = static_cast<S>(src[off]);
+            vi[q] = static_cast<S>(src[p.plane + off]);
+          }
         }
       }
     }
@@ -610,8 +638,8 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
         const int l = threadIdx.x + 256 * q;
         const int rr = p.rows_fast ? (l & 31) : l / KW, kk = p.rows_fast ? (l >> 5) : (l & (KW - 1));
         if (rr < TR && kk < TK) {
-          tre[rr][kk] = static_cast<S>(vr[q]);
-          tim[rr][kk] = static_cast<S>(vi[q]);
+          tre[rr][kk] = vr[q];
+          tim[rr][kk] = vi[q];
         }
       }
     }
@@ -718,8 +746,14 @@ __device__ __forceinline__ void open_body(const FinalDev* __restrict__ fd, const
     double tr = 1, ti = 0;
     if (f.open_off >= 0) {
       const int64_t off = lookup(tab, c, j);
-      tr = static_cast<double>(arena[f.open_off + off]);
-      ti = static_cast<double>(arena[f.open_off + f.open_plane + off]);
+      if (f.open_f32) {  // the product of a reduced-precision GEMM (complex64)
+        const float* of = reinterpret_cast<const float*>(arena) + f.open_off;
+        tr = of[off];
+        ti = of[f.open_plane + off];
+      } else {
+        tr = static_cast<double>(arena[f.open_off + off]);
+        ti = static_cast<double>(arena[f.open_off + f.open_plane + off]);
+      }
     }
     const double vr = tr * sr - ti * si, vi = tr * si + ti * sr;
     traces[2 * j] = vr;
@@ -758,13 +792,21 @@ __device__ __forceinline__ void final_body(const FinalDev* __restrict__ fd, cons
   result[2] = (d2 - S) / d2;
 }
 
-// C[i] = sum over splits s (in order) of W[s][i], block vb of vg.
-__device__ __forceinline__ void split_sum_body(const double* __restrict__ W, int ksplit, int64_t n,
-                                               double* __restrict__ C, int vb, int vg) {
+// C[i] = sum over splits s (in order) of W[s][i], block vb of vg: the FP32 partials of a K-split
+// tensor-core GEMM, added in FP32 with Kahan's compensation (the sum's error stays within a few
+// units in the last place of the largest partial, whatever the number of splits; no FP64
+// arithmetic, which GB300 runs at a small fraction of its FP32 rate).
+__device__ __forceinline__ void split_sum_body(const float* __restrict__ W, int ksplit, int64_t n,
+                                               float* __restrict__ C, int vb, int vg) {
   for (int64_t i = int64_t(vb) * kBodyThreads + threadIdx.x; i < n; i += int64_t(vg) * kBodyThreads) {
-    double v = 0;
-    for (int s = 0; s < ksplit; ++s) v += W[s * n + i];
-    C[i] = v;
+    float s = 0.0f, comp = 0.0f;
+    for (int k = 0; k < ksplit; ++k) {
+      const float y = W[k * n + i] - comp;
+      const float t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
+    C[i] = s;
   }
 }
 

@@ -1,9 +1,12 @@
 // Device-side step descriptors shared by the lowering (host) and the kernels (device).
 //
 // Storage: every tensor lives in one device arena in planar complex form -- a real plane of
-// 2^r elements followed by an imaginary plane of 2^r elements -- in the working precision
-// (double for AJF_PREC_F64, float otherwise). Element index = sum_i bit_i * 2^i, where bit i is
-// the tensor's i-th label. Scalars produced by full contractions are FP64 (double2 slots).
+// 2^r elements followed by an imaginary plane of 2^r elements. Tensors are complex128 (FP64
+// planes), except the products of reduced-precision GEMMs, which are complex64 (FP32 planes: the
+// GEMM promotes each result to one FP32 register sum, so nothing is lost); an element offset is in
+// units of the tensor's own element type from the arena base. Element index = sum_i bit_i * 2^i,
+// where bit i is the tensor's i-th label. Scalars produced by full contractions are FP64 (double2
+// slots).
 #pragma once
 #include <cstdint>
 
@@ -33,6 +36,8 @@ struct StepDev {
   int32_t ntl;            // tiled dot: bits of a tile (<= 10)
   int8_t tl[16];          // tiled dot: contracted-index bits of a tile, ordered by A position
   int8_t tlb[16];         // tiled dot: the same bits ordered by B position
+  int8_t fa, fb;          // A / B is complex64 (FP32 planes); the output C is always complex128
+  int8_t pad8[6];
 };
 
 // Operand preparation for a GEMM step: gather a complex tensor into a real row-major,
@@ -48,7 +53,7 @@ struct PermDev {
   int32_t embed;          // 1: X side (embedded), 0: Y side
   int32_t rows_fast;      // 1: read with lanes along rows (the source's stride-1 bit is a row bit)
   int32_t mode;           // operand format, see OperandMode
-  int32_t pad;
+  int32_t src_f32;        // the source is complex64 (FP32 planes), else complex128
 };
 
 enum OperandMode : int32_t {
@@ -83,6 +88,8 @@ struct FinalDev {
   int32_t n_qubits;
   int32_t alg;
   int32_t nblocks;               // blocks of the open-tensor pass
+  int32_t open_f32;              // the open tensor is complex64 (FP32 planes), else complex128
+  int32_t pad;
 };
 
 // One network of a persistent-kernel launch (one thread block each). Byte offsets are into the
@@ -142,9 +149,9 @@ struct QPhase {
   const void* desc;    // steps / perms / leaves / final record (device)
   const void* gemm;    // QK_GEMM: the GEMM's parameter block (device, 64-byte aligned)
   // per kind: LEAVES p0 = packed inputs; SPLITK / DOT p0 = split partials; SPLITK_DONE p0 =
-  // partials, p1 = scalar slots; SPLIT_SUM p0 = workspace, p1 = result; OPEN p0 = scalar slots,
-  // p1 = traces, p2 = block partials; FINAL p0 = scalar slots, p1 = result, p2 = block partials,
-  // p3 = optional copy of (S, F, 1 - F)
+  // partials, p1 = scalar slots; SPLIT_SUM p0 = workspace, p1 = result (both FP32, cast to this
+  // field's type); OPEN p0 = scalar slots, p1 = traces, p2 = block partials; FINAL p0 = scalar
+  // slots, p1 = result, p2 = block partials, p3 = optional copy of (S, F, 1 - F)
   double* p0;
   double* p1;
   double* p2;

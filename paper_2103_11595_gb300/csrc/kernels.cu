@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kBodyThreads) k_splitk_done(const StepDev* __r
 }
 
 // 4 blocks per SM (64 registers): the gather is bound by memory latency; measured on GB300 with
-// 98 registers (2 blocks per SM) a large gather reached 1.2-1.3 TB/s
+// 98 registers (2 blocks per SM) a large gather reached 1.2-1.3 TB/s. S: staging type (FP64 for
+// the FP64 operand mode, FP32 otherwise).
 template <typename S>
 __global__ void __launch_bounds__(kBodyThreads, 4) k_perm(const PermDev* __restrict__ perms,
                                                        const double* __restrict__ arena, char* __restrict__ base) {
@@ -101,11 +102,11 @@ __global__ void k_convert_check(const float* __restrict__ in, double* __restrict
 
 // ------------------------------------------------------------------ CUDA-core GEMM
 
-// C[M][N] (row-major, ldc = N, FP64) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous;
-// operands and accumulation in T (FP32 or FP64).
+// C[M][N] (row-major, ldc = N) = A[M][K] . B[N][K]^T with A and B row-major, K contiguous;
+// operands, accumulation and result in T (FP32 or FP64).
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __restrict__ A, const T* __restrict__ B,
-                                                                     double* __restrict__ C, int64_t M, int64_t N,
+                                                                     T* __restrict__ C, int64_t M, int64_t N,
                                                                      int64_t K) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ T As[BK][BM + 4];
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_simt(const T* __
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t gn = n0 + tc * TN + j;
-      if (gn < N) C[gm * N + gn] = static_cast<double>(acc[i][j]);
+      if (gn < N) C[gm * N + gn] = acc[i][j];
     }
   }
 }
@@ -337,31 +338,24 @@ static size_t table_bytes(const BitMap* const* maps, int n) {
   return b;
 }
 
-cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, bool f64, cudaStream_t s) {
+cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  if (f64) k_leaf<double><<<n, kBodyThreads, 0, s>>>(d_leaves, d_in, static_cast<double*>(arena));
-  else k_leaf<float><<<n, kBodyThreads, 0, s>>>(d_leaves, d_in, static_cast<float*>(arena));
+  k_leaf<double><<<n, kBodyThreads, 0, s>>>(d_leaves, d_in, static_cast<double*>(arena));
   return cudaGetLastError();
 }
 
-cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena, bool f64,
+cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena,
                          cudaStream_t s) {
   if (nsteps == 0) return cudaSuccess;
-  if (f64) k_small<double, double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, total_blocks, static_cast<double*>(arena));
-  else k_small<float, float><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, total_blocks, static_cast<float*>(arena));
+  k_small<double, double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, total_blocks, static_cast<double*>(arena));
   return cudaGetLastError();
 }
 
 cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena,
-                          double2* partial, double2* scalars, bool f64, cudaStream_t s) {
+                          double2* partial, double2* scalars, cudaStream_t s) {
   if (nsteps == 0) return cudaSuccess;
-  if (f64) {
-    k_splitk<double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const double*>(arena), partial);
-    k_splitk_done<double><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<double*>(arena), scalars);
-  } else {
-    k_splitk<float><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const float*>(arena), partial);
-    k_splitk_done<float><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<float*>(arena), scalars);
-  }
+  k_splitk<double><<<total_blocks, 256, smem, s>>>(d_steps, nsteps, static_cast<const double*>(arena), partial);
+  k_splitk_done<double><<<nsteps, 256, 0, s>>>(d_steps, nsteps, partial, static_cast<double*>(arena), scalars);
   return cudaGetLastError();
 }
 
@@ -394,8 +388,8 @@ cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t sm
                         bool op_f64, cudaStream_t s) {
   if (nperm == 0) return cudaSuccess;
   dim3 grid(grid_x, nperm);
-  // tensors are FP64 in every mode; the operand format (FP64 or a reduced one) is in each PermDev,
-  // and every PermDev of one launch has the same one
+  // the operand format (FP64 or a reduced one) is in each PermDev, and every PermDev of one launch
+  // has the same one; each source is complex128, or complex64 when a reduced-precision GEMM made it
   if (op_f64)
     k_perm<double><<<grid, 256, smem, s>>>(d_perms, static_cast<const double*>(arena), static_cast<char*>(base));
   else
@@ -412,17 +406,15 @@ cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, i
   } else {
     const unsigned grid = unsigned(((N + 63) / 64) * ((M + 127) / 128));
     k_gemm_simt<float, 128, 64, 8, 8, 4><<<grid, 256, 0, s>>>(static_cast<const float*>(A), static_cast<const float*>(B),
-                                                             static_cast<double*>(C), M, N, K);
+                                                             static_cast<float*>(C), M, N, K);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
-                         const double2* scalars, double* traces, double* partial, double* result, bool f64,
-                         cudaStream_t s) {
+                         const double2* scalars, double* traces, double* partial, double* result, cudaStream_t s) {
   const size_t smem = size_t(open_bits_nchunks) * 256 * sizeof(int64_t);
-  if (f64) k_open<double><<<nblocks, 256, smem, s>>>(d_fd, static_cast<const double*>(arena), scalars, traces, partial);
-  else k_open<float><<<nblocks, 256, smem, s>>>(d_fd, static_cast<const float*>(arena), scalars, traces, partial);
+  k_open<double><<<nblocks, 256, smem, s>>>(d_fd, static_cast<const double*>(arena), scalars, traces, partial);
   k_final<<<1, 32, 0, s>>>(d_fd, scalars, partial, result);
   return cudaGetLastError();
 }
@@ -440,15 +432,12 @@ size_t perm_table_bytes(const PermDev& p) {
 cudaError_t set_kernel_smem_limits() {
   const int big = 96 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_small<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_small<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_splitk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dot<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_perm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_open<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;
 }
 

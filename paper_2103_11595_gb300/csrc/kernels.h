@@ -15,11 +15,10 @@ cudaError_t static_arena_address(int device, void** ptr);
 size_t step_table_bytes(const StepDev& st);
 size_t perm_table_bytes(const PermDev& p);
 
-cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, bool f64, cudaStream_t s);
-cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena, bool f64,
-                         cudaStream_t s);
+cudaError_t launch_leaves(const LeafDev* d_leaves, int n, const double* d_in, void* arena, cudaStream_t s);
+cudaError_t launch_small(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena, cudaStream_t s);
 cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, void* arena,
-                          double2* partial, double2* scalars, bool f64, cudaStream_t s);
+                          double2* partial, double2* scalars, cudaStream_t s);
 // op_f64: the operands are FP64 (staged in FP64); otherwise every format is staged in FP32.
 cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
                         bool op_f64, cudaStream_t s);
@@ -32,8 +31,7 @@ cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, siz
 cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool f64,
                              cudaStream_t s);
 cudaError_t launch_final(const FinalDev* d_fd, int open_bits_nchunks, int nblocks, const void* arena,
-                         const double2* scalars, double* traces, double* partial, double* result, bool f64,
-                         cudaStream_t s);
+                         const double2* scalars, double* traces, double* partial, double* result, cudaStream_t s);
 // Persistent kernel: one thread block per network runs that network's whole program (leaves,
 // all steps level by level, the FP64 trace and F) -- n_jobs networks in one launch. `smem`:
 // dynamic shared memory per block (the largest work region among the jobs with job.smem = 1).
@@ -58,13 +56,13 @@ struct TcPrepared {
   unsigned grid = 0;
   size_t smem = 0;
   int ksplit = 1;
-  double* ws = nullptr;
-  double* C = nullptr;
+  float* ws = nullptr;
+  float* C = nullptr;
   int64_t n = 0;  // M * N
   bool ready = false;
 };
 cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, const int64_t* b_off, int terms,
-                            double* C, int64_t M, int64_t N, int64_t K, int kind, double* ws, int ksplit,
+                            float* C, int64_t M, int64_t N, int64_t K, int kind, float* ws, int ksplit,
                             int* d_status, unsigned long long wait_ns, int stall_loads);
 cudaError_t tc_gemm_run(const TcPrepared& t, cudaStream_t s);
 // Bound of every device-side wait in the GEMM and the step interpreter (nanoseconds).
@@ -85,13 +83,13 @@ cudaError_t launch_queue(const QPhase* d_phases, int nphases, const QTask* d_tas
 // its tile width, operand kind and work-item count.
 size_t queue_gemm_params_bytes();
 cudaError_t queue_gemm_params(const TcPrepared& t, void* out, int* bn, int* bf16, int* nwork);
-cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s);
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, float* C, int64_t M,
+                           int64_t N, int64_t K, int kind, float* ws, int ksplit, int* d_status, cudaStream_t s);
 // Same with an explicit bound on every device-side wait and a test hook: stall_loads = 1 makes the
 // producer issue no loads, so the MMA and epilogue waits expire and the kernel reports a status
 // code and returns.
-cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
+cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, float* C, int64_t M,
+                              int64_t N, int64_t K, int kind, float* ws, int ksplit, int* d_status, cudaStream_t s,
                               unsigned long long wait_ns, int stall_loads);
 
 }  // namespace ajf

@@ -100,7 +100,8 @@ void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& 
 
 // Estimated device time of one pairwise step with operand ranks ra, rb and result rank rc (labels
 // of dimension 2; runion = |a u b|, so K = 2^(ra + rb - runion)), following the lowering's choice
-// of kernel class (program.cpp) and GB300's rates: every tensor is complex FP64 in HBM, the
+// of kernel class (program.cpp) and GB300's rates: tensors are complex128 in HBM in the FP64 mode
+// and complex64 in the reduced-precision modes (p.elem_bytes per complex element), the
 // gate-absorption, split-K and trace kernels compute in FP64 on the CUDA cores, GEMM-class steps
 // gather both operands into the precision's operand terms and run one real GEMM of
 // 2M x N x 2K on the tensor cores (or on the CUDA cores in the FP64 / FP32 modes), and every
@@ -114,7 +115,7 @@ double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
   constexpr double kSMs = 152;
   const int rk = ra + rb - runion;
   const double flops = 8.0 * std::ldexp(1.0, runion);  // 8 per complex multiply-add
-  const double io = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * 16.0;
+  const double io = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb) + std::ldexp(1.0, rc)) * p.elem_bytes;
   if (rc == 0) return std::max(io / kBw, flops / (p.precision == AJF_PREC_F64 ? kFp64 : kFp32)) + 3e-6;
   const int ma = ra - rk, nb = rb - rk;
   const bool gemm = ma >= 4 && nb >= 4 && rk >= 3 && ma + nb + rk >= 18;
@@ -142,8 +143,8 @@ double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
     tn = Nt >= 128 ? 128 : Nt;
   }
   const double operands = terms * eb * (Mt * Kt + Nt * Kt);
-  const double gather = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb)) * 16.0 + operands;
-  const double out = Mt * Nt * 8.0;
+  const double gather = (std::ldexp(1.0, ra) + std::ldexp(1.0, rb)) * p.elem_bytes + operands;
+  const double out = Mt * Nt * p.elem_bytes / 2;  // real planes of the complex result
   double tiles = std::ceil(Mt / tm) * std::ceil(Nt / tn);
   if (tc) tiles *= std::max(1.0, std::min(std::ceil(kSMs / tiles) * 2.0, Kt * eb / 1024.0));  // K splits
   const double eff = std::min(1.0, tiles / kSMs);

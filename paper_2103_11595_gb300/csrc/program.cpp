@@ -129,7 +129,12 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   P.persistent = persistent;
   P.alg = net.alg;
   P.precision = precision;
-  P.f64 = true;  // tensors are FP64 in HBM in every mode; the precision mode sets the GEMM operands
+  // tensors in HBM: complex128 (two FP64 planes), except the products of reduced-precision GEMMs,
+  // which are complex64 (two FP32 planes). Such a GEMM promotes every result to one FP32 register
+  // sum (or sums its K splits in FP32), and the gathers of the next GEMMs split FP32 values, so
+  // nothing is lost; the small steps keep FP64 results, whose rounding would otherwise add up
+  // over the hundreds of gate absorptions of a network. Traces, sum |t|^2, F and 1 - F are FP64
+  // in every mode.
   P.elem = 8;
   const int L = static_cast<int>(net.leaf_labels.size());
   const int S = static_cast<int>(path.steps.size());
@@ -204,6 +209,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     labels[L + s] = out;
     if (static_cast<int>(out.size()) != static_cast<int>(st.out.size()))
       throw std::runtime_error("internal: step output rank mismatch");
+    // (a rough traffic figure: complex128 throughout)
     const double bytes = (std::ldexp(1.0, static_cast<int>(la.size())) + std::ldexp(1.0, static_cast<int>(lb.size())) +
                           std::ldexp(1.0, rc)) * 2.0 * P.elem;
     P.flops += 8.0 * mnk;
@@ -235,7 +241,9 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
   // ---- arena: work region offsets by first fit in launch order
   FirstFit ff;
   std::vector<size_t> toff(L + S, 0);
-  auto tensor_bytes = [&](int id) { return 2 * (size_t(1) << labels[id].size()) * P.elem; };
+  std::vector<char> t32(L + S, 0);  // complex64 tensors: the products of reduced-precision GEMMs
+  auto elem = [&](int id) -> size_t { return t32[id] ? 4 : 8; };
+  auto tensor_bytes = [&](int id) { return 2 * (size_t(1) << labels[id].size()) * elem(id); };
   for (int i = 0; i < L; ++i) toff[i] = ff.alloc(tensor_bytes(i));
   auto release_dead = [&](int upto_pos, const std::vector<int>& ids) {
     for (int id : ids)
@@ -282,9 +290,11 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
         std::memset(&d, 0, sizeof(d));
         const auto& la = labels[I.a];
         const auto& lb = labels[I.b];
-        d.a = static_cast<int64_t>(toff[I.a] / P.elem);
-        d.b = static_cast<int64_t>(toff[I.b] / P.elem);
-        d.c = static_cast<int64_t>(toff[c] / P.elem);
+        d.a = static_cast<int64_t>(toff[I.a] / elem(I.a));
+        d.b = static_cast<int64_t>(toff[I.b] / elem(I.b));
+        d.c = static_cast<int64_t>(toff[c] / elem(c));
+        d.fa = t32[I.a];
+        d.fb = t32[I.b];
         d.pa = int64_t(1) << la.size();
         d.pb = int64_t(1) << lb.size();
         d.pc = int64_t(1) << labels[c].size();
@@ -345,8 +355,9 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
         }
         smem = std::max(smem, cls == C_DOT ? dot_smem_bytes(d) : step_table_bytes(d));
         ln.flops += 8.0 * std::ldexp(1.0, d.rc + d.rk);
-        ln.bytes += (std::ldexp(1.0, static_cast<int>(la.size())) + std::ldexp(1.0, static_cast<int>(lb.size())) +
-                     (d.rc ? std::ldexp(1.0, d.rc) : 0.0)) * 2.0 * P.elem;
+        ln.bytes += (std::ldexp(1.0, static_cast<int>(la.size())) * elem(I.a) +
+                     std::ldexp(1.0, static_cast<int>(lb.size())) * elem(I.b) +
+                     (d.rc ? std::ldexp(1.0, d.rc) * elem(c) : 0.0)) * 2.0;
         P.steps.push_back(d);
         consumed.push_back(I.a);
         consumed.push_back(I.b);
@@ -388,7 +399,8 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       PermDev px, py;
       std::memset(&px, 0, sizeof(px));
       std::memset(&py, 0, sizeof(py));
-      px.src = static_cast<int64_t>(toff[I.a] / P.elem);
+      px.src = static_cast<int64_t>(toff[I.a] / elem(I.a));
+      px.src_f32 = t32[I.a];
       px.plane = int64_t(1) << lx.size();
       px.rows = make_map(xf, lx);
       px.cols = make_map(I.shared, lx);
@@ -397,7 +409,8 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
       px.embed = 1;
       px.rows_fast = contains(xf, lx[0]) ? 1 : 0;
       px.mode = gmode;
-      py.src = static_cast<int64_t>(toff[I.b] / P.elem);
+      py.src = static_cast<int64_t>(toff[I.b] / elem(I.b));
+      py.src_f32 = t32[I.b];
       py.plane = int64_t(1) << ly.size();
       py.rows = make_map(yf, ly);
       py.cols = make_map(I.shared, ly);
@@ -423,16 +436,18 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
                                               int64_t(1) << std::max(0, I.n + I.k - tile_bits));
       lp.blocks = static_cast<int>(std::min<int64_t>(std::max<int64_t>(tiles, 1), 4 * 152));
       lp.smem = std::max(perm_table_bytes(px), perm_table_bytes(py));
-      // gather traffic: both complex FP64 operands read once, every operand term written once
-      lp.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) + std::ldexp(1.0, static_cast<int>(ly.size()))) * 16.0 +
+      // gather traffic: both complex operands read once, every operand term written once
+      lp.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) * elem(I.a) +
+                  std::ldexp(1.0, static_cast<int>(ly.size())) * elem(I.b)) * 2.0 +
                  static_cast<double>(gterms) * static_cast<double>(xbytes + ybytes);
       P.perms.push_back(px);
       P.perms.push_back(py);
       P.launches.push_back(lp);
       release_dead(exec_pos[s], {I.a, I.b});
+      t32[c] = op_f64 ? 0 : 1;  // reduced-precision GEMMs write complex64
       toff[c] = ff.alloc(tensor_bytes(c));
       const int ksplit = use_tc ? tc_gemm_splits(Mt, Nt, Kt, tc_kind) : 1;
-      const size_t ws_bytes = ksplit > 1 ? size_t(ksplit) * size_t(Mt) * size_t(Nt) * 8 : 0;
+      const size_t ws_bytes = ksplit > 1 ? size_t(ksplit) * size_t(Mt) * size_t(Nt) * 4 : 0;  // FP32 partials
       const size_t ws = ws_bytes ? ff.alloc(ws_bytes) : 0;
       Launch lg;
       lg.ksplit = ksplit;
@@ -462,8 +477,9 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
         lg.npass = 1;
       }
       lg.flops = 8.0 * std::ldexp(1.0, I.m + I.n + I.k);
-      lg.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) + std::ldexp(1.0, static_cast<int>(ly.size())) +
-                  std::ldexp(1.0, static_cast<int>(labels[c].size()))) * 2.0 * P.elem;
+      lg.bytes = (std::ldexp(1.0, static_cast<int>(lx.size())) * elem(I.a) +
+                  std::ldexp(1.0, static_cast<int>(ly.size())) * elem(I.b) +
+                  std::ldexp(1.0, static_cast<int>(labels[c].size())) * elem(c)) * 2.0;
       gemm_launches.push_back(static_cast<int>(P.launches.size()));
       P.launches.push_back(lg);
       for (int t = 0; t < gterms; ++t) ff.release(xo[t], xbytes);
@@ -489,7 +505,8 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     if (!labels[id].empty()) open_id = id;
   f.open_bits = static_cast<int32_t>(net.open_labels.size());
   if (open_id >= 0) {
-    f.open_off = static_cast<int64_t>(toff[open_id] / P.elem);
+    f.open_off = static_cast<int64_t>(toff[open_id] / elem(open_id));
+    f.open_f32 = t32[open_id];
     f.open_plane = int64_t(1) << labels[open_id].size();
     f.open_map = make_map(net.open_labels, labels[open_id]);
     if (labels[open_id].size() != net.open_labels.size()) throw std::runtime_error("internal: open tensor rank");
@@ -553,13 +570,14 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     d.fix_val = 0;
     P.leaves.push_back(d);
   }
+  const int64_t wel32 = static_cast<int64_t>(P.off_work / 4);  // element offsets of complex64 tensors
   for (auto& d : P.steps) {
-    d.a += wel;
-    d.b += wel;
+    d.a += d.fa ? wel32 : wel;
+    d.b += d.fb ? wel32 : wel;
     d.c += wel;
   }
   for (auto& p : P.perms) {
-    p.src += wel;
+    p.src += p.src_f32 ? wel32 : wel;
     for (int t = 0; t < 3; ++t) p.dst[t] += static_cast<int64_t>(P.off_work);
   }
   for (int li : gemm_launches) {
@@ -571,7 +589,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
     g.c_off += static_cast<int64_t>(P.off_work);
     g.ws_off += static_cast<int64_t>(P.off_work);
   }
-  if (f.open_off >= 0) f.open_off += wel;
+  if (f.open_off >= 0) f.open_off += f.open_f32 ? wel32 : wel;
   return P;
 }
 
@@ -621,8 +639,10 @@ std::string check_program(const Program& P) {
   const size_t work_lo = P.off_work, work_hi = P.off_work + P.work_bytes;
   if (P.arena_bytes != work_hi) return "arena size differs from the end of its work region";
   const int64_t inputs_complex = static_cast<int64_t>(P.input_bytes / 16);
-  auto tensor = [&](int64_t off_el, int64_t plane) {
-    return Span{static_cast<size_t>(off_el) * P.elem, static_cast<size_t>(off_el + 2 * plane) * P.elem};
+  // a tensor's bytes: element offset and plane in units of its own type (complex64: FP32 planes)
+  auto tensor = [&](int64_t off_el, int64_t plane, bool f32 = false) {
+    const size_t e = f32 ? 4 : 8;
+    return Span{static_cast<size_t>(off_el) * e, static_cast<size_t>(off_el + 2 * plane) * e};
   };
   auto in_work = [&](const Span& s) { return s.lo >= work_lo && s.hi <= work_hi && s.lo < s.hi; };
 
@@ -686,7 +706,7 @@ std::string check_program(const Program& P) {
         // every operand bit is an output or a contracted bit: otherwise elements would be skipped
         if (ua != (ba == 64 ? ~0ull : (uint64_t(1) << ba) - 1) || ub != (bb == 64 ? ~0ull : (uint64_t(1) << bb) - 1))
           return ws + ": an operand bit is not addressed";
-        const Span sa = tensor(d.a, d.pa), sb = tensor(d.b, d.pb);
+        const Span sa = tensor(d.a, d.pa, d.fa), sb = tensor(d.b, d.pb, d.fb);
         if (!in_work(sa) || !in_work(sb)) return ws + ": an operand lies outside the work region";
         R.push_back(sa);
         R.push_back(sb);
@@ -731,7 +751,7 @@ std::string check_program(const Program& P) {
         if (!add_positions(g.rows, bp, used) || !add_positions(g.cols, bp, used))
           return ws + ": source addresses repeat or overflow";
         if (used != (uint64_t(1) << bp) - 1) return ws + ": a source bit is not addressed";
-        const Span src = tensor(g.src, g.plane);
+        const Span src = tensor(g.src, g.plane, g.src_f32);
         if (!in_work(src)) return ws + ": source outside the work region";
         R.push_back(src);
         const size_t rows = size_t(1) << (g.rbits + (g.embed ? 1 : 0)), cols = size_t(1) << (g.kbits + 1);
@@ -776,12 +796,14 @@ std::string check_program(const Program& P) {
         R.push_back(a);
         R.push_back(b);
       }
-      const Span c{static_cast<size_t>(ln.c_off), static_cast<size_t>(ln.c_off) + size_t(ln.M) * size_t(ln.N) * 8};
+      // the result: complex64 from a reduced-precision GEMM, complex128 from the FP64 one
+      const size_t ce = ln.op_f64 ? 8 : 4;
+      const Span c{static_cast<size_t>(ln.c_off), static_cast<size_t>(ln.c_off) + size_t(ln.M) * size_t(ln.N) * ce};
       if (!in_work(c)) return who + ": result outside the work region";
       W.push_back(c);
       if (ln.ksplit > 1) {
         const Span w{static_cast<size_t>(ln.ws_off),
-                     static_cast<size_t>(ln.ws_off) + size_t(ln.ksplit) * size_t(ln.M) * size_t(ln.N) * 8};
+                     static_cast<size_t>(ln.ws_off) + size_t(ln.ksplit) * size_t(ln.M) * size_t(ln.N) * 4};
         if (!in_work(w)) return who + ": K-split workspace outside the work region";
         W.push_back(w);  // written by the GEMM and read back by the split sum of the same launch
       }
@@ -802,7 +824,7 @@ std::string check_program(const Program& P) {
     if (bo < 0 || f.open_map.nbits != f.open_bits || bo != f.open_bits || !add_positions(f.open_map, bo, used) ||
         used != (uint64_t(1) << bo) - 1)
       return "final pass: open-tensor addresses";
-    const Span so = tensor(f.open_off, f.open_plane);
+    const Span so = tensor(f.open_off, f.open_plane, f.open_f32 != 0);
     if (!in_work(so)) return "final pass: open tensor outside the work region";
     unit_reads[uf].push_back(so);
   } else if (f.open_bits != 0) {

@@ -22,8 +22,8 @@ struct Launch {
   int32_t tc_kind = 0;           // 0 tf32, 1 bf16
   int32_t op_f64 = 1;            // CUDA-core GEMM: FP64 (1) or FP32 (0) operands
   int64_t c_off = 0;             // byte offset of C
-  int32_t ksplit = 1;            // tensor-core GEMM: K splits (> 1: FP64 partials in the workspace)
-  int64_t ws_off = 0;            // byte offset of the split workspace (ksplit * M * N doubles)
+  int32_t ksplit = 1;            // tensor-core GEMM: K splits (> 1: FP32 partials in the workspace)
+  int64_t ws_off = 0;            // byte offset of the split workspace (ksplit * M * N floats)
   int64_t M = 0, N = 0, K = 0;
   double flops = 0, bytes = 0;   // algorithmic work of the complex step this launch belongs to
 };
@@ -31,8 +31,7 @@ struct Launch {
 struct Program {
   int alg = 0;
   int precision = AJF_PREC_F64;
-  bool f64 = true;
-  size_t elem = 8;               // bytes per real element in the arena
+  size_t elem = 8;               // bytes per real element of a complex128 tensor (complex64 ones: 4)
   std::vector<LeafDev> leaves;
   std::vector<StepDev> steps;
   std::vector<PermDev> perms;

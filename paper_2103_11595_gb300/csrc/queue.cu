@@ -40,7 +40,7 @@ constexpr int kQTmemStride = 256;                          // two partials of up
 constexpr uint32_t kQTmemCols = kQBufs * kQTmemStride;
 constexpr size_t kQScratch = size_t(kQSlots) * kQSlotBytes;  // 192 KiB
 constexpr size_t kQArrays = 96 * 1024;                     // body arrays after the offset tables
-constexpr size_t kQSmem = kQScratch + kTcControlBytes + kTcStageBytes + 1024 /* alignment */;
+constexpr size_t kQSmem = kQScratch + kTcControlBytes + 1024 /* alignment */;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -97,7 +97,8 @@ __device__ __noinline__ void q_perm(const QPhase& ph, int v, uint8_t* smem) {
                              *reinterpret_cast<PermSmem<float>*>(smem + kQArrays));
 }
 __device__ __noinline__ void q_split_sum(const QPhase& ph, int v) {
-  split_sum_body(ph.p0, ph.ksplit, ph.n, ph.p1, v, ph.nblocks);
+  split_sum_body(reinterpret_cast<const float*>(ph.p0), ph.ksplit, ph.n, reinterpret_cast<float*>(ph.p1), v,
+                 ph.nblocks);
 }
 __device__ __noinline__ void q_open(const QPhase& ph, int v, uint8_t* smem) {
   open_body<double, SyncBody>(static_cast<const FinalDev*>(ph.desc), reinterpret_cast<const double*>(ph.base),

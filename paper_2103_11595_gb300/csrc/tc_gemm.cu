@@ -58,6 +58,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "bodies.cuh"
 #include "fp_bits.h"
 #include "kernels.h"
 #include "tc_gemm_dev.cuh"
@@ -159,7 +160,7 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   if (p.slots < p.terms) return cudaErrorInvalidValue;
   p.bufs = 256 / BN > kMaxBufs ? kMaxBufs : 256 / BN;  // each buffer: 2 partials x BN TMEM columns
   p.tmem_stride = 2 * BN;
-  const size_t smem = size_t(p.slots) * p.slot_bytes + kTcControlBytes + kTcStageBytes + 1024 /* alignment */;
+  const size_t smem = size_t(p.slots) * p.slot_bytes + kTcControlBytes + 1024 /* alignment */;
   const int64_t mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt;
   if (mt > 0x7FFFFFFF || nt > 0x7FFFFFFF) return cudaErrorInvalidValue;
@@ -228,20 +229,16 @@ int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind) {
 
 namespace {
 
-// C[i] = sum over splits s (in order) of W[s][i]
-__global__ void __launch_bounds__(256) k_split_sum(const double* __restrict__ W, int ksplit, int64_t n,
-                                                   double* __restrict__ C) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    double v = 0;
-    for (int s = 0; s < ksplit; ++s) v += W[s * n + i];
-    C[i] = v;
-  }
+// C[i] = sum over splits s (in order) of W[s][i] (compensated FP32 sum)
+__global__ void __launch_bounds__(kBodyThreads) k_split_sum(const float* __restrict__ W, int ksplit, int64_t n,
+                                                            float* __restrict__ C) {
+  split_sum_body(W, ksplit, n, C, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
 }
 
 }  // namespace
 
 cudaError_t tc_gemm_prepare(TcPrepared* t, char* base, const int64_t* a_off, const int64_t* b_off, int terms,
-                            double* C, int64_t M, int64_t N, int64_t K, int kind, double* ws, int ksplit,
+                            float* C, int64_t M, int64_t N, int64_t K, int kind, float* ws, int ksplit,
                             int* d_status, unsigned long long wait_ns, int stall_loads) {
   static_assert(sizeof(TcParams) <= sizeof(t->params), "kernel parameters exceed the prepared-launch buffer");
   t->ready = false;
@@ -303,17 +300,17 @@ cudaError_t tc_gemm_run(const TcPrepared& t, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || t.ksplit == 1) return e;
   const int64_t blocks = (t.n + 255) / 256 < 4096 ? (t.n + 255) / 256 : 4096;
-  k_split_sum<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t.ws, t.ksplit, t.n, t.C);
+  k_split_sum<<<static_cast<unsigned>(blocks), kBodyThreads, 0, s>>>(t.ws, t.ksplit, t.n, t.C);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                           int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s) {
+cudaError_t launch_gemm_tc(char* base, const int64_t* a_off, const int64_t* b_off, int terms, float* C, int64_t M,
+                           int64_t N, int64_t K, int kind, float* ws, int ksplit, int* d_status, cudaStream_t s) {
   return launch_gemm_tc_ex(base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, s, kWaitNs, 0);
 }
 
-cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, double* C, int64_t M,
-                              int64_t N, int64_t K, int kind, double* ws, int ksplit, int* d_status, cudaStream_t s,
+cudaError_t launch_gemm_tc_ex(char* base, const int64_t* a_off, const int64_t* b_off, int terms, float* C, int64_t M,
+                              int64_t N, int64_t K, int kind, float* ws, int ksplit, int* d_status, cudaStream_t s,
                               unsigned long long wait_ns, int stall_loads) {
   TcPrepared t;
   cudaError_t e = tc_gemm_prepare(&t, base, a_off, b_off, terms, C, M, N, K, kind, ws, ksplit, d_status, wait_ns,

@@ -36,7 +36,7 @@ constexpr unsigned long long kWaitNs = kTcWaitNs;
 struct TcParams {
   CUtensorMap amap[kMaxTerms];
   CUtensorMap bmap[kMaxTerms];
-  double* C;
+  float* C;                          // the product (FP32: each value is one promoted register sum)
   const float* sa;                   // scaled fp16 operands: A's scales [K block][M], B's [K block][N]
   const float* sb;
   int* status;
@@ -48,7 +48,7 @@ struct TcParams {
   int64_t tiles;
   int32_t tmem_stride;               // TMEM columns per partial buffer (two partials of BN columns each)
   int32_t pad0;
-  double* ws;                        // split partials [ksplit][M][N] (ksplit > 1)
+  float* ws;                         // split partials [ksplit][M][N] (ksplit > 1)
   uint32_t idesc;
   uint32_t slot_bytes;
   unsigned long long wait_ns;        // bound of every wait
@@ -171,19 +171,24 @@ struct TcShared {
   uint32_t sfull0;                   // scaled fp16: the scales of TMEM buffer b have arrived
   float* scales;                     // scaled fp16: per TMEM buffer, 128 row scales then 128 column scales
   volatile int* abort_flag;
-  float* stage;                      // epilogue store staging: per epilogue warp, 32 rows x kStageCols
+  float* stage;                      // epilogue store staging (see kStageCols)
   uint32_t tmem;
 };
 constexpr int kScaleFloats = 256;    // floats of scales per TMEM buffer
-// The epilogue writes its FP64 tile through shared memory, kStageCols columns at a time: a thread
-// owns one row, so storing straight from registers would touch 32 rows (32 cache lines) per warp
-// store. Staged (as FP32; converted to FP64 after the read-back), each warp store covers 4 rows x
-// 128 contiguous bytes, whole L2 lines: on GB300 a 128 x 128 FP64 tile pattern written in 64-byte
-// row pieces reached 3.4 TB/s, in 128-byte pieces 5.4 TB/s. The 16-byte chunks of a staged row are
-// XOR-swizzled by (row / 2) % 4, so the row-wise writes (8 rows per phase) and the read-back (two
-// rows per half-warp) are both free of bank conflicts.
-constexpr int kStageCols = 16;
-constexpr uint32_t kTcStageBytes = kEpiWarps * 32 * kStageCols * 4;
+// The epilogue writes its FP32 tile through shared memory, kStageCols(kind) columns at a time: a
+// thread owns one row, so storing straight from registers would touch 32 rows (32 cache lines) per
+// warp store. Staged, each warp store covers whole row segments: 4 rows x 128 bytes (32 columns)
+// for the TF32 and bf16 kinds, 8 rows x 64 bytes (16 columns) for the scaled fp16 kind, whose
+// scale buffers take part of the space. (On GB300 a tile pattern written in 64-byte row pieces
+// reached 3.4 TB/s, in 128-byte pieces 5.4 TB/s.) The 16-byte chunks of a staged row are
+// XOR-swizzled so that the row-wise writes (8 rows per phase) and the read-back (one or two rows
+// per 8 lanes) are both free of bank conflicts. The staging area starts at the scale buffers
+// (unused by the TF32 and bf16 kinds) and holds kEpiWarps x 32 rows x 32 floats; the scaled fp16
+// kind stages after its scale buffers, 16 columns wide (as does every kind when a thread holds
+// only 16 columns, BN = 32).
+__host__ __device__ constexpr int stage_cols(int kind) { return kind == 2 ? 16 : 32; }
+constexpr uint32_t kTcStageBytes = kEpiWarps * 32 * 32 * 4;
+static_assert(kMaxBufs * kScaleFloats * 4 + kEpiWarps * 32 * 16 * 4 <= kTcStageBytes, "staging layout");
 
 // Ring positions of the three roles; they continue from one call of tc_gemm_items to the next
 // (the barrier phases must), so a caller keeps one TcRing per thread for the block's lifetime.
@@ -202,9 +207,10 @@ struct TcRing {
 };
 
 // Layout of the pipeline's control region (kTcControlBytes from `bars`, 16-byte aligned): the
-// barrier arrays, the TMEM address slot, the abort flag, then the scale buffers of the scaled fp16
-// kind (kMaxBufs x kScaleFloats floats); the epilogue's staging buffers (kTcStageBytes) follow it.
-constexpr uint32_t kTcControlBytes = 256 + kMaxBufs * kScaleFloats * 4;
+// barrier arrays, the TMEM address slot and the abort flag in the first 256 bytes, then
+// kTcStageBytes shared by the scale buffers of the scaled fp16 kind (kMaxBufs x kScaleFloats
+// floats) and the epilogue's staging buffers.
+constexpr uint32_t kTcControlBytes = 256 + kTcStageBytes;
 __device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, TcShared& sh) {
   sh.slots = slots;
   sh.full0 = smem_u32(bars);
@@ -215,7 +221,7 @@ __device__ __forceinline__ uint32_t* tc_layout(uint8_t* slots, uint8_t* bars, Tc
   sh.sfull0 = sh.drain0 + 8;              // scales of buffer b arrived
   sh.abort_flag = reinterpret_cast<volatile int*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 12);
   sh.scales = reinterpret_cast<float*>(bars + 256);
-  sh.stage = reinterpret_cast<float*>(bars + kTcControlBytes);
+  sh.stage = reinterpret_cast<float*>(bars + 256);
   return reinterpret_cast<uint32_t*>(bars + 16 * kMaxSlots + 24 * kMaxBufs + 8);  // TMEM address slot
 }
 
@@ -424,7 +430,7 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
       // rows/columns beyond M, N were zero-filled by TMA and are not stored; M and N are powers of
       // two >= 32 and >= 16, so a warp's 32 rows and COLS columns are all inside or all outside
       const bool mine = row < p.M && col0 < p.N;
-      double* dbase = p.ksplit > 1 ? p.ws + static_cast<int64_t>(wi / tiles) * p.M * p.N : p.C;
+      float* dbase = p.ksplit > 1 ? p.ws + static_cast<int64_t>(wi / tiles) * p.M * p.N : p.C;
 #pragma unroll
       for (int j = 0; j < COLS; ++j) acc[j] = 0.0f;
       for (int kb = kb0; kb < kb1; ++kb) {
@@ -491,29 +497,34 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
         if (lane == 0) mbar_arrive(sh.acce0 + 8 * b);
       }
       if (!ok) break;
-      // the MMA warp is already filling the next buffers while this tile is written; FP32 -> FP64
-      // is exact and runs on the integer pipe (GB300's FP64 rate would make a hardware conversion
-      // per element a visible cost of the store). `mine` is the same for the whole warp.
+      // the MMA warp is already filling the next buffers while this tile is written. `mine` is the
+      // same for the whole warp.
       if (mine) {
-        float* st = sh.stage + (warp - kEpiWarp0) * 32 * kStageCols;
-        float4* srow = reinterpret_cast<float4*>(st + lane * kStageCols);
-        const int wsw = (lane >> 1) & 3;
-        // read-back: lane l carries the float pair l % 8 (columns 2 (l % 8), + 1) of rows 4 i + l / 8
-        const int rr = lane >> 3, pr = lane & 7;
-        double* drow = dbase + (row - lane + rr) * p.N + col0 + 2 * pr;
+        constexpr int SC = stage_cols(kKind) < COLS ? stage_cols(kKind) : COLS;  // staged columns: 32 or 16
+        constexpr int CH16 = SC / 4;                      // 16-byte chunks per staged row: 8 or 4
+        constexpr int RPI = 32 / CH16;                    // rows per warp store: 4 or 8
+        float* st = sh.stage + (kKind == 2 ? kMaxBufs * kScaleFloats : 0) + (warp - kEpiWarp0) * 32 * SC;
+        float4* srow = reinterpret_cast<float4*>(st + lane * SC);
+        // chunk j of row r sits at position j ^ sw(r): sw = r % 8 for 8 chunks per row (128-byte
+        // rows all start on bank 0), (r / 2) % 4 for 4 chunks (64-byte rows: even and odd rows
+        // start on banks 0 and 16)
+        const int wsw = CH16 == 8 ? (lane & 7) : ((lane >> 1) & 3);
+        // read-back: warp store i covers rows RPI i .. RPI i + RPI - 1; lane l carries chunk
+        // l % CH16 of row RPI i + l / CH16
+        const int rr = lane / CH16, pc = lane % CH16;
+        float* drow = dbase + (row - lane + rr) * p.N + col0 + 4 * pc;
 #pragma unroll
-        for (int c = 0; c < COLS; c += kStageCols) {
+        for (int c = 0; c < COLS; c += SC) {
 #pragma unroll
-          for (int j = 0; j < kStageCols / 4; ++j)
+          for (int j = 0; j < CH16; ++j)
             srow[j ^ wsw] = make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
           __syncwarp();
 #pragma unroll
-          for (int i = 0; i < 32 / 4; ++i) {
-            const int rs = 4 * i + rr;
-            const float2 v = reinterpret_cast<const float2*>(st + rs * kStageCols +
-                                                             4 * ((pr >> 1) ^ ((rs >> 1) & 3)))[pr & 1];
-            *reinterpret_cast<double2*>(drow + 4 * i * p.N + c) =
-                make_double2(f32_to_f64_scaled(v.x, 0, 1.0), f32_to_f64_scaled(v.y, 0, 1.0));
+          for (int i = 0; i < 32 / RPI; ++i) {
+            const int rs = RPI * i + rr;
+            const int rsw = CH16 == 8 ? (rs & 7) : ((rs >> 1) & 3);
+            *reinterpret_cast<float4*>(drow + RPI * i * p.N + c) =
+                reinterpret_cast<const float4*>(st + rs * SC)[pc ^ rsw];
           }
           __syncwarp();
         }
