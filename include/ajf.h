@@ -471,17 +471,6 @@ ajf_status ajf_selftest_queue_timeout(int device, double wait_ms, int32_t *code)
 ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t N, int64_t K, const double *A,
                                    const double *B, double *C);
 
-/* Self-test of the FP32 -> FP64 conversion that the tensor-core GEMM epilogue runs on the integer
- * pipe (no paper counterpart; used by the test suite). On device `device`, for each of the n
- * floats x of `in`, out receives the double x * s, where s = 1 + q * 2^-46 with
- * q = round((scale - 1) * 2^46); |scale - 1| must be below 2^-10 (the GEMM epilogue uses
- * scale = 1, an exact conversion). Normal x: within 2 units in the last place of the exact
- * product; zero keeps its sign; subnormal, infinite and NaN x as the hardware x * s.
- * in and out are host memory; the call allocates and frees its own device memory and
- * synchronises the device. Errors: AJF_E_ARG (NULL pointer, n < 0, scale), AJF_E_NOMEM,
- * AJF_E_CUDA. */
-ajf_status ajf_selftest_convert(int device, const float *in, double *out, int64_t n, double scale);
-
 /* Alg. I (alg = 1) or Alg. II (alg = 2) over several contexts at once: each context's device
  * program is enqueued on that context's own stream (give each context its own stream for the
  * circuits to overlap on the GPU), then all results are read back; out[i] receives context i's.

@@ -132,7 +132,6 @@ def lib() -> ctypes.CDLL:
             "ajf_version": (ctypes.c_char_p, []),
             "ajf_selftest_gemm": (I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_fidelity_noalloc": (I32, [P, ctypes.c_int, D, ctypes.POINTER(Result)]),
-            "ajf_selftest_convert": (I32, [ctypes.c_int, P, P, I64, D]),
             "ajf_selftest_split_gemm": (I32, [ctypes.c_int, ctypes.c_int, I64, I64, I64, P, P, P]),
             "ajf_selftest_wait_timeout": (I32, [ctypes.c_int, D, ctypes.POINTER(I32)]),
             "ajf_learned_param_count": (I32, []),
@@ -387,17 +386,6 @@ def ajf_selftest_split_gemm(device: int, precision: str, A: np.ndarray, B: np.nd
     if st != AJF_OK:
         raise AjfError(st, "ajf_selftest_split_gemm failed")
     return C
-
-
-def ajf_selftest_convert(device: int, x: np.ndarray, scale: float = 1.0) -> np.ndarray:
-    """Integer-pipe conversion self-test: float32 x -> float64 x * (1 + q 2^-46) with
-    q = round((scale - 1) 2^46)."""
-    x = np.ascontiguousarray(x, dtype=np.float32)
-    out = np.empty(x.shape, np.float64)
-    st = lib().ajf_selftest_convert(device, _ptr(x), _ptr(out), x.size, float(scale))
-    if st != AJF_OK:
-        raise AjfError(st, "ajf_selftest_convert failed")
-    return out
 
 
 def ajf_plan_launches(ctx) -> list:

@@ -1878,26 +1878,6 @@ ajf_status ajf_selftest_split_gemm(int device, int precision, int64_t M, int64_t
   return st;
 }
 
-ajf_status ajf_selftest_convert(int device, const float* in, double* out, int64_t n, double scale) {
-  if (!in || !out || n < 0 || !(std::fabs(scale - 1.0) < std::ldexp(1.0, -10))) return AJF_E_ARG;
-  const int64_t q = std::llround(std::ldexp(scale - 1.0, 46));
-  scale = 1.0 + std::ldexp(static_cast<double>(q), -46);  // the factor the kernel applies
-  if (n == 0) return AJF_OK;
-  if (cudaSetDevice(device) != cudaSuccess) return AJF_E_CUDA;
-  const size_t ib = size_t(n) * 4, ob = size_t(n) * 8;
-  const size_t off_o = (ib + 255) / 256 * 256;
-  char* d = nullptr;
-  if (cudaMalloc(&d, off_o + ob) != cudaSuccess) return AJF_E_NOMEM;
-  ajf_status st = AJF_OK;
-  if (cudaMemcpy(d, in, ib, cudaMemcpyHostToDevice) != cudaSuccess ||
-      launch_convert_check(reinterpret_cast<const float*>(d), reinterpret_cast<double*>(d + off_o), n, q, scale,
-                           0) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(out, d + off_o, ob, cudaMemcpyDeviceToHost) != cudaSuccess)
-    st = AJF_E_CUDA;
-  cudaFree(d);
-  return st;
-}
-
 ajf_status ajf_plan_launches(const ajf_ctx* c, ajf_launch_info* out, int cap, int* n) {
   if (!c || !n || cap < 0 || (cap > 0 && !out)) return AJF_E_ARG;
   if (!c->planned) return AJF_E_STATE;

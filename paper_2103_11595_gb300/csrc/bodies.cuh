@@ -30,7 +30,6 @@
 #include <type_traits>
 
 #include "device.h"
-#include "fp_bits.h"
 
 namespace ajf {
 

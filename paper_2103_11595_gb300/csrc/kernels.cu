@@ -20,7 +20,6 @@
 
 #include "bodies.cuh"
 #include "device.h"
-#include "fp_bits.h"
 #include "kernels.h"
 
 namespace ajf {
@@ -91,13 +90,6 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(const FinalDev* __restric
 __global__ void k_final(const FinalDev* __restrict__ fd, const double2* __restrict__ scalars,
                         const double* __restrict__ partial, double* __restrict__ result) {
   if (threadIdx.x == 0) final_body(fd, scalars, partial, result);
-}
-
-// Check of the integer-pipe conversion (test entry point): FP32 x -> FP64 x * (1 + q * 2^-46).
-__global__ void k_convert_check(const float* __restrict__ in, double* __restrict__ out, int64_t n, int64_t q,
-                                double scale) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    out[i] = f32_to_f64_scaled(in[i], q, scale);
 }
 
 // ------------------------------------------------------------------ CUDA-core GEMM
@@ -363,13 +355,6 @@ size_t dot_smem_bytes(const StepDev& st) {
   const BitMap* maps[2] = {&st.ka, &st.kb};
   const size_t nt = size_t(1) << st.ntl;
   return table_bytes(maps, 2) + nt * (8 + 8 + 8 + 8 + 2) + 16;
-}
-
-cudaError_t launch_convert_check(const float* in, double* out, int64_t n, int64_t q, double scale, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
-  k_convert_check<<<static_cast<unsigned>(blocks), 256, 0, s>>>(in, out, n, q, scale);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,

@@ -25,7 +25,6 @@ cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t sm
 // Tiled FP64 full contraction (k_dot) of steps with a scalar result, then the partial-sum pass.
 size_t dot_smem_bytes(const StepDev& st);
 // f32_products: FP32 products summed in FP32 per tile, tile sums in FP64 (reduced-precision modes).
-cudaError_t launch_convert_check(const float* in, double* out, int64_t n, int64_t q, double scale, cudaStream_t s);
 cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,
                        double2* partial, double2* scalars, bool f32_products, cudaStream_t s);
 cudaError_t launch_gemm_simt(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool f64,

@@ -59,7 +59,6 @@
 #include <mutex>
 
 #include "bodies.cuh"
-#include "fp_bits.h"
 #include "kernels.h"
 #include "tc_gemm_dev.cuh"
 

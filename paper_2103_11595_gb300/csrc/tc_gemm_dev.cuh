@@ -9,7 +9,6 @@
 
 #include <cstdint>
 
-#include "fp_bits.h"
 #include "kernels.h"
 
 namespace ajf {
