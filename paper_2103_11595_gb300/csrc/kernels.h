@@ -38,13 +38,13 @@ cudaError_t launch_persistent(const InterpJob* d_jobs, int n_jobs, const InterpO
                               cudaStream_t s);
 constexpr size_t kPersistentSmemMax = 96 * 1024;
 
-// Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (FP64, row-major) =
+// Tensor-core GEMM (tcgen05, tc_gemm.cu): C[M][N] (FP32, row-major) =
 // sum_{i + j < terms} A_i[M][K] . B_j[N][K]^T for the split terms A_t, B_t (byte offsets from
-// `base`), FP32 accumulation promoted per K block. kind 0: tf32, 1: bf16.
+// `base`), FP32 accumulation promoted per K block. kind 0: tf32, 1: bf16, 2: scaled fp16.
 // Returns cudaErrorNotSupported when the shape is not tile-aligned.
 bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int kind);
 // K splits for an M x N x K GEMM: GEMMs with fewer 128 x BN tiles than SMs divide K over several
-// CTAs, each writing an FP64 partial tile to a workspace of ksplit * M * N doubles that a
+// CTAs, each writing an FP32 partial tile to a workspace of ksplit * M * N floats that a
 // deterministic pass then sums into C. 1 = no split (no workspace).
 int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind);
 // A tensor-core GEMM launch prepared on the host (tensor maps, tiling, kernel parameters), so that
