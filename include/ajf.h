@@ -73,9 +73,11 @@ enum {
   AJF_PREC_F16X3 = 6   /* fp16 operands in two terms scaled by a power of two per row and K block,
                           three tcgen05 products (the scale undone per K block in the epilogue) */
 };
-/* Tensors are FP64 (planar complex) in device memory in every mode; a mode only sets how the
- * operands of the GEMM-class steps are rounded or split. Leaves, small steps, the final
- * contraction to a scalar, sum_i |t_i|^2, F_J and 1 - F_J are FP64 in every mode. */
+/* Tensors are planar complex in device memory: complex128 (FP64 planes), except the results of
+ * the reduced modes' GEMM-class steps, which are complex64 (FP32 planes; each value is one FP32
+ * register sum of the GEMM, so nothing is lost). A mode sets how the operands of the GEMM-class
+ * steps are rounded or split. Leaves, small steps, the final contraction to a scalar,
+ * sum_i |t_i|^2, F_J and 1 - F_J are FP64 in every mode. */
 
 enum {
   AJF_LOWER_DEFAULT = 0,   /* GEMM-class steps on tensor cores / CUDA-core GEMMs, one launch per
