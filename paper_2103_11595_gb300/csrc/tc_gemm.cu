@@ -173,7 +173,10 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   // work items are (tile, K split) pairs: a GEMM with few tiles but many K splits still spreads
   // over every SM
   const int64_t work = tiles * static_cast<int64_t>(p.ksplit);
-  const int64_t grid = work < sms ? work : sms;
+  // as few CTAs as keep the number of rounds (work items per CTA) at its minimum: the last round
+  // is no longer partly empty, and the SMs left over run other streams' kernels meanwhile
+  const int64_t rounds = (work + sms - 1) / sms;
+  const int64_t grid = (work + rounds - 1) / rounds;
   // A/B type: TF32 = 2 (kind::tf32), BF16 = 1, F16 = 0 (kind::f16); D = F32; both K-major
   const uint32_t fmt = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
