@@ -1,7 +1,7 @@
 // Tensor-core GEMM on sm_103a: tcgen05.mma with TMEM accumulators, TMA-fed shared-memory stages,
 // and promotion of partial sums to round-to-nearest FP32 on the CUDA cores.
 //
-//   C[M][N] (FP64, row-major) = sum_{i + j < T} A_i[M][K] . B_j[N][K]^T
+//   C[M][N] (FP32, row-major) = sum_{i + j < T} A_i[M][K] . B_j[N][K]^T
 //
 // A_t and B_t (t < T) are the terms of a split operand -- x = x_0 + x_1 (+ x_2) -- stored
 // K-contiguous (K-major) in TF32 (FP32 containers) or bf16. T = 1 is a plain one-pass product;
@@ -25,15 +25,15 @@
 //    relative to |P1| and so at most ~2^-31 of the result per instruction;
 //  * promotion: eight epilogue warps add P0 + P1 of every K block into FP32 registers with
 //    round-to-nearest (unbiased), at most kMaxBlocksPerSplit blocks per register sum; longer
-//    contractions are split over K and the FP64 partial tiles summed in a fixed order.
-// No calibrated correction factor is involved; the result is stored as FP32 -> FP64 exactly.
+//    contractions are split over K and the FP32 partial tiles summed (compensated) in a fixed order.
+// No calibrated correction factor is involved; the promoted FP32 sums are the stored result.
 // The two-term splits (TF32 and bf16 three-product modes) keep a floating leading term, whose 11
 // or 8 significant bits follow each entry: their P0 truncates like a plain accumulation, one
 // promoted K block at a time, and they are bounded modes, not FP32-class ones.
 //
-// Kernel structure (persistent: one CTA per SM walks the 128 x BN output tiles in a grouped
-// raster order; 320 threads; the slot and TMEM-buffer rings continue from tile to tile so the
-// loads and MMAs of the next tile overlap the FP64 store of the current one):
+// Kernel structure (persistent: at most one CTA per SM walks the 128 x BN output tiles in a
+// grouped raster order; 320 threads; the slot and TMEM-buffer rings continue from tile to tile so
+// the loads and MMAs of the next tile overlap the store of the current one):
 //   warp 0, lane 0 : TMA producer -- for every K block and term, the A tile (128 rows x 128 B) and
 //                    the B tile (BN rows x 128 B), 128-byte swizzle, into a ring of slots
 //                    (mbarrier expect-tx / complete-tx);
@@ -42,10 +42,10 @@
 //                    to release slots and hand partials to the epilogue;
 //   warps 2..9     : epilogue -- two warps per TMEM lane quarter (warp % 4), each owning half of
 //                    the BN columns of its rows: tcgen05.ld, FP32 round-to-nearest accumulation in
-//                    registers, FP64 store of the tile (rows < M, columns < N) staged through
+//                    registers, FP32 store of the tile (rows < M, columns < N) staged through
 //                    shared memory so that every warp store writes whole 128-byte row segments.
 // Work items are (tile, K split) pairs. GEMMs with fewer tiles than SMs, or with more than
-// kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP64 partial
+// kMaxBlocksPerSplit K blocks, split K over several work items; each split writes an FP32 partial
 // tile to a workspace and k_split_sum adds the splits in a fixed order (deterministic).
 // Every wait is bounded by the global timer (2 s); on expiry the kernel records a status code,
 // stops issuing work, waits (bounded again) for the TMA loads and MMAs it already issued,
@@ -167,7 +167,7 @@ cudaError_t prepare_tile(TcParams& p, TcPrepared* t, int64_t M, int64_t N) {
   p.mtn = static_cast<int32_t>(mt);
   p.group = static_cast<int32_t>(mt < 8 ? mt : 8);
   p.tiles = tiles;
-  // persistent grid: one CTA per SM (the kernel holds 1 CTA/SM), each walking tiles with a stride
+  // persistent grid: at most one CTA per SM (the kernel holds 1 CTA/SM), each walking tiles with a stride
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
   // work items are (tile, K split) pairs: a GEMM with few tiles but many K splits still spreads
@@ -222,7 +222,7 @@ int tc_gemm_splits(int64_t M, int64_t N, int64_t K, int kind) {
     if (kp > kblocks / 8) kp = kblocks / 8;
     if (kp > ks) ks = kp;
   }
-  // workspace of ksplit * M * N doubles: at most 8 GiB (beyond that, fewer and longer splits)
+  // workspace of ksplit * M * N FP32 values: at most 2^30 of them (beyond that, fewer and longer splits)
   while (ks > 1 && ks * M * N * 8 > (int64_t(8) << 30)) --ks;
   if (ks <= 1) return 1;
   const int64_t per = (kblocks + ks - 1) / ks;

@@ -22,7 +22,7 @@ constexpr int kThreads = 320;        // producer warp, MMA warp, eight epilogue 
 constexpr int kEpiWarps = 8;
 constexpr int kEpiWarp0 = 2;       // epilogue warps 2..9: warp w reads TMEM lanes 32 * (w % 4) .. + 31
 // The FP32 register accumulation of promoted partials spans at most this many K blocks: longer
-// contractions are split over K (FP64 partial tiles summed afterwards), so the small late
+// contractions are split over K (FP32 partial tiles summed afterwards), so the small late
 // partials of a long FP32 running sum are not lost.
 constexpr int kMaxBlocksPerSplit = 64;
 // SM count the K-split heuristic plans for (GB300); the split count only changes how work is
@@ -414,7 +414,7 @@ __device__ __forceinline__ bool tc_gemm_items(const TcParams& p, uint32_t wi0, u
     r.mbphase = bphase;
     r.mphase = phase;
   } else if (warp >= kEpiWarp0) {
-    // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP64 per tile
+    // ---- epilogue: promote partials into round-to-nearest FP32 registers, store FP32 per tile
     const int q = warp & 3, h = (warp - kEpiWarp0) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
     float acc[COLS];
