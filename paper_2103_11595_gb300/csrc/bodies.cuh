@@ -284,10 +284,22 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
   V* sre = reinterpret_cast<V*>(locB + nt);
   V* sim = sre + nt;
   uint16_t* a_of_b = reinterpret_cast<uint16_t*>(sim + nt);  // B-order local index -> A-order
-  build_table(st.ka, t_ka);
-  build_table(st.kb, t_kb);
   uint64_t tilemask = 0;
   for (int i = 0; i < ntl; ++i) tilemask |= uint64_t(1) << st.tl[i];
+  // the tile number's bits are the contracted bits outside the tile, lowest first: tables over the
+  // tile number give a tile's base offsets in A and B with a few shared-memory reads (they have
+  // at most as many chunks as the tables over all contracted bits, whose space they take)
+  BitMap ta, tb;
+  ta.nbits = tb.nbits = st.rk - ntl;
+  for (int i = 0, j = 0; i < st.rk; ++i) {
+    if ((tilemask >> i) & 1) continue;
+    ta.pos[j] = st.ka.pos[i];
+    tb.pos[j] = st.kb.pos[i];
+    ++j;
+  }
+  const int c_ta = nchunks(ta.nbits);
+  build_table(ta, t_ka);
+  build_table(tb, t_kb);
   for (int l = threadIdx.x; l < nt; l += kBodyThreads) {
     int64_t oa = 0, ob = 0;
     uint64_t kk = 0;
@@ -309,17 +321,10 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
   const int64_t ntiles = int64_t(1) << (st.rk - ntl);
   double re = 0, im = 0;
   with_operands(arena, st.a, st.fa, st.b, st.fb, [&](const auto* A, const auto* B) {
-    // the tile's base offsets in A and B: the tile number spread over the non-tile bits
+    // the tile's base offsets in A and B
     auto tile_base = [&](int64_t t, int64_t& ba, int64_t& bb) {
-      uint64_t base = 0;
-      int64_t rem = t;
-      for (int i = 0; i < st.rk && rem; ++i) {
-        if ((tilemask >> i) & 1) continue;
-        if (rem & 1) base |= uint64_t(1) << i;
-        rem >>= 1;
-      }
-      ba = lookup(t_ka, c_ka, static_cast<int64_t>(base));
-      bb = lookup(t_kb, c_kb, static_cast<int64_t>(base));
+      ba = lookup(t_ka, c_ta, t);
+      bb = lookup(t_kb, c_ta, t);
     };
     // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
     // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
