@@ -578,6 +578,124 @@ struct PermSmem {
   int qre[32], qim[32];
 };
 
+// The three bf16 terms of 8 consecutive values of one row block (OPM_BF16X3, quantum 2^qexp),
+// packed 8 per 16 bytes; the same arithmetic, in the same order, as store_operand2.
+__device__ __forceinline__ void split8_bf16x3(const float (&x)[8], int qexp, uint4& hi, uint4& mid, uint4& lo) {
+  uint32_t h[4], m[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float h0 = lead_term(x[2 * j], qexp), h1 = lead_term(x[2 * j + 1], qexp);
+    const float r0 = x[2 * j] - h0, r1 = x[2 * j + 1] - h1;
+    const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
+    const float2 mf = __bfloat1622float2(mb);
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(h0, h1);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+    h[j] = *reinterpret_cast<const uint32_t*>(&hb);
+    m[j] = *reinterpret_cast<const uint32_t*>(&mb);
+    l[j] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  mid = make_uint4(m[0], m[1], m[2], m[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ uint4 neg_bf16x8(uint4 v) {
+  return make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+}
+
+// The six-product bf16 split over whole 32-row x 64-k tiles (R >= 32, K >= 64). Each thread splits
+// 8 consecutive k of one row -- the row's quantum from a max over the row's 8 threads (lanes of
+// one aligned group of 8) -- and writes every term with 16-byte stores; the embedded side's
+// second copies reuse the split (-Im is Im with the sign bits flipped). Two barriers per tile.
+// The values are those of the general loop below, which handles every other case.
+template <typename Sync>
+__device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double* __restrict__ arena,
+                                                  char* __restrict__ base, int vb, int vg, const int64_t* t_r,
+                                                  int c_r, const int64_t* t_k, int c_k, PermSmem<float>& sm) {
+  const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
+  const int64_t ntk = K / 64, ntiles = (R / 32) * ntk;
+  const double* src = arena + p.src;
+  const float* srcf = reinterpret_cast<const float*>(arena) + p.src;
+  const int64_t ld = 2 * K;
+  const int lead = lead_bits(OPM_BF16X3);
+  uint4* d0 = reinterpret_cast<uint4*>(base + p.dst[0]);
+  uint4* d1 = reinterpret_cast<uint4*>(base + p.dst[1]);
+  uint4* d2 = reinterpret_cast<uint4*>(base + p.dst[2]);
+  // split phase: row i of the tile, k chunk c (k = 8c .. 8c + 7)
+  const int i = threadIdx.x >> 3, c = threadIdx.x & 7;
+  auto store3 = [&](int64_t idx, const uint4& a, const uint4& b, const uint4& e) {
+    d0[idx >> 3] = a;
+    d1[idx >> 3] = b;
+    d2[idx >> 3] = e;
+  };
+  for (int64_t tile = vb; tile < ntiles; tile += vg) {
+    const int64_t r0 = (tile / ntk) * 32, k0 = (tile % ntk) * 64;
+    if (threadIdx.x < 32) sm.roff[threadIdx.x] = lookup(t_r, c_r, r0 + threadIdx.x);
+    else if (threadIdx.x < 96) sm.koff[threadIdx.x - 32] = lookup(t_k, c_k, k0 + threadIdx.x - 32);
+    Sync::sync();
+    {
+      // all loads (x 2 planes) of a thread are issued before its shared-memory stores
+      float vr[8], vi[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : (l >> 6), kk = p.rows_fast ? (l >> 5) : (l & 63);
+        const int64_t off = sm.roff[rr] + sm.koff[kk];
+        if (p.src_f32) {
+          vr[q] = srcf[off];
+          vi[q] = srcf[p.plane + off];
+        } else {
+          vr[q] = static_cast<float>(src[off]);
+          vi[q] = static_cast<float>(src[p.plane + off]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = threadIdx.x + 256 * q;
+        const int rr = p.rows_fast ? (l & 31) : (l >> 6), kk = p.rows_fast ? (l >> 5) : (l & 63);
+        sm.tre[rr][kk] = vr[q];
+        sm.tim[rr][kk] = vi[q];
+      }
+    }
+    Sync::sync();
+    const int64_t r = r0 + i, k = k0 + 8 * c;
+    uint4 h, m, l;
+    {
+      float x[8];
+      float mx = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        x[j] = sm.tre[i][8 * c + j];
+        mx = fmaxf(mx, fabsf(x[j]));
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      split8_bf16x3(x, quantum_exp(mx, lead), h, m, l);
+    }
+    store3(r * ld + k, h, m, l);                                  // (s=0, t=0) or Y side: Re
+    if (p.embed) store3((R + r) * ld + K + k, h, m, l);           // (s=1, t=1): Re
+    {
+      float x[8];
+      float mx = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        x[j] = sm.tim[i][8 * c + j];
+        mx = fmaxf(mx, fabsf(x[j]));
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      split8_bf16x3(x, quantum_exp(mx, lead), h, m, l);
+    }
+    if (p.embed) {
+      store3((R + r) * ld + k, h, m, l);                                       // (s=1, t=0):  Im
+      store3(r * ld + K + k, neg_bf16x8(h), neg_bf16x8(m), neg_bf16x8(l));     // (s=0, t=1): -Im
+    } else {
+      store3(r * ld + K + k, h, m, l);                                         // Y side: Im
+    }
+  }
+  Sync::sync();
+}
+
 template <typename S, typename Sync>
 __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, const double* __restrict__ arena,
                                           char* __restrict__ base, int vb, int vg, int vy, int64_t* tab,
@@ -596,6 +714,12 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
   build_table(p.rows, t_r);
   build_table(p.cols, t_k);
   Sync::sync();
+  if constexpr (sizeof(S) == 4) {
+    if (p.mode == OPM_BF16X3 && p.rbits >= 5 && p.kbits >= 6) {
+      perm_tiles_bf16x3<Sync>(p, arena, base, vb, vg, t_r, c_r, t_k, c_k, sm);
+      return;
+    }
+  }
   const bool split = sizeof(S) == 4 && split_mode(p.mode);
   const int lead = lead_bits(p.mode);
   // K block of the six-product split in complex k: 64 elements of one plane; with K below that,
