@@ -319,6 +319,13 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
   }
   Sync::sync();
   const int64_t ntiles = int64_t(1) << (st.rk - ntl);
+  // vector form: both operands FP32 with their two lowest positions the tile's two lowest bits in
+  // both orders (always so for a full contraction, whose tile holds each operand's five lowest
+  // positions) and 16-byte aligned planes: a thread's 4 consecutive tile-local indices are then 4
+  // consecutive elements of A (A order) and of B (B order), one 16-byte load per plane
+  const bool vec = kF32 && st.fa && st.fb && ntl == 10 && st.ka.pos[st.tl[0]] == 0 && st.ka.pos[st.tl[1]] == 1 &&
+                   st.kb.pos[st.tlb[0]] == 0 && st.kb.pos[st.tlb[1]] == 1 &&
+                   ((st.a | st.pa | st.b | st.pb) & 3) == 0;
   double re = 0, im = 0;
   with_operands(arena, st.a, st.fa, st.b, st.fb, [&](const auto* A, const auto* B) {
     // the tile's base offsets in A and B
@@ -326,6 +333,61 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
       ba = lookup(t_ka, c_ta, t);
       bb = lookup(t_kb, c_ta, t);
     };
+    using TA = typename std::remove_cv<typename std::remove_pointer<decltype(A)>::type>::type;
+    using TB = typename std::remove_cv<typename std::remove_pointer<decltype(B)>::type>::type;
+    if constexpr (kF32 && std::is_same<TA, float>::value && std::is_same<TB, float>::value) {
+      if (vec) {
+        // thread t owns tile-local indices 4t .. 4t + 3 in both orders; the next tile's four
+        // 16-byte loads are in flight while the current tile is multiplied. A is staged at
+        // l ^ ((l >> 5) & 31) as below; each B element then reads its A partner there.
+        const int l0 = 4 * threadIdx.x;
+        const int64_t oA = locA[l0], oB = locB[l0];
+        const int k5 = (l0 >> 5) & 31;
+        int sa[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int la = a_of_b[l0 + j];
+          sa[j] = la ^ ((la >> 5) & 31);
+        }
+        float4 ar, ai, br, bi;
+        auto load4 = [&](int64_t t) {
+          int64_t ba, bb;
+          tile_base(t, ba, bb);
+          ar = *reinterpret_cast<const float4*>(A + ba + oA);
+          ai = *reinterpret_cast<const float4*>(A + st.pa + ba + oA);
+          br = *reinterpret_cast<const float4*>(B + bb + oB);
+          bi = *reinterpret_cast<const float4*>(B + st.pb + bb + oB);
+        };
+        int64_t t = split;
+        if (t < ntiles) load4(t);
+        while (t < ntiles) {
+          sre[(l0 + 0) ^ k5] = ar.x;
+          sre[(l0 + 1) ^ k5] = ar.y;
+          sre[(l0 + 2) ^ k5] = ar.z;
+          sre[(l0 + 3) ^ k5] = ar.w;
+          sim[(l0 + 0) ^ k5] = ai.x;
+          sim[(l0 + 1) ^ k5] = ai.y;
+          sim[(l0 + 2) ^ k5] = ai.z;
+          sim[(l0 + 3) ^ k5] = ai.w;
+          const float cb[8] = {br.x, br.y, br.z, br.w, bi.x, bi.y, bi.z, bi.w};
+          Sync::sync();
+          const int64_t tn = t + st.nsplit;
+          if (tn < ntiles) load4(tn);
+          float fre = 0.0f, fim = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float xr = sre[sa[j]], xi = sim[sa[j]];
+            fre += xr * cb[j] - xi * cb[4 + j];
+            fim += xr * cb[4 + j] + xi * cb[j];
+          }
+          re += fre;
+          im += fim;
+          Sync::sync();
+          t = tn;
+        }
+        return;
+      }
+    }
     // Software pipeline: the A and B values of the next tile (kPer per thread; tiles hold at most
     // 2^10 = 256 * kPer elements) are loaded into registers while the current tile is multiplied,
     // so the loads of two tiles are in flight. Staged A values sit at index l ^ ((l >> 5) & 31):
