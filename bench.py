@@ -269,15 +269,20 @@ def main():
     insts = [W.mid(s) for s in shard_seeds(rank, n_inst, args.first_seed)]
     streams = [torch.cuda.Stream() for _ in insts]
 
+    def make_context(inst, s, precision, use_graph=True, simplify="none"):
+        c = ajf.Context(dev, s.cuda_stream)
+        ajf.load_instance(c.handle, inst)
+        info = ajf.ajf_plan(c.handle, 2, precision=precision, trials=args.trials, use_graph=use_graph,
+                            simplify=simplify)
+        ajf.ajf_upload(c.handle)
+        return c, info
+
     def make_contexts(precision, use_graph=True, simplify="none"):
         ctxs, infos = [], []
         for inst, s in zip(insts, streams):
-            c = ajf.Context(dev, s.cuda_stream)
-            ajf.load_instance(c.handle, inst)
-            infos.append(ajf.ajf_plan(c.handle, 2, precision=precision, trials=args.trials, use_graph=use_graph,
-                                      simplify=simplify))
-            ajf.ajf_upload(c.handle)
+            c, info = make_context(inst, s, precision, use_graph, simplify)
             ctxs.append(c)
+            infos.append(info)
         return ctxs, infos
 
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -322,6 +327,14 @@ def main():
     # ---- fast path: timed region with clock sampling
     ctxs, infos = make_contexts(args.precision)
     lpt = sorted(range(len(ctxs)), key=lambda i: -infos[i]["flops"])
+    # the two instances with the most planned work have the longest chains of dependent launches:
+    # their streams take the device's highest priority, so their kernels get SMs first as SMs free
+    # up (measured on the mid step: 1,118 -> 1,136 evals/s; all ten graded by rank: 1,124)
+    top = torch.cuda.Stream.priority_range()[1]
+    for i in lpt[:2]:
+        ctxs[i].close()
+        streams[i] = torch.cuda.Stream(priority=top)
+        ctxs[i], infos[i] = make_context(insts[i], streams[i], args.precision)
     with ClockSampler(dev) as clk:
         total_ms = timed_steps(ctxs, args.steps, args.warmup, lpt)
     clocks = clk.summary()
@@ -523,6 +536,8 @@ def main():
                        else WORKLOAD + f" (only seeds {args.first_seed}..{args.first_seed + n_inst - 1})",
                        "precision": args.precision, "planner": "auto",
                        "trials": args.trials, "l2": "flushed (256 MiB write) before every step",
+                       "streams": "one per instance, launched heaviest first; the two heaviest at the "
+                                  "highest stream priority",
                        "parallelism": f"{world} independent ranks (weak scaling)"},
             "tflops": flops_per_step * args.steps * world / total_s / 1e12,
             "flops_per_step": flops_per_step,
@@ -608,12 +623,17 @@ def small_networks_line(args, world, rank, local):
     # in the requested precision, each on a stream of its own with its CUDA graph
     pers, big, big_streams, order = [], [], [], []
     infos = []
+    pflops = []
     for inst, alg in jobs:
         probe = ajf.Context(-1)
         ajf.load_instance(probe.handle, inst)
-        pinfo = ajf.ajf_plan(probe.handle, alg, trials=args.trials, lowering="persistent")
+        pflops.append(ajf.ajf_plan(probe.handle, alg, trials=args.trials, lowering="persistent")["flops"])
         probe.close()
-        if pinfo["flops"] <= pers_flops_max:
+    # as in the mid step: the two networks with the most work run on the highest-priority streams
+    top = torch.cuda.Stream.priority_range()[1]
+    heavy = set(sorted((j for j in range(n_jobs) if pflops[j] > pers_flops_max), key=lambda j: -pflops[j])[:2])
+    for j, (inst, alg) in enumerate(jobs):
+        if pflops[j] <= pers_flops_max:
             c = ajf.Context(dev, stream.cuda_stream)
             ajf.load_instance(c.handle, inst)
             infos.append(ajf.ajf_plan(c.handle, alg, trials=args.trials, lowering="persistent"))
@@ -621,7 +641,7 @@ def small_networks_line(args, world, rank, local):
             order.append(("p", len(pers)))
             pers.append(c)
         else:
-            s = torch.cuda.Stream()
+            s = torch.cuda.Stream(priority=top) if j in heavy else torch.cuda.Stream()
             c = ajf.Context(dev, s.cuda_stream)
             ajf.load_instance(c.handle, inst)
             infos.append(ajf.ajf_plan(c.handle, alg, precision=args.precision, trials=args.trials, use_graph=True))
@@ -641,13 +661,16 @@ def small_networks_line(args, world, rank, local):
         pers_rows[alg] = row
         row += len(groups[alg])
     big_rows = list(range(row, row + len(big)))
+    # launch order of the large networks: the most planned work first
+    big_flops = [infos[j]["flops"] for j, (kind, _) in enumerate(order) if kind == "b"]
+    big_order = sorted(range(len(big)), key=lambda k: -big_flops[k])
 
     def step():
         fork = torch.cuda.Event()
         fork.record(stream)
-        for k, c in enumerate(big):
+        for k in big_order:
             big_streams[k].wait_event(fork)
-            ajf.ajf_launch(c.handle, out[big_rows[k]].data_ptr())
+            ajf.ajf_launch(big[k].handle, out[big_rows[k]].data_ptr())
         for alg in sorted(groups):
             hs = [pers[i].handle for i in groups[alg]]
             ajf.ajf_launch_persistent(hs, out[pers_rows[alg]].data_ptr())
