@@ -109,7 +109,7 @@ void finish_components(std::vector<Labels>& ts, std::vector<char>& alive, Path& 
 // occupy every SM runs proportionally slower.
 double step_seconds(int ra, int rb, int runion, int rc, const PlanParams& p) {
   constexpr double kBw = 5.0e12;        // achieved HBM bandwidth of the streaming kernels (B/s)
-  constexpr double kGatherBw = 2.0e12;  // achieved bandwidth of the operand gather (permuted reads)
+  constexpr double kGatherBw = 3.4e12;  // achieved bandwidth of the operand gather (permuted reads, ncu)
   constexpr double kFp64 = 1.0e12;      // FP64 CUDA-core rate (flop/s)
   constexpr double kFp32 = 40e12;       // FP32 CUDA-core rate
   constexpr double kSMs = 152;
