@@ -415,7 +415,6 @@ ajf_status enqueue_program(ajf_ctx* c, cudaStream_t s, ajf_ctx::TcPrepSet* tc = 
   const PermDev* perms = reinterpret_cast<const PermDev*>(base + P.off_perms);
   double2* partial = reinterpret_cast<double2*>(base + P.off_partial);
   double2* scalars = reinterpret_cast<double2*>(base + P.off_scalars);
-  int* status = reinterpret_cast<int*>(base + P.off_status);
   // tensor-core GEMM set-up (tensor maps, tiling) is done on the host once per program and arena,
   // outside the timed launches
   {

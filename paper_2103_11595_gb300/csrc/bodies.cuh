@@ -266,7 +266,25 @@ __device__ __forceinline__ void splitk_body(const StepDev* __restrict__ steps, i
 // products of each tile are formed and summed in FP32 per thread (FP32 operands: complex64
 // tensors as they are, complex128 ones rounded; relative error ~1e-7 per term) and the tile sums
 // are accumulated in FP64.
-template <typename T, bool kF32, typename Sync>
+// Asynchronous global -> shared copies (4 bytes, or 16 bytes with both addresses 16-byte aligned),
+// committed in groups; cp_async_wait<N> returns once at most N of this thread's groups are pending.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, bool kF32, typename Sync, bool kStaged = false>
 __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int nsteps, const T* __restrict__ arena,
                                          double2* __restrict__ partial, int vb, int64_t* tab, double* red_re,
                                          double* red_im) {
@@ -348,6 +366,61 @@ __device__ __forceinline__ void dot_body(const StepDev* __restrict__ steps, int 
         for (int j = 0; j < 4; ++j) {
           const int la = a_of_b[l0 + j];
           sa[j] = la ^ ((la >> 5) & 31);
+        }
+        if constexpr (kStaged) {
+          // Staged form: asynchronous copies into three shared-memory stages, two tiles ahead of
+          // the one being multiplied, with no registers held for them. A stage is four arrays of
+          // 1024 floats (A re, A im at the swizzled positions above, B re, B im in B order); 6 of
+          // the 12 arrays overlay locA .. sim (24 KB, free once this thread's offsets and A
+          // positions are in registers), the other 6 follow the layout (dot_smem_bytes).
+          float* const R = reinterpret_cast<float*>(locA);
+          float* const X = reinterpret_cast<float*>(reinterpret_cast<char*>(locA) + nt * 34);
+          auto arr = [&](int k) -> float* { return k < 6 ? R + k * 1024 : X + (k - 6) * 1024; };
+          Sync::sync();  // every thread has read locA, locB and a_of_b
+          auto issue = [&](int sg, int64_t t) {
+            int64_t ba, bb;
+            tile_base(t, ba, bb);
+            float* const dr = arr(4 * sg);
+            float* const di = arr(4 * sg + 1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              cp_async4(dr + ((l0 + j) ^ k5), A + ba + oA + j);
+              cp_async4(di + ((l0 + j) ^ k5), A + st.pa + ba + oA + j);
+            }
+            cp_async16(arr(4 * sg + 2) + l0, B + bb + oB);
+            cp_async16(arr(4 * sg + 3) + l0, B + st.pb + bb + oB);
+          };
+          const int64_t ns = st.nsplit;
+          int64_t t = split;
+          if (t < ntiles) issue(0, t);
+          cp_async_commit();
+          if (t + ns < ntiles) issue(1, t + ns);
+          cp_async_commit();
+          int sg = 0;
+          while (t < ntiles) {
+            cp_async_wait<1>();  // this thread's copies of tile t have landed
+            Sync::sync();        // everyone's have, and stage (sg + 2) % 3 is no longer read
+            if (t + 2 * ns < ntiles) issue(sg == 0 ? 2 : sg - 1, t + 2 * ns);
+            cp_async_commit();
+            const float* const xr = arr(4 * sg);
+            const float* const xi = arr(4 * sg + 1);
+            const float4 br = *reinterpret_cast<const float4*>(arr(4 * sg + 2) + l0);
+            const float4 bi = *reinterpret_cast<const float4*>(arr(4 * sg + 3) + l0);
+            const float cb[8] = {br.x, br.y, br.z, br.w, bi.x, bi.y, bi.z, bi.w};
+            float fre = 0.0f, fim = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float ar = xr[sa[j]], ai = xi[sa[j]];
+              fre += ar * cb[j] - ai * cb[4 + j];
+              fim += ar * cb[4 + j] + ai * cb[j];
+            }
+            re += fre;
+            im += fim;
+            t += ns;
+            sg = sg == 2 ? 0 : sg + 1;
+          }
+          cp_async_wait<0>();
+          return;
         }
         float4 ar, ai, br, bi;
         auto load4 = [&](int64_t t) {

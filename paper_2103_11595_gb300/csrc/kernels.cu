@@ -49,13 +49,13 @@ __global__ void __launch_bounds__(kBodyThreads) k_splitk(const StepDev* __restri
 }
 
 // 4 blocks per SM (64 registers): the tiled trace is bound by memory latency, and its grid is
-// sized for 4 blocks per SM
+// sized for 4 blocks per SM (3 for the staged FP32 form, whose stages take more shared memory)
 template <typename T, bool kF32>
 __global__ void __launch_bounds__(kBodyThreads, 4) k_dot(const StepDev* __restrict__ steps, int nsteps,
                                                       const T* __restrict__ arena, double2* __restrict__ partial) {
   extern __shared__ int64_t tab[];
   __shared__ double red_re[kBodyThreads], red_im[kBodyThreads];
-  dot_body<T, kF32, SyncBlock>(steps, nsteps, arena, partial, blockIdx.x, tab, red_re, red_im);
+  dot_body<T, kF32, SyncBlock, kF32>(steps, nsteps, arena, partial, blockIdx.x, tab, red_re, red_im);
 }
 
 template <typename T>
@@ -351,10 +351,14 @@ cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, 
   return cudaGetLastError();
 }
 
-size_t dot_smem_bytes(const StepDev& st) {
+bool dot_staged(const StepDev& st, bool f32_products) { return f32_products && st.fa && st.fb && st.ntl == 10; }
+
+size_t dot_smem_bytes(const StepDev& st, bool f32_products) {
   const BitMap* maps[2] = {&st.ka, &st.kb};
   const size_t nt = size_t(1) << st.ntl;
-  return table_bytes(maps, 2) + nt * (8 + 8 + 8 + 8 + 2) + 16;
+  // the staged form adds 6 of its 12 stage arrays (nt floats each) after the layout below; the
+  // other 6 overlay the offset and staging arrays once their values are in registers
+  return table_bytes(maps, 2) + nt * (8 + 8 + 8 + 8 + 2) + 16 + (dot_staged(st, f32_products) ? 6 * nt * 4 : 0);
 }
 
 cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,

@@ -23,7 +23,10 @@ cudaError_t launch_splitk(const StepDev* d_steps, int nsteps, int total_blocks, 
 cudaError_t launch_perm(const PermDev* d_perms, int nperm, int grid_x, size_t smem, const void* arena, void* base,
                         bool op_f64, cudaStream_t s);
 // Tiled FP64 full contraction (k_dot) of steps with a scalar result, then the partial-sum pass.
-size_t dot_smem_bytes(const StepDev& st);
+// The tiled dot's staged form (FP32 operands, FP32 products): the step qualifies on the host side;
+// the kernel also checks the operands' bit positions and alignment and otherwise falls back.
+bool dot_staged(const StepDev& st, bool f32_products);
+size_t dot_smem_bytes(const StepDev& st, bool f32_products);
 // f32_products: FP32 products summed in FP32 per tile, tile sums in FP64 (reduced-precision modes).
 cudaError_t launch_dot(const StepDev* d_steps, int nsteps, int total_blocks, size_t smem, const void* arena,
                        double2* partial, double2* scalars, bool f32_products, cudaStream_t s);

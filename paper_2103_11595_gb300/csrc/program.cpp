@@ -336,8 +336,10 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
           }
           const int64_t tiles = int64_t(1) << (d.rk - d.ntl);
           // at most 4 blocks per SM (152 SMs): each block amortises its offset-table set-up over
-          // more tiles (measured on the mid workload against 8 per SM: 1.88 -> 1.79 ms per step)
-          const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * kPlanSMsDot));
+          // more tiles (measured on the mid workload against 8 per SM: 1.88 -> 1.79 ms per step);
+          // 3 per SM for the staged FP32 form (three tiles of shared-memory stages per block)
+          const int64_t per_sm = dot_staged(d, precision != AJF_PREC_F64) ? 3 : 4;
+          const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(tiles, per_sm * kPlanSMsDot));
           d.nsplit = static_cast<int32_t>(nsplit);
           d.poff = static_cast<int64_t>(partials);
           partials += static_cast<size_t>(nsplit);
@@ -353,7 +355,7 @@ Program lower(const Network& net, const Path& path, int precision, size_t inputs
           if (d.rc == 0) d.scalar_slot = scalar_slots++;
           blocks += static_cast<int>(nout * nsplit);
         }
-        smem = std::max(smem, cls == C_DOT ? dot_smem_bytes(d) : step_table_bytes(d));
+        smem = std::max(smem, cls == C_DOT ? dot_smem_bytes(d, precision != AJF_PREC_F64) : step_table_bytes(d));
         ln.flops += 8.0 * std::ldexp(1.0, d.rc + d.rk);
         ln.bytes += (std::ldexp(1.0, static_cast<int>(la.size())) * elem(I.a) +
                      std::ldexp(1.0, static_cast<int>(lb.size())) * elem(I.b) +
