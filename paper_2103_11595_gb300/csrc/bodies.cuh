@@ -746,7 +746,8 @@ __device__ __forceinline__ uint4 neg_bf16x8(uint4 v) {
 template <typename Sync>
 __device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double* __restrict__ arena,
                                                   char* __restrict__ base, int vb, int vg, const int64_t* t_r,
-                                                  int c_r, const int64_t* t_k, int c_k, PermSmem<float>& sm) {
+                                                  int c_r, const int64_t* t_k, int c_k, PermSmem<float>& sm,
+                                                  PermSmem<float>* sm2) {
   const int64_t R = int64_t(1) << p.rbits, K = int64_t(1) << p.kbits;
   const int64_t ntk = K / 64, ntiles = (R / 32) * ntk;
   const double* src = arena + p.src;
@@ -763,44 +764,28 @@ __device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double
     d1[idx >> 3] = b;
     d2[idx >> 3] = e;
   };
-  for (int64_t tile = vb; tile < ntiles; tile += vg) {
+  // the source offsets of a tile's 32 rows and 64 k (threads 0..95)
+  auto lookups = [&](PermSmem<float>& b, int64_t tile) {
     const int64_t r0 = (tile / ntk) * 32, k0 = (tile % ntk) * 64;
-    if (threadIdx.x < 32) sm.roff[threadIdx.x] = lookup(t_r, c_r, r0 + threadIdx.x);
-    else if (threadIdx.x < 96) sm.koff[threadIdx.x - 32] = lookup(t_k, c_k, k0 + threadIdx.x - 32);
-    Sync::sync();
-    {
-      // all loads (x 2 planes) of a thread are issued before its shared-memory stores
-      float vr[8], vi[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int l = threadIdx.x + 256 * q;
-        const int rr = p.rows_fast ? (l & 31) : (l >> 6), kk = p.rows_fast ? (l >> 5) : (l & 63);
-        const int64_t off = sm.roff[rr] + sm.koff[kk];
-        if (p.src_f32) {
-          vr[q] = srcf[off];
-          vi[q] = srcf[p.plane + off];
-        } else {
-          vr[q] = static_cast<float>(src[off]);
-          vi[q] = static_cast<float>(src[p.plane + off]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int l = threadIdx.x + 256 * q;
-        const int rr = p.rows_fast ? (l & 31) : (l >> 6), kk = p.rows_fast ? (l >> 5) : (l & 63);
-        sm.tre[rr][kk] = vr[q];
-        sm.tim[rr][kk] = vi[q];
-      }
-    }
-    Sync::sync();
-    const int64_t r = r0 + i, k = k0 + 8 * c;
+    if (threadIdx.x < 32) b.roff[threadIdx.x] = lookup(t_r, c_r, r0 + threadIdx.x);
+    else if (threadIdx.x < 96) b.koff[threadIdx.x - 32] = lookup(t_k, c_k, k0 + threadIdx.x - 32);
+  };
+  // thread element q (of 8): tile row rr and column kk, lanes along the source-contiguous index
+  auto elem = [&](int q, int& rr, int& kk) {
+    const int l = threadIdx.x + 256 * q;
+    rr = p.rows_fast ? (l & 31) : (l >> 6);
+    kk = p.rows_fast ? (l >> 5) : (l & 63);
+  };
+  // split and store a staged tile
+  auto split_tile = [&](const PermSmem<float>& b, int64_t tile) {
+    const int64_t r = (tile / ntk) * 32 + i, k = (tile % ntk) * 64 + 8 * c;
     uint4 h, m, l;
     {
       float x[8];
       float mx = 0.f;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        x[j] = sm.tre[i][8 * c + j];
+        x[j] = b.tre[i][8 * c + j];
         mx = fmaxf(mx, fabsf(x[j]));
       }
 #pragma unroll
@@ -814,7 +799,7 @@ __device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double
       float mx = 0.f;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        x[j] = sm.tim[i][8 * c + j];
+        x[j] = b.tim[i][8 * c + j];
         mx = fmaxf(mx, fabsf(x[j]));
       }
 #pragma unroll
@@ -827,6 +812,74 @@ __device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double
     } else {
       store3(r * ld + K + k, h, m, l);                                         // Y side: Im
     }
+  };
+  if (sm2 != nullptr && p.src_f32) {
+    // Complex64 source and a second tile buffer: the next tile's values are copied
+    // asynchronously into the other buffer while this one is split, so a tile's load latency
+    // overlaps the previous tile's split and stores instead of following it.
+    PermSmem<float>* const buf[2] = {&sm, sm2};
+    auto issue = [&](PermSmem<float>& b) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int rr, kk;
+        elem(q, rr, kk);
+        const int64_t off = b.roff[rr] + b.koff[kk];
+        cp_async4(&b.tre[rr][kk], srcf + off);
+        cp_async4(&b.tim[rr][kk], srcf + p.plane + off);
+      }
+    };
+    int64_t tile = vb;
+    if (tile < ntiles) lookups(*buf[0], tile);
+    Sync::sync();
+    if (tile < ntiles) issue(*buf[0]);
+    cp_async_commit();
+    int cur = 0;
+    for (; tile < ntiles; tile += vg) {
+      const int64_t next = tile + vg;
+      // buf[cur ^ 1]'s offsets were last read by the copies of two tiles back, issued before the
+      // previous barrier
+      if (next < ntiles) lookups(*buf[cur ^ 1], next);
+      cp_async_wait<0>();
+      Sync::sync();  // this tile's values and the next tile's offsets are visible; every thread
+                     // has split the previous tile, whose buffer the next copies overwrite
+      if (next < ntiles) issue(*buf[cur ^ 1]);
+      cp_async_commit();
+      split_tile(*buf[cur], tile);
+      cur ^= 1;
+    }
+    cp_async_wait<0>();
+    Sync::sync();
+    return;
+  }
+  for (int64_t tile = vb; tile < ntiles; tile += vg) {
+    lookups(sm, tile);
+    Sync::sync();
+    {
+      // all loads (x 2 planes) of a thread are issued before its shared-memory stores
+      float vr[8], vi[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int rr, kk;
+        elem(q, rr, kk);
+        const int64_t off = sm.roff[rr] + sm.koff[kk];
+        if (p.src_f32) {
+          vr[q] = srcf[off];
+          vi[q] = srcf[p.plane + off];
+        } else {
+          vr[q] = static_cast<float>(src[off]);
+          vi[q] = static_cast<float>(src[p.plane + off]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int rr, kk;
+        elem(q, rr, kk);
+        sm.tre[rr][kk] = vr[q];
+        sm.tim[rr][kk] = vi[q];
+      }
+    }
+    Sync::sync();
+    split_tile(sm, tile);
   }
   Sync::sync();
 }
@@ -834,7 +887,7 @@ __device__ __forceinline__ void perm_tiles_bf16x3(const PermDev& p, const double
 template <typename S, typename Sync>
 __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, const double* __restrict__ arena,
                                           char* __restrict__ base, int vb, int vg, int vy, int64_t* tab,
-                                          PermSmem<S>& sm) {
+                                          PermSmem<S>& sm, PermSmem<float>* sm2 = nullptr) {
   constexpr int TKMAX = PermSmem<S>::TKMAX;
   auto& tre = sm.tre;
   auto& tim = sm.tim;
@@ -851,7 +904,7 @@ __device__ __forceinline__ void perm_body(const PermDev* __restrict__ perms, con
   Sync::sync();
   if constexpr (sizeof(S) == 4) {
     if (p.mode == OPM_BF16X3 && p.rbits >= 5 && p.kbits >= 6) {
-      perm_tiles_bf16x3<Sync>(p, arena, base, vb, vg, t_r, c_r, t_k, c_k, sm);
+      perm_tiles_bf16x3<Sync>(p, arena, base, vb, vg, t_r, c_r, t_k, c_k, sm, sm2);
       return;
     }
   }

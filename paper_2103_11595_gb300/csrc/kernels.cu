@@ -75,7 +75,12 @@ __global__ void __launch_bounds__(kBodyThreads, 4) k_perm(const PermDev* __restr
                                                        const double* __restrict__ arena, char* __restrict__ base) {
   extern __shared__ int64_t tab[];
   __shared__ PermSmem<S> sm;
-  perm_body<S, SyncBlock>(perms, arena, base, blockIdx.x, gridDim.x, blockIdx.y, tab, sm);
+  if constexpr (sizeof(S) == 4) {
+    __shared__ PermSmem<float> sm2;  // second tile buffer of the six-product split's copy pipeline
+    perm_body<S, SyncBlock>(perms, arena, base, blockIdx.x, gridDim.x, blockIdx.y, tab, sm, &sm2);
+  } else {
+    perm_body<S, SyncBlock>(perms, arena, base, blockIdx.x, gridDim.x, blockIdx.y, tab, sm);
+  }
 }
 
 template <typename T>
